@@ -1,0 +1,174 @@
+/*
+ * nc_pcg.h -- C ABI of the GB300 Newton-Chebyshev preconditioned CG library.
+ *
+ * Method: Bergamaschi & Martinez, "Parallel Newton-Chebyshev Polynomial
+ * Preconditioners for the Conjugate Gradient method".  The library solves
+ * A x = b (A symmetric positive definite, Sec. 1) by PCG whose preconditioner
+ * is z = P_k(A) r, the degree-k Chebyshev polynomial of Sec. 3 applied with
+ * k matrix-vector products by the three-term recurrence of Algorithm 2, with
+ * the modified parameter theta' = s*theta of Sec. 4.
+ *
+ * Conventions for every entry point
+ *  - Pointers named *_dev are CUDA device pointers (for instance the storage
+ *    of torch CUDA tensors) on the current device; pointers named *_host are
+ *    host pointers.  Vectors are dense, contiguous, float64, length n.
+ *  - Memory passed in is owned by the caller.  A matrix handle BORROWS the
+ *    caller's arrays: they must stay alive and unchanged until the handle is
+ *    destroyed.  Memory the library allocates (scaled copies, workspaces) is
+ *    owned by the handle and released by its destroy call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; calls that return host values
+ *    (results, bounds) synchronise that stream before returning.
+ *  - Errors are reported only through nc_status; no call aborts the process.
+ *    On error, output handles are set to NULL and nothing is leaked.
+ *  - A handle may be used by one host thread and one stream at a time.
+ */
+#ifndef NC_PCG_H
+#define NC_PCG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NC_API __attribute__((visibility("default")))
+#else
+#define NC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nc_matrix_s* nc_matrix;
+typedef struct nc_solver_s* nc_solver;
+
+typedef enum {
+    NC_OK = 0,
+    NC_ERR_ARG = 1,          /* invalid argument (null pointer, size, bounds)        */
+    NC_ERR_CUDA = 2,         /* a CUDA runtime call failed                            */
+    NC_ERR_OOM = 3,          /* device allocation failed                              */
+    NC_ERR_INDEFINITE = 4,   /* (p,Ap) <= 0 or (r,z) <= 0: A or P_k(A) not SPD       */
+    NC_ERR_MAXIT = 5,        /* maxit reached before ||r|| <= tol ||b||               */
+    NC_ERR_BREAKDOWN = 6,    /* NaN or Inf in a reduction                             */
+    NC_ERR_UNSUPPORTED = 7   /* option combination not implemented for this format    */
+} nc_status;
+
+/* Value type of the matrix inside P_k(A) (the outer CG stays float64). */
+typedef enum { NC_F64 = 0, NC_F32 = 1, NC_BF16 = 2 } nc_dtype;
+
+typedef struct {
+    int apply_dtype;   /* nc_dtype: F64 = plain method; F32: float32 matrix and
+                          vectors inside P_k; BF16: bfloat16 matrix values,
+                          float32 vectors and accumulation.                     */
+    int rr_period;     /* > 0: replace r by b - A x in float64 every rr_period
+                          iterations (mixed precision); 0 = never.              */
+    int x0_is_zero;    /* 1: ignore x on input and start from x0 = 0 (saves the
+                          initial product b - A x0).                            */
+    int use_graph;     /* 1 (default): one CUDA graph per solve with the
+                          stopping test evaluated on the device; 0: host loop
+                          reading the residual every iteration.                 */
+} nc_options;
+
+typedef struct {
+    int32_t iters;        /* PCG iterations                                      */
+    int32_t status;       /* nc_status of the solve                              */
+    double relres;        /* ||r_i|| / ||b||, recurrence residual, scaled system */
+    double true_relres;   /* ||b - A x|| / ||b|| recomputed at exit, same system */
+    int64_t n_spmv;       /* products with A: (k+1) per iteration (Table 4)      */
+    int64_t n_dot;        /* dot products: 3 per iteration (Table 4)             */
+} nc_result;
+
+/* Fill `opt` with the defaults: F64, no residual replacement, x0 from x,
+ * graph on. */
+NC_API void nc_options_default(nc_options* opt);
+NC_API const char* nc_strerror(nc_status s);
+NC_API const char* nc_version(void);
+/* Text of the last CUDA runtime error seen by this thread (after NC_ERR_CUDA). */
+NC_API const char* nc_last_cuda_error(void);
+
+/* ---- Matrices ------------------------------------------------------------
+ * The paper needs only v -> A v (Sec. 1, "matrix-free regime"); Sec. 5.2 keeps
+ * complete consecutive rows together (block-row distribution).  Handles hold
+ * the operator the polynomial is applied to.
+ */
+
+/* CSR, float64 values.  rowptr_dev: n+1 int32 (rowptr[0] = 0, nondecreasing,
+ * rowptr[n] = nnz); col_dev: nnz int32 in [0, n); val_dev: nnz float64.
+ * Borrowed.  n = 0 is accepted (an empty system).  NC_ERR_ARG on n < 0,
+ * nnz < 0, nnz >= 2^31 or a null pointer with n > 0. */
+NC_API nc_status nc_matrix_csr(int64_t n, int64_t nnz, const int32_t* rowptr_dev,
+                        const int32_t* col_dev, const double* val_dev, nc_matrix* out);
+
+/* Symmetric diagonal (Jacobi) scaling A_s = D^{-1/2} A D^{-1/2}, D = diag(A)
+ * (Sec. 2, end: "symmetrically scaled by the diagonal"; Sec. 5: all matrices
+ * are scaled before solving).  Returns a new handle that OWNS the scaled
+ * values and d^{-1/2}; it still borrows A's index arrays, so A's arrays must
+ * outlive it.  pcg_solve on a solver built on this handle solves the
+ * original system A x = b: it forms b_s = D^{-1/2} b, solves A_s y = b_s
+ * (the stopping test is on this scaled system) and returns x = D^{-1/2} y.
+ * NC_ERR_ARG if a diagonal entry is missing or not positive. */
+NC_API nc_status nc_matrix_jacobi(nc_matrix A, void* stream, nc_matrix* out);
+
+/* y_dev = A x_dev for the handle's operator.  x_dev, y_dev: n float64,
+ * distinct buffers. */
+NC_API nc_status nc_matvec(nc_matrix A, const double* x_dev, double* y_dev, void* stream);
+
+/* Estimate an interval [lmin, lmax] containing the spectrum (needed by
+ * Algorithm 1 step 1 and by Algorithm 2; Sec. 5.1 uses the power method and
+ * DACG, this library a `steps`-step Lanczos run without reorthogonalisation
+ * from the start vector v0_dev, n float64, nonzero).  lmax is made safe:
+ * max(ritz_max + |b_m s_m|, 1.01 ritz_max), capped by the Gershgorin bound
+ * max_i sum_j |a_ij| when that lies in [ritz_max, lmax); lmin = ritz_min.
+ * ritz_min / ritz_max (may be NULL) return the raw extreme Ritz values.
+ * NC_ERR_ARG if steps < 1 or steps > 256. */
+NC_API nc_status nc_bounds_lanczos(nc_matrix A, int steps, const double* v0_dev, void* stream,
+                            double* lmin, double* lmax, double* ritz_min, double* ritz_max);
+
+/* Gershgorin upper bound max_i sum_j |a_ij| of the handle's operator. */
+NC_API nc_status nc_gershgorin(nc_matrix A, void* stream, double* bound);
+
+NC_API nc_status nc_matrix_destroy(nc_matrix A);
+
+/* ---- Solver -------------------------------------------------------------- */
+
+/* Build a solver for the handle's operator with spectral interval
+ * [lambda_min, lambda_max] (Sec. 3: I = [alpha, beta] containing the
+ * spectrum), polynomial degree degree_k >= 0 (k matrix-vector products per
+ * application; k = 0 is diagonal-scaled CG, P = 1/theta) and theta scale
+ * theta_scale = s > 0 (Sec. 4: theta' = s theta, delta unchanged, sigma =
+ * theta'/delta; s = 1 is the exact Chebyshev polynomial, the paper uses
+ * 1.01 and 1.001).  The recurrence scalars rho_0..rho_k (Eq. rhocheb) are
+ * computed here in float64.  opt may be NULL (defaults).  Allocates the
+ * workspaces (about 8 float64 vectors) and, for F32/BF16 apply, a converted
+ * copy of the matrix values.  The matrix handle must outlive the solver.
+ * NC_ERR_ARG unless 0 < lambda_min < lambda_max, degree_k <= 4096. */
+NC_API nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degree_k,
+                    double theta_scale, const nc_options* opt, void* stream, nc_solver* out);
+
+/* z_dev = P_k(A) v_dev (Algorithm 2 with the recurrence indices rho_k,
+ * rho_{k-1} that its derivation requires), in the solver's apply precision
+ * (inputs and outputs float64).  For parity checks and standalone use. */
+NC_API nc_status pcg_apply_poly(nc_solver S, const double* v_dev, double* z_dev, void* stream);
+
+/* Solve A x = b by PCG (three dot products and k+1 products with A per
+ * iteration, Table 4), stopping when ||r_i|| <= tol ||b|| (Sec. 5) or after
+ * maxit iterations.  b_dev: n float64 (read only); x_dev: n float64, the
+ * initial guess on input (ignored if opt.x0_is_zero) and the solution on
+ * output.  `res` (may be NULL) receives the counts and residuals; the
+ * returned status equals res->status.  On NC_ERR_MAXIT, NC_ERR_INDEFINITE or
+ * NC_ERR_BREAKDOWN x_dev holds the last iterate.  b = 0 returns x = 0 with
+ * 0 iterations.  Synchronises `stream`. */
+NC_API nc_status pcg_solve(nc_solver S, const double* b_dev, double* x_dev, double tol, int maxit,
+                    void* stream, nc_result* res);
+
+/* As pcg_solve with host buffers: copies b_host (n float64) to the device,
+ * solves, and copies the solution back to x_host.  Pinned host memory gives
+ * asynchronous copies; pageable memory works too. */
+NC_API nc_status pcg_solve_host(nc_solver S, const double* b_host, double* x_host, double tol,
+                         int maxit, void* stream, nc_result* res);
+
+NC_API nc_status pcg_destroy(nc_solver S);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NC_PCG_H */

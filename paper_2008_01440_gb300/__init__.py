@@ -1,0 +1,46 @@
+"""GB300-native Newton-Chebyshev polynomial-preconditioned CG (sm_103a).
+
+The compute path is the C-ABI library ``libncpcg.so`` (hand-written CUDA,
+``csrc/``); ``binding`` marshals torch tensors into its calls.  There is no
+CPU fallback: importing the package builds the library if it is missing
+(nvcc required) and raises if that is impossible.
+"""
+import os as _os
+
+from .build import LIB as _LIB
+from .build import build as _build
+
+if not _os.path.exists(_LIB):
+    _build()
+
+from .binding import (  # noqa: F401
+    NC_BF16,
+    NC_ERR_ARG,
+    NC_ERR_BREAKDOWN,
+    NC_ERR_CUDA,
+    NC_ERR_INDEFINITE,
+    NC_ERR_MAXIT,
+    NC_ERR_OOM,
+    NC_ERR_UNSUPPORTED,
+    NC_F32,
+    NC_F64,
+    NC_OK,
+    LIB_PATH,
+    Matrix,
+    NcError,
+    Solver,
+    lib,
+    make_options,
+    nc_bounds_lanczos,
+    nc_gershgorin,
+    nc_matrix_csr,
+    nc_matrix_destroy,
+    nc_matrix_jacobi,
+    nc_matvec,
+    nc_version,
+    pcg_apply_poly,
+    pcg_destroy,
+    pcg_setup,
+    pcg_solve,
+    pcg_solve_host,
+)

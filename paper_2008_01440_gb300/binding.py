@@ -1,0 +1,257 @@
+"""ctypes binding of libncpcg (include/nc_pcg.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: torch tensors are turned into device pointers and
+streams into ``cudaStream_t`` handles; every step of the solve runs in the
+library's CUDA kernels.  Importing this module fails loudly when the library
+has not been built (``__graft_entry__.build()`` or
+``python -m paper_2008_01440_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libncpcg.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libncpcg.so not built at {LIB_PATH}; run paper_2008_01440_gb300.build.build()")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+NC_OK, NC_ERR_ARG, NC_ERR_CUDA, NC_ERR_OOM, NC_ERR_INDEFINITE, NC_ERR_MAXIT, NC_ERR_BREAKDOWN, \
+    NC_ERR_UNSUPPORTED = range(8)
+NC_F64, NC_F32, NC_BF16 = 0, 1, 2
+_DTYPES = {"f64": NC_F64, "f32": NC_F32, "bf16": NC_BF16}
+# statuses a solve may end with while still returning a meaningful iterate
+SOLVE_STATUSES = (NC_OK, NC_ERR_MAXIT, NC_ERR_INDEFINITE, NC_ERR_BREAKDOWN)
+
+
+class nc_options(ctypes.Structure):
+    _fields_ = [("apply_dtype", ctypes.c_int), ("rr_period", ctypes.c_int),
+                ("x0_is_zero", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class nc_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("relres", ctypes.c_double),
+                ("true_relres", ctypes.c_double), ("n_spmv", ctypes.c_int64), ("n_dot", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_dbl = ctypes.c_double
+_pd = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "nc_options_default": (None, [ctypes.POINTER(nc_options)]),
+    "nc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "nc_version": (ctypes.c_char_p, []),
+    "nc_last_cuda_error": (ctypes.c_char_p, []),
+    "nc_matrix_csr": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "nc_matrix_jacobi": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "nc_matvec": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "nc_bounds_lanczos": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _pd, _pd, _pd, _pd]),
+    "nc_gershgorin": (ctypes.c_int, [_vp, _vp, _pd]),
+    "nc_matrix_destroy": (ctypes.c_int, [_vp]),
+    "pcg_setup": (ctypes.c_int, [_vp, _dbl, _dbl, ctypes.c_int, _dbl, ctypes.POINTER(nc_options), _vp,
+                                 ctypes.POINTER(_vp)]),
+    "pcg_apply_poly": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "pcg_solve": (ctypes.c_int, [_vp, _vp, _vp, _dbl, ctypes.c_int, _vp, ctypes.POINTER(nc_result)]),
+    "pcg_solve_host": (ctypes.c_int, [_vp, _vp, _vp, _dbl, ctypes.c_int, _vp, ctypes.POINTER(nc_result)]),
+    "pcg_destroy": (ctypes.c_int, [_vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class NcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib.nc_strerror(status).decode()
+        if status == NC_ERR_CUDA:
+            msg += ": " + lib.nc_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != NC_OK:
+        raise NcError(status, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t, dtype=None, n=None, what="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what}: expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{what}: expected {dtype}, got {t.dtype}")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{what}: expected {n} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+@dataclass
+class Matrix:
+    """Owning wrapper of an nc_matrix handle; keeps the borrowed tensors alive."""
+    handle: int
+    n: int
+    keep: tuple
+    parent: "Matrix | None" = None
+
+    def close(self):
+        if self.handle:
+            lib.nc_matrix_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class Solver:
+    handle: int
+    n: int
+    matrix: Matrix
+    degree: int
+
+    def close(self):
+        if self.handle:
+            lib.pcg_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nc_version() -> str:
+    return lib.nc_version().decode()
+
+
+def nc_matrix_csr(rowptr, col, val) -> Matrix:
+    import torch
+    n = rowptr.numel() - 1
+    nnz = col.numel()
+    h = _vp()
+    _check(lib.nc_matrix_csr(n, nnz, _ptr(rowptr, torch.int32, what="rowptr"),
+                             _ptr(col, torch.int32, what="col"), _ptr(val, torch.float64, nnz, "val"),
+                             ctypes.byref(h)), "nc_matrix_csr")
+    return Matrix(h.value, n, (rowptr, col, val))
+
+
+def nc_matrix_jacobi(A: Matrix, stream=None) -> Matrix:
+    h = _vp()
+    _check(lib.nc_matrix_jacobi(A.handle, _stream(stream), ctypes.byref(h)), "nc_matrix_jacobi")
+    return Matrix(h.value, A.n, A.keep, parent=A)
+
+
+def nc_matvec(A: Matrix, x, y, stream=None):
+    import torch
+    _check(lib.nc_matvec(A.handle, _ptr(x, torch.float64, A.n, "x"), _ptr(y, torch.float64, A.n, "y"),
+                         _stream(stream)), "nc_matvec")
+
+
+def nc_gershgorin(A: Matrix, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(lib.nc_gershgorin(A.handle, _stream(stream), ctypes.byref(out)), "nc_gershgorin")
+    return out.value
+
+
+def nc_bounds_lanczos(A: Matrix, steps: int, v0, stream=None):
+    """Return (lmin, lmax, ritz_min, ritz_max)."""
+    import torch
+    lo, hi, rmin, rmax = (ctypes.c_double() for _ in range(4))
+    _check(lib.nc_bounds_lanczos(A.handle, steps, _ptr(v0, torch.float64, A.n, "v0"), _stream(stream),
+                                 ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(rmin), ctypes.byref(rmax)),
+           "nc_bounds_lanczos")
+    return lo.value, hi.value, rmin.value, rmax.value
+
+
+def make_options(apply_dtype="f64", rr_period=0, x0_is_zero=False, use_graph=True) -> nc_options:
+    o = nc_options()
+    lib.nc_options_default(ctypes.byref(o))
+    o.apply_dtype = _DTYPES[apply_dtype] if isinstance(apply_dtype, str) else int(apply_dtype)
+    o.rr_period = int(rr_period)
+    o.x0_is_zero = int(bool(x0_is_zero))
+    o.use_graph = int(bool(use_graph))
+    return o
+
+
+def pcg_setup(A: Matrix, lambda_min: float, lambda_max: float, degree_k: int, theta_scale: float = 1.0,
+              stream=None, **options) -> Solver:
+    opt = make_options(**options)
+    h = _vp()
+    _check(lib.pcg_setup(A.handle, float(lambda_min), float(lambda_max), int(degree_k), float(theta_scale),
+                         ctypes.byref(opt), _stream(stream), ctypes.byref(h)), "pcg_setup")
+    return Solver(h.value, A.n, A, int(degree_k))
+
+
+def pcg_apply_poly(S: Solver, v, z, stream=None):
+    import torch
+    _check(lib.pcg_apply_poly(S.handle, _ptr(v, torch.float64, S.n, "v"), _ptr(z, torch.float64, S.n, "z"),
+                              _stream(stream)), "pcg_apply_poly")
+
+
+def pcg_solve(S: Solver, b, x, tol: float, maxit: int, stream=None) -> dict:
+    import torch
+    res = nc_result()
+    st = lib.pcg_solve(S.handle, _ptr(b, torch.float64, S.n, "b"), _ptr(x, torch.float64, S.n, "x"),
+                       float(tol), int(maxit), _stream(stream), ctypes.byref(res))
+    if st not in SOLVE_STATUSES:
+        _check(st, "pcg_solve")
+    return res.as_dict()
+
+
+def pcg_solve_host(S: Solver, b, x, tol: float, maxit: int, stream=None) -> dict:
+    """b, x: host (CPU) float64 tensors or numpy arrays of length n (pinned for async copies)."""
+    res = nc_result()
+
+    def hptr(a, what):
+        import numpy as np
+        try:
+            import torch
+            if isinstance(a, torch.Tensor):
+                if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != S.n:
+                    raise TypeError(f"{what}: expected a contiguous CPU float64 tensor of length {S.n}")
+                return a.data_ptr()
+        except ImportError:
+            pass
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size == S.n):
+            raise TypeError(f"{what}: expected a contiguous float64 array of length {S.n}")
+        return a.ctypes.data
+
+    st = lib.pcg_solve_host(S.handle, hptr(b, "b"), hptr(x, "x"), float(tol), int(maxit), _stream(stream),
+                            ctypes.byref(res))
+    if st not in SOLVE_STATUSES:
+        _check(st, "pcg_solve_host")
+    return res.as_dict()
+
+
+def pcg_destroy(S: Solver):
+    S.close()
+
+
+def nc_matrix_destroy(A: Matrix):
+    A.close()

@@ -1,0 +1,685 @@
+// C ABI of libncpcg: matrix handles, the polynomial setup, Lanczos bounds
+// and the PCG solve (declarations and contracts in include/nc_pcg.h).
+//
+// A solve is one CUDA graph: a prologue (||b||, r0, z0 = P_k r0, p0 = z0)
+// followed by a conditional WHILE node whose body is one PCG iteration
+//   q = A p, (p,q) -> alpha;  x += alpha p, r -= alpha q, (r,r) -> stop?;
+//   z = P_k(A) r (k fused steps, the last with (r,z) -> beta);  p = z + beta p
+// and whose condition is written on the device by the p-update kernel, so
+// the host waits once per solve.  Every kernel of the body returns at once
+// after the stopping test has fired, so the final iteration does not apply
+// the preconditioner (the counts of Table 4: (k+1) products with A and 3 dot
+// products per iteration).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nc_common.cuh"
+
+using namespace nc;
+
+enum MatKind : int { MAT_CSR = 0 };
+
+struct nc_matrix_s {
+    int kind = MAT_CSR;
+    int64_t n = 0, nnz = 0;
+    const int32_t* rowptr = nullptr;
+    const int32_t* col = nullptr;
+    const double* val = nullptr;    // values used by products (borrowed or owned_val)
+    double* owned_val = nullptr;    // scaled copy (nc_matrix_jacobi)
+    double* dis = nullptr;          // d^{-1/2} of the scaling, owned
+};
+
+struct nc_solver_s {
+    nc_matrix A = nullptr;
+    int64_t n = 0;
+    int k = 0;
+    double s = 1.0, lmin = 0.0, lmax = 0.0;
+    nc_options opt{};
+    double theta = 0.0, delta = 0.0, sigma = 0.0;
+    std::vector<double> ca, cb, cc, cd;   // per Chebyshev step 1..k (index 0 unused)
+    bool mixed = false;
+    int vdt = NC_F64;
+    const void* pval = nullptr;           // matrix values inside P_k
+    void* lval = nullptr;                 // converted copy (F32/BF16), owned
+    double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    void* buf[3] = {nullptr, nullptr, nullptr};
+    float* r32 = nullptr;
+    PcgScalars* S = nullptr;
+    double* partials = nullptr;
+    unsigned int* counter = nullptr;
+    PcgScalars* h_io = nullptr;           // pinned host copy of the scalars
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_failed = false;
+};
+
+namespace {
+
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+#define NC_CU(call)                                   \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) {                      \
+            g_last_cuda = e_;                         \
+            return NC_ERR_CUDA;                       \
+        }                                             \
+    } while (0)
+
+#define NC_TRY(call)                     \
+    do {                                 \
+        nc_status s_ = (call);           \
+        if (s_ != NC_OK) return s_;      \
+    } while (0)
+
+nc_status dev_alloc(void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        *p = nullptr;
+        return NC_ERR_OOM;
+    }
+    if (e != cudaSuccess) {
+        g_last_cuda = e;
+        *p = nullptr;
+        return NC_ERR_CUDA;
+    }
+    return NC_OK;
+}
+
+template <typename T>
+nc_status dev_alloc_n(T** p, int64_t count) {
+    return dev_alloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)(count > 0 ? count : 1));
+}
+
+void dev_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+int64_t max_partials(int64_t n) {
+    const int64_t rows = (n + kBlock - 1) / kBlock;
+    return (rows > kVecGrid ? rows : kVecGrid) + 1;
+}
+
+Reduce make_reduce(double* partials, unsigned int* counter, PcgScalars* S, double* out, int fin) {
+    Reduce R;
+    R.partials = partials;
+    R.counter = counter;
+    R.S = S;
+    R.out = out;
+    R.fin = fin;
+    return R;
+}
+
+// y = ca u + cb w + cc r + cd (A u) with the handle's float64 values
+cudaError_t op_step_f64(nc_matrix A, const double* u, const double* w, const double* r, double* y,
+                        double ca, double cb, double cc, double cd, int dot, const double* rdot,
+                        const Reduce& R, const int* done, cudaStream_t st) {
+    return launch_csr_step((int)A->n, A->rowptr, A->col, A->val, NC_F64, false, true, u, w, r, y, ca,
+                           cb, cc, cd, dot, rdot, R, done, st);
+}
+
+// Cyclic Jacobi eigen-decomposition of a small symmetric matrix (row-major),
+// eigenvectors in the columns of V.  Used only for the Lanczos tridiagonal.
+void sym_eig(int m, std::vector<double>& a, std::vector<double>& V) {
+    V.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) V[(size_t)i * m + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                const double v = a[(size_t)i * m + j] * a[(size_t)i * m + j];
+                tot += v;
+                if (i != j) off += v;
+            }
+        if (off <= 1e-32 * tot || off == 0.0) break;
+        for (int p = 0; p < m - 1; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                const double apq = a[(size_t)p * m + q];
+                if (apq == 0.0) continue;
+                const double app = a[(size_t)p * m + p], aqq = a[(size_t)q * m + q];
+                const double th = (aqq - app) / (2.0 * apq);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < m; ++k) {   // columns p, q
+                    const double akp = a[(size_t)k * m + p], akq = a[(size_t)k * m + q];
+                    a[(size_t)k * m + p] = c * akp - s * akq;
+                    a[(size_t)k * m + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < m; ++k) {   // rows p, q
+                    const double apk = a[(size_t)p * m + k], aqk = a[(size_t)q * m + k];
+                    a[(size_t)p * m + k] = c * apk - s * aqk;
+                    a[(size_t)q * m + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < m; ++k) {
+                    const double vkp = V[(size_t)k * m + p], vkq = V[(size_t)k * m + q];
+                    V[(size_t)k * m + p] = c * vkp - s * vkq;
+                    V[(size_t)k * m + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+// ---- solver internals -------------------------------------------------------
+
+// Coefficients of the fused steps from rho_k (Eq. rhocheb), theta' = s theta.
+void setup_coefficients(nc_solver S) {
+    const double theta = S->s * (S->lmax + S->lmin) / 2.0;
+    const double delta = (S->lmax - S->lmin) / 2.0;
+    const double sigma = theta / delta;
+    S->theta = theta;
+    S->delta = delta;
+    S->sigma = sigma;
+    const int k = S->k;
+    std::vector<double> rho(k + 1);
+    rho[0] = 1.0 / sigma;
+    for (int j = 1; j <= k; ++j) rho[j] = 1.0 / (2.0 * sigma - rho[j - 1]);
+    S->ca.assign(k + 1, 0.0);
+    S->cb.assign(k + 1, 0.0);
+    S->cc.assign(k + 1, 0.0);
+    S->cd.assign(k + 1, 0.0);
+    if (k >= 1) {   // x_1 = (2 rho_1/delta)(2 r - A r/theta), product applied to u = r
+        S->ca[1] = 4.0 * rho[1] / delta;
+        S->cd[1] = -2.0 * rho[1] / (delta * theta);
+    }
+    for (int j = 2; j <= k; ++j) {
+        S->ca[j] = 2.0 * sigma * rho[j];
+        S->cb[j] = -rho[j] * rho[j - 1];
+        S->cc[j] = 2.0 * rho[j] / delta;
+        S->cd[j] = -2.0 * rho[j] / delta;
+    }
+    if (k >= 2) {   // x_0 = r/theta: fold the x_{k-2} term of step 2 into its r term
+        S->cc[2] += S->cb[2] / theta;
+        S->cb[2] = 0.0;
+    }
+}
+
+// z = P_k(A) r.  r64: float64 residual; the mixed path reads S->r32 (which
+// must already hold (float) r64).  fin: reduction of (r, z) or FIN_NONE.
+cudaError_t enqueue_poly(nc_solver S, const double* r64, double* z, int fin, const int* done,
+                         cudaStream_t st) {
+    const int n = (int)S->n;
+    const Reduce R = make_reduce(S->partials, S->counter, S->S, nullptr, fin);
+    if (S->k == 0) return launch_scale_dot(n, r64, 1.0 / S->theta, z, R, done, st);
+    const void* rx = S->mixed ? static_cast<const void*>(S->r32) : static_cast<const void*>(r64);
+    nc_matrix A = S->A;
+    for (int j = 1; j <= S->k; ++j) {
+        const void* u = (j == 1) ? rx : S->buf[(j - 1) % 3];
+        const void* w = (j >= 3) ? S->buf[(j - 2) % 3] : nullptr;
+        const bool last = (j == S->k);
+        void* y = last ? static_cast<void*>(z) : S->buf[j % 3];
+        const int dot = (last && fin != FIN_NONE) ? 1 : 0;
+        cudaError_t e = launch_csr_step(n, A->rowptr, A->col, S->pval, S->vdt, S->mixed,
+                                        last || !S->mixed, u, w, rx, y, S->ca[j], S->cb[j], S->cc[j],
+                                        S->cd[j], dot, r64, R, done, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_prologue(nc_solver S, cudaStream_t st) {
+    const int n = (int)S->n;
+    const int* done = &S->S->done;
+    cudaError_t e;
+    e = launch_dot(n, S->b, S->b, make_reduce(S->partials, S->counter, S->S, nullptr, FIN_BB), nullptr, st);
+    if (e) return e;
+    if (S->opt.x0_is_zero) {
+        e = launch_copy(n, S->b, S->r, nullptr, st);
+    } else {
+        const Reduce none = make_reduce(S->partials, S->counter, S->S, nullptr, FIN_NONE);
+        e = op_step_f64(S->A, S->x, nullptr, S->b, S->r, 0.0, 0.0, 1.0, -1.0, 0, nullptr, none, nullptr, st);
+    }
+    if (e) return e;
+    if (S->mixed) {
+        e = launch_convert(S->n, S->r, NC_F32, S->r32, st);
+        if (e) return e;
+    }
+    e = launch_dot(n, S->r, S->r, make_reduce(S->partials, S->counter, S->S, nullptr, FIN_RR0), nullptr, st);
+    if (e) return e;
+    e = enqueue_poly(S, S->r, S->z, FIN_RZ0, done, st);
+    if (e) return e;
+    return launch_copy(n, S->z, S->p, done, st);
+}
+
+cudaError_t enqueue_body(nc_solver S, cudaGraphConditionalHandle h, int use_cond, cudaStream_t st) {
+    const int n = (int)S->n;
+    const int* done = &S->S->done;
+    cudaError_t e;
+    e = op_step_f64(S->A, S->p, nullptr, nullptr, S->q, 0.0, 0.0, 0.0, 1.0, 2, nullptr,
+                    make_reduce(S->partials, S->counter, S->S, nullptr, FIN_ALPHA), done, st);
+    if (e) return e;
+    e = launch_axpy2_rr(n, S->x, S->r, S->p, S->q, S->mixed ? S->r32 : nullptr,
+                        make_reduce(S->partials, S->counter, S->S, nullptr, FIN_RR), st);
+    if (e) return e;
+    e = enqueue_poly(S, S->r, S->z, FIN_BETA, done, st);
+    if (e) return e;
+    return launch_p_update(n, S->p, S->z, S->S, h, use_cond, st);
+}
+
+nc_status build_graph(nc_solver S) {
+    cudaGraph_t g = nullptr, gp = nullptr, gb = nullptr;
+    cudaGraphNode_t np = nullptr, nw = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    nc_status st = NC_ERR_CUDA;
+    cudaError_t e;
+    do {
+        if ((e = cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal))) break;
+        cudaError_t e1 = enqueue_prologue(S, S->cap);
+        e = cudaStreamEndCapture(S->cap, &gp);
+        if (e1) { e = e1; break; }
+        if (e) break;
+        if ((e = cudaGraphCreate(&g, 0))) break;
+        if ((e = cudaGraphAddChildGraphNode(&np, g, nullptr, 0, gp))) break;
+        if ((e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault))) break;
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if ((e = cudaGraphAddNode(&nw, g, &np, nullptr, 1, &cp))) break;
+        gb = cp.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(S->cap, gb, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal)))
+            break;
+        e1 = enqueue_body(S, h, 1, S->cap);
+        cudaGraph_t gb_out = nullptr;
+        e = cudaStreamEndCapture(S->cap, &gb_out);
+        if (e1) { e = e1; break; }
+        if (e) break;
+        if ((e = cudaGraphInstantiate(&S->exec, g, 0))) break;
+        st = NC_OK;
+    } while (0);
+    if (st != NC_OK) {
+        g_last_cuda = e;
+        cudaGetLastError();
+        S->exec = nullptr;
+    }
+    if (gp) cudaGraphDestroy(gp);
+    if (g) cudaGraphDestroy(g);
+    return st;
+}
+
+nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol, int maxit,
+                    cudaStream_t st, nc_result* res) {
+    const int n = (int)S->n;
+    PcgScalars init;
+    std::memset(&init, 0, sizeof(init));
+    init.tol2 = tol * tol;
+    init.maxit = maxit;
+    init.status = NC_ERR_MAXIT;
+    // the pinned staging block is reused by every solve; the previous solve
+    // synchronised the stream, so it is free
+    *S->h_io = init;
+    NC_CU(cudaMemcpyAsync(S->S, S->h_io, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
+    NC_CU(launch_copy_in(n, b_dev, x_dev, S->A->dis, S->opt.x0_is_zero, S->b, S->x, st));
+    bool graph = S->opt.use_graph && !S->graph_failed;
+    if (graph && S->exec == nullptr) {
+        if (build_graph(S) != NC_OK) {
+            S->graph_failed = true;
+            graph = false;
+        }
+    }
+    if (graph) {
+        NC_CU(cudaGraphLaunch(S->exec, st));
+    } else {
+        NC_CU(enqueue_prologue(S, st));
+        for (;;) {
+            NC_CU(cudaMemcpyAsync(S->h_io, S->S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+            NC_CU(cudaStreamSynchronize(st));
+            if (S->h_io->done) break;
+            NC_CU(enqueue_body(S, 0, 0, st));
+        }
+    }
+    // true residual of the (scaled) system at exit
+    const Reduce none = make_reduce(S->partials, S->counter, S->S, nullptr, FIN_NONE);
+    NC_CU(op_step_f64(S->A, S->x, nullptr, S->b, S->q, 0.0, 0.0, 1.0, -1.0, 0, nullptr, none, nullptr, st));
+    NC_CU(launch_dot(n, S->q, S->q, make_reduce(S->partials, S->counter, S->S, nullptr, FIN_TRUE), nullptr, st));
+    NC_CU(launch_copy_out(n, S->x, S->A->dis, S->S, x_dev, st));
+    NC_CU(cudaMemcpyAsync(S->h_io, S->S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+    NC_CU(cudaStreamSynchronize(st));
+    const PcgScalars& o = *S->h_io;
+    const double bnorm = std::sqrt(o.bb);
+    nc_result rr;
+    rr.iters = o.iter;
+    rr.status = o.status;
+    rr.relres = bnorm > 0 ? std::sqrt(o.rr) / bnorm : 0.0;
+    rr.true_relres = bnorm > 0 ? std::sqrt(o.rr_true) / bnorm : 0.0;
+    rr.n_dot = o.n_dot;
+    rr.n_spmv = (int64_t)o.iter + (int64_t)S->k * o.n_prec;
+    if (res) *res = rr;
+    return (nc_status)o.status;
+}
+
+}  // namespace
+
+// =============================================================================
+extern "C" {
+
+void nc_options_default(nc_options* opt) {
+    if (!opt) return;
+    opt->apply_dtype = NC_F64;
+    opt->rr_period = 0;
+    opt->x0_is_zero = 0;
+    opt->use_graph = 1;
+}
+
+const char* nc_strerror(nc_status s) {
+    switch (s) {
+    case NC_OK: return "ok";
+    case NC_ERR_ARG: return "invalid argument";
+    case NC_ERR_CUDA: return "CUDA runtime error";
+    case NC_ERR_OOM: return "device out of memory";
+    case NC_ERR_INDEFINITE: return "indefinite operator or preconditioner ((p,Ap) or (r,z) <= 0)";
+    case NC_ERR_MAXIT: return "maximum iterations reached";
+    case NC_ERR_BREAKDOWN: return "NaN or Inf in a reduction";
+    case NC_ERR_UNSUPPORTED: return "unsupported option for this matrix format";
+    }
+    return "unknown status";
+}
+
+const char* nc_version(void) { return "ncpcg 0.1 (sm_103a)"; }
+
+const char* nc_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda); }
+
+nc_status nc_matrix_csr(int64_t n, int64_t nnz, const int32_t* rowptr_dev, const int32_t* col_dev,
+                        const double* val_dev, nc_matrix* out) {
+    if (!out) return NC_ERR_ARG;
+    *out = nullptr;
+    if (n < 0 || nnz < 0 || nnz >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31)) return NC_ERR_ARG;
+    if (n > 0 && (!rowptr_dev || (nnz > 0 && (!col_dev || !val_dev)))) return NC_ERR_ARG;
+    nc_matrix A = new (std::nothrow) nc_matrix_s();
+    if (!A) return NC_ERR_OOM;
+    A->kind = MAT_CSR;
+    A->n = n;
+    A->nnz = nnz;
+    A->rowptr = rowptr_dev;
+    A->col = col_dev;
+    A->val = val_dev;
+    *out = A;
+    return NC_OK;
+}
+
+nc_status nc_matrix_jacobi(nc_matrix A, void* stream, nc_matrix* out) {
+    if (!A || !out) return NC_ERR_ARG;
+    *out = nullptr;
+    if (A->dis) return NC_ERR_ARG;   // already scaled
+    cudaStream_t st = as_stream(stream);
+    nc_matrix B = new (std::nothrow) nc_matrix_s(*A);
+    if (!B) return NC_ERR_OOM;
+    B->owned_val = nullptr;
+    B->dis = nullptr;
+    int* bad = nullptr;
+    int h_bad = 0;
+    nc_status s = NC_OK;
+    do {
+        if ((s = dev_alloc_n(&B->dis, A->n)) != NC_OK) break;
+        if ((s = dev_alloc_n(&B->owned_val, A->nnz)) != NC_OK) break;
+        if ((s = dev_alloc_n(&bad, 1)) != NC_OK) break;
+        cudaError_t e;
+        if ((e = cudaMemsetAsync(bad, 0, sizeof(int), st)) ||
+            (e = launch_csr_diag((int)A->n, A->rowptr, A->col, A->val, B->dis, bad, st)) ||
+            (e = launch_csr_scale((int)A->n, A->rowptr, A->col, A->val, B->dis, B->owned_val, st)) ||
+            (e = cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st))) {
+            g_last_cuda = e;
+            s = NC_ERR_CUDA;
+            break;
+        }
+        if (h_bad) s = NC_ERR_ARG;
+    } while (0);
+    dev_free(bad);
+    if (s != NC_OK) {
+        dev_free(B->dis);
+        dev_free(B->owned_val);
+        delete B;
+        return s;
+    }
+    B->val = B->owned_val;
+    *out = B;
+    return NC_OK;
+}
+
+nc_status nc_matvec(nc_matrix A, const double* x_dev, double* y_dev, void* stream) {
+    if (!A || (A->n > 0 && (!x_dev || !y_dev)) || x_dev == y_dev) return NC_ERR_ARG;
+    const Reduce none = make_reduce(nullptr, nullptr, nullptr, nullptr, FIN_NONE);
+    NC_CU(op_step_f64(A, x_dev, nullptr, nullptr, y_dev, 0.0, 0.0, 0.0, 1.0, 0, nullptr, none, nullptr,
+                      as_stream(stream)));
+    return NC_OK;
+}
+
+nc_status nc_gershgorin(nc_matrix A, void* stream, double* bound) {
+    if (!A || !bound) return NC_ERR_ARG;
+    cudaStream_t st = as_stream(stream);
+    unsigned long long* d = nullptr;
+    unsigned long long h = 0;
+    NC_TRY(dev_alloc_n(&d, 1));
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(d, 0, sizeof(*d), st)) ||
+        (e = launch_csr_gershgorin((int)A->n, A->rowptr, A->val, d, st)) ||
+        (e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st))) {
+        g_last_cuda = e;
+        dev_free(d);
+        return NC_ERR_CUDA;
+    }
+    dev_free(d);
+    double v;
+    std::memcpy(&v, &h, sizeof(v));
+    *bound = v;
+    return NC_OK;
+}
+
+nc_status nc_bounds_lanczos(nc_matrix A, int steps, const double* v0_dev, void* stream, double* lmin,
+                            double* lmax, double* ritz_min, double* ritz_max) {
+    if (!A || !v0_dev || !lmin || !lmax || steps < 1 || steps > 256 || A->n < 1) return NC_ERR_ARG;
+    cudaStream_t st = as_stream(stream);
+    const int n = (int)A->n;
+    double *vp = nullptr, *v = nullptr, *w = nullptr, *part = nullptr, *sc = nullptr;
+    unsigned int* cnt = nullptr;
+    nc_status s = NC_OK;
+    std::vector<double> al, be;
+    do {
+        if ((s = dev_alloc_n(&vp, n)) || (s = dev_alloc_n(&v, n)) || (s = dev_alloc_n(&w, n)) ||
+            (s = dev_alloc_n(&part, max_partials(n))) || (s = dev_alloc_n(&sc, 4)) ||
+            (s = dev_alloc_n(&cnt, 1)))
+            break;
+        cudaError_t e = cudaSuccess;
+        double h = 0.0;
+        auto fetch = [&](double* out) -> cudaError_t {
+            cudaError_t ee = cudaMemcpyAsync(out, sc, sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (ee) return ee;
+            return cudaStreamSynchronize(st);
+        };
+        const Reduce Rs = make_reduce(part, cnt, nullptr, sc, FIN_STORE);
+        if ((e = cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st)) ||
+            (e = cudaMemsetAsync(vp, 0, sizeof(double) * n, st)) ||
+            (e = launch_dot(n, v0_dev, v0_dev, Rs, nullptr, st)) || (e = fetch(&h))) {
+            g_last_cuda = e;
+            s = NC_ERR_CUDA;
+            break;
+        }
+        if (!(h > 0.0) || !std::isfinite(h)) { s = NC_ERR_ARG; break; }
+        if ((e = launch_div(n, v0_dev, std::sqrt(h), v, st))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
+        double b_prev = 0.0;
+        for (int j = 0; j < steps; ++j) {
+            double a = 0.0, ww = 0.0;
+            // w = A v - b_prev v_prev, a = (w, v)
+            if ((e = op_step_f64(A, v, vp, nullptr, w, 0.0, -b_prev, 0.0, 1.0, 2, nullptr, Rs, nullptr, st)) ||
+                (e = fetch(&a)) ||
+                // w = w - a v, ||w||^2
+                (e = launch_axpy_dot(n, -a, v, w, Rs, st)) || (e = fetch(&ww))) {
+                g_last_cuda = e;
+                s = NC_ERR_CUDA;
+                break;
+            }
+            const double b = std::sqrt(ww);
+            al.push_back(a);
+            be.push_back(b);
+            if (b == 0.0 || !std::isfinite(b)) break;
+            // v_prev <- v, v <- w / b
+            if ((e = launch_div(n, w, b, vp, st))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
+            std::swap(vp, v);
+            b_prev = b;
+        }
+    } while (0);
+    dev_free(vp); dev_free(v); dev_free(w); dev_free(part); dev_free(sc); dev_free(cnt);
+    if (s != NC_OK) return s;
+    const int m = (int)al.size();
+    for (int i = 0; i < m; ++i)
+        if (!std::isfinite(al[i])) return NC_ERR_BREAKDOWN;
+    std::vector<double> T((size_t)m * m, 0.0), V;
+    for (int i = 0; i < m; ++i) {
+        T[(size_t)i * m + i] = al[i];
+        if (i + 1 < m) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = be[i];
+    }
+    sym_eig(m, T, V);
+    int imin = 0, imax = 0;
+    for (int i = 1; i < m; ++i) {
+        if (T[(size_t)i * m + i] < T[(size_t)imin * m + imin]) imin = i;
+        if (T[(size_t)i * m + i] > T[(size_t)imax * m + imax]) imax = i;
+    }
+    const double rmin = T[(size_t)imin * m + imin], rmax = T[(size_t)imax * m + imax];
+    const double resid = std::fabs(be[m - 1] * V[(size_t)(m - 1) * m + imax]);
+    double upper = std::fmax(rmax + resid, 1.01 * rmax);
+    double g = 0.0;
+    NC_TRY(nc_gershgorin(A, stream, &g));
+    if (rmax <= g && g < upper) upper = g;
+    *lmin = rmin;
+    *lmax = upper;
+    if (ritz_min) *ritz_min = rmin;
+    if (ritz_max) *ritz_max = rmax;
+    return NC_OK;
+}
+
+nc_status nc_matrix_destroy(nc_matrix A) {
+    if (!A) return NC_ERR_ARG;
+    dev_free(A->owned_val);
+    dev_free(A->dis);
+    delete A;
+    return NC_OK;
+}
+
+nc_status pcg_destroy(nc_solver S);
+
+nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degree_k, double theta_scale,
+                    const nc_options* opt, void* stream, nc_solver* out) {
+    if (!out) return NC_ERR_ARG;
+    *out = nullptr;
+    if (!A || !(lambda_min > 0.0) || !(lambda_max > lambda_min) || !std::isfinite(lambda_max) ||
+        degree_k < 0 || degree_k > 4096 || !(theta_scale > 0.0) || !std::isfinite(theta_scale))
+        return NC_ERR_ARG;
+    nc_options o;
+    nc_options_default(&o);
+    if (opt) o = *opt;
+    if (o.apply_dtype != NC_F64 && o.apply_dtype != NC_F32 && o.apply_dtype != NC_BF16) return NC_ERR_ARG;
+    if (o.rr_period < 0) return NC_ERR_ARG;
+    if (o.rr_period > 0) return NC_ERR_UNSUPPORTED;
+    cudaStream_t st = as_stream(stream);
+    nc_solver S = new (std::nothrow) nc_solver_s();
+    if (!S) return NC_ERR_OOM;
+    S->A = A;
+    S->n = A->n;
+    S->k = degree_k;
+    S->s = theta_scale;
+    S->lmin = lambda_min;
+    S->lmax = lambda_max;
+    S->opt = o;
+    S->mixed = o.apply_dtype != NC_F64;
+    S->vdt = o.apply_dtype;
+    setup_coefficients(S);
+    const int64_t n = S->n;
+    nc_status s = NC_OK;
+    do {
+        if ((s = dev_alloc_n(&S->b, n)) || (s = dev_alloc_n(&S->x, n)) || (s = dev_alloc_n(&S->r, n)) ||
+            (s = dev_alloc_n(&S->z, n)) || (s = dev_alloc_n(&S->p, n)) || (s = dev_alloc_n(&S->q, n)) ||
+            (s = dev_alloc_n(&S->partials, max_partials(n))) || (s = dev_alloc_n(&S->counter, 1)) ||
+            (s = dev_alloc_n(&S->S, 1)))
+            break;
+        const size_t vb = S->mixed ? sizeof(float) : sizeof(double);
+        for (int i = 0; i < 3 && s == NC_OK; ++i) s = dev_alloc(&S->buf[i], vb * (size_t)(n > 0 ? n : 1));
+        if (s) break;
+        if (S->mixed) {
+            if ((s = dev_alloc_n(&S->r32, n))) break;
+            const size_t eb = S->vdt == NC_F32 ? 4 : 2;
+            if ((s = dev_alloc(&S->lval, eb * (size_t)(A->nnz > 0 ? A->nnz : 1)))) break;
+            cudaError_t e = launch_convert(A->nnz, A->val, S->vdt, S->lval, st);
+            if (e) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
+            S->pval = S->lval;
+        } else {
+            S->pval = A->val;
+        }
+        cudaError_t e;
+        if ((e = cudaMemsetAsync(S->counter, 0, sizeof(unsigned int), st)) ||
+            (e = cudaMemsetAsync(S->S, 0, sizeof(PcgScalars), st))) {
+            g_last_cuda = e; s = NC_ERR_CUDA; break;
+        }
+        if ((e = cudaMallocHost(&S->h_io, sizeof(PcgScalars)))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
+        if ((e = cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
+        if ((e = cudaStreamSynchronize(st))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
+    } while (0);
+    if (s != NC_OK) {
+        pcg_destroy(S);
+        return s;
+    }
+    *out = S;
+    return NC_OK;
+}
+
+nc_status pcg_apply_poly(nc_solver S, const double* v_dev, double* z_dev, void* stream) {
+    if (!S || (S->n > 0 && (!v_dev || !z_dev)) || v_dev == z_dev) return NC_ERR_ARG;
+    if (S->n == 0) return NC_OK;
+    cudaStream_t st = as_stream(stream);
+    if (S->mixed) NC_CU(launch_convert(S->n, v_dev, NC_F32, S->r32, st));
+    NC_CU(enqueue_poly(S, v_dev, z_dev, FIN_NONE, nullptr, st));
+    return NC_OK;
+}
+
+nc_status pcg_solve(nc_solver S, const double* b_dev, double* x_dev, double tol, int maxit, void* stream,
+                    nc_result* res) {
+    if (!S || !(tol >= 0.0) || maxit < 0) return NC_ERR_ARG;
+    if (S->n == 0) {
+        if (res) *res = nc_result{0, NC_OK, 0.0, 0.0, 0, 0};
+        return NC_OK;
+    }
+    if (!b_dev || !x_dev || b_dev == x_dev) return NC_ERR_ARG;
+    return run_solve(S, b_dev, x_dev, tol, maxit, as_stream(stream), res);
+}
+
+nc_status pcg_solve_host(nc_solver S, const double* b_host, double* x_host, double tol, int maxit,
+                         void* stream, nc_result* res) {
+    if (!S || !(tol >= 0.0) || maxit < 0) return NC_ERR_ARG;
+    if (S->n == 0) {
+        if (res) *res = nc_result{0, NC_OK, 0.0, 0.0, 0, 0};
+        return NC_OK;
+    }
+    if (!b_host || !x_host) return NC_ERR_ARG;
+    cudaStream_t st = as_stream(stream);
+    const size_t bytes = sizeof(double) * (size_t)S->n;
+    // stage b in q and x0 in z (both are rewritten by the solve before use)
+    NC_CU(cudaMemcpyAsync(S->q, b_host, bytes, cudaMemcpyHostToDevice, st));
+    if (!S->opt.x0_is_zero) NC_CU(cudaMemcpyAsync(S->z, x_host, bytes, cudaMemcpyHostToDevice, st));
+    // copy_in reads the staged vectors before any kernel of the solve writes q or z
+    nc_status s = run_solve(S, S->q, S->z, tol, maxit, st, res);
+    if (s == NC_ERR_CUDA || s == NC_ERR_ARG) return s;
+    NC_CU(cudaMemcpyAsync(x_host, S->z, bytes, cudaMemcpyDeviceToHost, st));
+    NC_CU(cudaStreamSynchronize(st));
+    return s;
+}
+
+nc_status pcg_destroy(nc_solver S) {
+    if (!S) return NC_ERR_ARG;
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->cap) cudaStreamDestroy(S->cap);
+    dev_free(S->b); dev_free(S->x); dev_free(S->r); dev_free(S->z); dev_free(S->p); dev_free(S->q);
+    for (int i = 0; i < 3; ++i) dev_free(S->buf[i]);
+    dev_free(S->r32); dev_free(S->lval); dev_free(S->partials); dev_free(S->counter); dev_free(S->S);
+    if (S->h_io) cudaFreeHost(S->h_io);
+    delete S;
+    return NC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// Internal declarations shared by the CUDA translation units of libncpcg.
+//
+// Device-side PCG state lives in one PcgScalars block so that a whole solve
+// can run as a CUDA graph with no host round trip: every reduction kernel
+// finishes its own dot product in the last CTA to arrive ("last block"
+// pattern, no spin-wait) and that CTA derives the next PCG scalar (alpha,
+// beta, the stopping test) in place.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/nc_pcg.h"
+
+namespace nc {
+
+constexpr int kBlock = 256;           // threads per CTA of the row kernels
+constexpr int kChunk = 2048;          // nonzeros staged in shared memory per pass
+constexpr int kSMs = 152;             // GB300 streaming multiprocessors
+constexpr int kVecGrid = kSMs * 4;    // CTAs of the grid-stride vector kernels
+
+// What the last CTA of a reduction does with the finished sum.
+enum Fin : int {
+    FIN_NONE = 0,
+    FIN_STORE = 1,   // *out = sum
+    FIN_BB = 2,      // bb = (b, b)
+    FIN_RR0 = 3,     // initial (r, r): converged before the first iteration?
+    FIN_RZ0 = 4,     // initial (r, z)
+    FIN_ALPHA = 5,   // (p, q): alpha = rz / pq
+    FIN_RR = 6,      // (r, r) after the update: iteration count and stopping test
+    FIN_BETA = 7,    // new (r, z): beta = rz_new / rz
+    FIN_TRUE = 8     // ||b - A x||^2 at exit
+};
+
+struct PcgScalars {
+    double rz, pq, alpha, beta, rr, bb, tol2, rr_true;
+    int iter, maxit, done, status;
+    int n_dot, n_prec, pad0, pad1;
+};
+
+struct Reduce {
+    double* partials;        // >= gridDim.x doubles
+    unsigned int* counter;   // 0 between reductions; reset by the last CTA
+    PcgScalars* S;           // for the PCG finalize kinds
+    double* out;             // FIN_STORE target
+    int fin;
+};
+
+// ---- device helpers -------------------------------------------------------
+
+// Sum over a CTA of BS threads; the result is valid in every lane of warp 0.
+// The butterfly gives identical values in all lanes and a fixed order, so the
+// reduction is deterministic.
+template <int BS>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    v = (threadIdx.x < BS / 32) ? sh[threadIdx.x] : 0.0;
+    if (warp == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;
+}
+
+__device__ __forceinline__ void finalize(const Reduce& R, double s) {
+    PcgScalars* S = R.S;
+    const bool finite = isfinite(s);
+    switch (R.fin) {
+    case FIN_STORE:
+        *R.out = s;
+        break;
+    case FIN_BB:
+        S->bb = s;
+        break;
+    case FIN_RR0:
+        S->rr = s;
+        if (!finite) { S->status = NC_ERR_BREAKDOWN; S->done = 1; }
+        else if (S->bb == 0.0 || s <= S->tol2 * S->bb) { S->status = NC_OK; S->done = 1; }
+        else if (S->maxit <= 0) { S->status = NC_ERR_MAXIT; S->done = 1; }
+        break;
+    case FIN_RZ0:
+        S->n_dot += 1; S->n_prec += 1;
+        S->rz = s;
+        if (!(s > 0.0)) { S->status = finite ? NC_ERR_INDEFINITE : NC_ERR_BREAKDOWN; S->done = 1; }
+        break;
+    case FIN_ALPHA:
+        S->n_dot += 1;
+        S->pq = s;
+        if (!(s > 0.0) || !finite) { S->status = finite ? NC_ERR_INDEFINITE : NC_ERR_BREAKDOWN; S->done = 1; }
+        else S->alpha = S->rz / s;
+        break;
+    case FIN_RR:
+        S->n_dot += 1;
+        S->rr = s;
+        S->iter += 1;
+        if (!finite) { S->status = NC_ERR_BREAKDOWN; S->done = 1; }
+        else if (s <= S->tol2 * S->bb) { S->status = NC_OK; S->done = 1; }
+        else if (S->iter >= S->maxit) { S->status = NC_ERR_MAXIT; S->done = 1; }
+        break;
+    case FIN_BETA:
+        S->n_dot += 1; S->n_prec += 1;
+        if (!(s > 0.0) || !finite) { S->status = finite ? NC_ERR_INDEFINITE : NC_ERR_BREAKDOWN; S->done = 1; }
+        else { S->beta = s / S->rz; S->rz = s; }
+        break;
+    case FIN_TRUE:
+        S->rr_true = s;
+        break;
+    default:
+        break;
+    }
+}
+
+// Each CTA contributes v (one value per thread); the last CTA to finish sums
+// the per-CTA partials in a fixed order and applies R.fin.  Must be reached
+// by every thread of every CTA of the grid.
+template <int BS>
+__device__ __forceinline__ void grid_reduce(double v, const Reduce& R) {
+    __shared__ double sh[32];
+    __shared__ int is_last;
+    v = block_sum<BS>(v, sh);
+    if (threadIdx.x == 0) {
+        R.partials[blockIdx.x] = v;
+        __threadfence();
+        const unsigned int t = atomicAdd(R.counter, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        double s = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += BS) s += __ldcg(&R.partials[i]);
+        s = block_sum<BS>(s, sh);
+        if (threadIdx.x == 0) {
+            finalize(R, s);
+            *R.counter = 0u;
+        }
+    }
+}
+
+// ---- host-side launchers (defined in nc_csr.cu / nc_vec.cu) ---------------
+
+enum VecKind : int { VK_F64 = 0, VK_F32 = 1 };
+
+// y = ca*u + cb*w + cc*r + cd*(A u) for a CSR matrix with value type vdt
+// (nc_dtype) and vector type given by the pointers' kinds: x_f32 selects
+// float u/w/r; y_f64 selects a float64 output.  dot: 0 none, 1 (rdot, y),
+// 2 (u, y); the reduction finishes with R.  Coefficients equal to zero skip
+// their loads.  Kernels return at once when *done != 0 (done may be null).
+cudaError_t launch_csr_step(int n, const int32_t* rowptr, const int32_t* col, const void* val,
+                            int vdt, bool x_f32, bool y_f64, const void* u, const void* w,
+                            const void* r, void* y, double ca, double cb, double cc, double cd,
+                            int dot, const double* rdot, const Reduce& R, const int* done,
+                            cudaStream_t st);
+
+cudaError_t launch_csr_diag(int n, const int32_t* rowptr, const int32_t* col, const double* val,
+                            double* dis, int* bad, cudaStream_t st);
+cudaError_t launch_csr_scale(int n, const int32_t* rowptr, const int32_t* col, const double* val,
+                             const double* dis, double* out, cudaStream_t st);
+cudaError_t launch_csr_gershgorin(int n, const int32_t* rowptr, const double* val,
+                                  unsigned long long* out_bits, cudaStream_t st);
+cudaError_t launch_convert(int64_t count, const double* in, int out_dt, void* out, cudaStream_t st);
+
+int vec_grid(int64_t n);
+
+// x += alpha p; r -= alpha q; r32 = (float) r (if r32); (r, r) -> FIN_RR
+cudaError_t launch_axpy2_rr(int n, double* x, double* r, const double* p, const double* q,
+                            float* r32, const Reduce& R, cudaStream_t st);
+// p = z + beta p; then (if use_cond) set the loop condition to !done
+cudaError_t launch_p_update(int n, double* p, const double* z, PcgScalars* S,
+                            cudaGraphConditionalHandle h, int use_cond, cudaStream_t st);
+// z = c r and (r, z) (degree-0 preconditioner); skip if *done
+cudaError_t launch_scale_dot(int n, const double* r, double c, double* z, const Reduce& R,
+                             const int* done, cudaStream_t st);
+// (a, b) -> R (skip if *done when done != null)
+cudaError_t launch_dot(int n, const double* a, const double* b, const Reduce& R, const int* done,
+                       cudaStream_t st);
+// y = x (skip if *done)
+cudaError_t launch_copy(int n, const double* x, double* y, const int* done, cudaStream_t st);
+// b_s = dis .* b (or b); x_s = 0 if zero else x ./ dis (or x)
+cudaError_t launch_copy_in(int n, const double* b, const double* x, const double* dis, int zero,
+                           double* bs, double* xs, cudaStream_t st);
+// x = dis .* x_s (or x_s); x = 0 when S->bb == 0
+cudaError_t launch_copy_out(int n, const double* xs, const double* dis, const PcgScalars* S,
+                            double* x, cudaStream_t st);
+// y = y + a x and (y, y) -> R
+cudaError_t launch_axpy_dot(int n, double a, const double* x, double* y, const Reduce& R,
+                            cudaStream_t st);
+// y = x / d
+cudaError_t launch_div(int n, const double* x, double d, double* y, cudaStream_t st);
+
+}  // namespace nc

@@ -1,0 +1,64 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+entry point that include/*.h declares (no compute calls here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        for m in re.finditer(r"^NC_API\s+[\w\s\*]+?\b(\w+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2008_01440_gb300.build import build
+    return build()
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for required in ("pcg_setup", "pcg_solve", "pcg_apply_poly", "nc_matrix_csr", "nc_bounds_lanczos"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_entry_points(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.nc_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.nc_version()
+    lib.nc_strerror.restype = ctypes.c_char_p
+    assert lib.nc_strerror(0) == b"ok"
+    # argument validation happens before any CUDA call
+    h = ctypes.c_void_p()
+    assert lib.nc_matrix_csr(ctypes.c_int64(-1), ctypes.c_int64(0), None, None, None, ctypes.byref(h)) == 1
+    assert lib.nc_matrix_csr(ctypes.c_int64(0), ctypes.c_int64(0), None, None, None, ctypes.byref(h)) == 0
+    assert lib.nc_matrix_destroy(h) == 0
+    assert lib.pcg_setup(None, ctypes.c_double(1.0), ctypes.c_double(2.0), 3, ctypes.c_double(1.0), None, None,
+                         ctypes.byref(h)) == 1
+
+
+def test_binding_imports_and_matches_header(libpath):
+    import paper_2008_01440_gb300 as nc
+    from paper_2008_01440_gb300 import binding
+    assert set(binding._SIGS) == set(declared_symbols())
+    assert nc.nc_version().startswith("ncpcg")
+
+
+def test_built_only_for_sm103a():
+    from paper_2008_01440_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
