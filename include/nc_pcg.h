@@ -49,7 +49,8 @@ typedef enum {
     NC_ERR_INDEFINITE = 4,   /* (p,Ap) <= 0 or (r,z) <= 0: A or P_k(A) not SPD       */
     NC_ERR_MAXIT = 5,        /* maxit reached before ||r|| <= tol ||b||               */
     NC_ERR_BREAKDOWN = 6,    /* NaN or Inf in a reduction                             */
-    NC_ERR_UNSUPPORTED = 7   /* option combination not implemented for this format    */
+    NC_ERR_UNSUPPORTED = 7,  /* option combination not implemented for this format    */
+    NC_ERR_SCRATCH_LIMIT = 8 /* n above the fixed scratch of nc_apply_poly_csr_noalloc */
 } nc_status;
 
 /* Value type of the matrix inside P_k(A) (the outer CG stays float64). */
@@ -167,6 +168,33 @@ NC_API nc_status pcg_solve_host(nc_solver S, const double* b_host, double* x_hos
                          int maxit, void* stream, nc_result* res);
 
 NC_API nc_status pcg_destroy(nc_solver S);
+
+/* ---- No-allocation apply ---------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory when they apply the preconditioner
+ * (a solver that draws all device memory from its own fixed arena, a
+ * real-time loop where cudaMalloc/cudaFree and the synchronisation they can
+ * imply are not allowed, a plugin inside a framework that owns the device
+ * heap).  It computes the same z_dev = P_k(A) v_dev as pcg_apply_poly for a
+ * CSR matrix with float64 values (arguments as in nc_matrix_csr and
+ * pcg_setup), but builds no handle and calls no allocator: the float64
+ * recurrence keeps two of its three work vectors in one fixed device array
+ * of 2 x nc_apply_poly_noalloc_max_n() doubles (16 MiB) that every device
+ * loading the library holds until the process exits, and uses z_dev as the
+ * third.  n above nc_apply_poly_noalloc_max_n() (2^20) is rejected with
+ * NC_ERR_SCRATCH_LIMIT before any work.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (several streams or host threads
+ * on one device) race and must be serialised by the caller.  Nothing in the
+ * array needs to start at zero (every slot is written before it is read).
+ * v_dev and z_dev: n float64, distinct; work is enqueued on `stream`. */
+NC_API nc_status nc_apply_poly_csr_noalloc(int64_t n, const int32_t* rowptr_dev, const int32_t* col_dev,
+                                           const double* val_dev, double lambda_min, double lambda_max,
+                                           int degree_k, double theta_scale, const double* v_dev,
+                                           double* z_dev, void* stream);
+/* Largest n accepted by nc_apply_poly_csr_noalloc. */
+NC_API int64_t nc_apply_poly_noalloc_max_n(void);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,7 @@ from .binding import (  # noqa: F401
     NC_ERR_INDEFINITE,
     NC_ERR_MAXIT,
     NC_ERR_OOM,
+    NC_ERR_SCRATCH_LIMIT,
     NC_ERR_UNSUPPORTED,
     NC_F32,
     NC_F64,
@@ -31,6 +32,8 @@ from .binding import (  # noqa: F401
     Solver,
     lib,
     make_options,
+    nc_apply_poly_csr_noalloc,
+    nc_apply_poly_noalloc_max_n,
     nc_bounds_lanczos,
     nc_gershgorin,
     nc_matrix_csr,

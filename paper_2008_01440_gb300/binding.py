@@ -22,7 +22,7 @@ if not os.path.exists(LIB_PATH):
 lib = ctypes.CDLL(LIB_PATH)
 
 NC_OK, NC_ERR_ARG, NC_ERR_CUDA, NC_ERR_OOM, NC_ERR_INDEFINITE, NC_ERR_MAXIT, NC_ERR_BREAKDOWN, \
-    NC_ERR_UNSUPPORTED = range(8)
+    NC_ERR_UNSUPPORTED, NC_ERR_SCRATCH_LIMIT = range(9)
 NC_F64, NC_F32, NC_BF16 = 0, 1, 2
 _DTYPES = {"f64": NC_F64, "f32": NC_F32, "bf16": NC_BF16}
 # statuses a solve may end with while still returning a meaningful iterate
@@ -64,6 +64,9 @@ _SIGS = {
     "pcg_solve": (ctypes.c_int, [_vp, _vp, _vp, _dbl, ctypes.c_int, _vp, ctypes.POINTER(nc_result)]),
     "pcg_solve_host": (ctypes.c_int, [_vp, _vp, _vp, _dbl, ctypes.c_int, _vp, ctypes.POINTER(nc_result)]),
     "pcg_destroy": (ctypes.c_int, [_vp]),
+    "nc_apply_poly_csr_noalloc": (ctypes.c_int, [_i64, _vp, _vp, _vp, _dbl, _dbl, ctypes.c_int, _dbl, _vp, _vp,
+                                                 _vp]),
+    "nc_apply_poly_noalloc_max_n": (_i64, []),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -247,6 +250,24 @@ def pcg_solve_host(S: Solver, b, x, tol: float, maxit: int, stream=None) -> dict
     if st not in SOLVE_STATUSES:
         _check(st, "pcg_solve_host")
     return res.as_dict()
+
+
+def nc_apply_poly_noalloc_max_n() -> int:
+    return int(lib.nc_apply_poly_noalloc_max_n())
+
+
+def nc_apply_poly_csr_noalloc(rowptr, col, val, lambda_min: float, lambda_max: float, degree_k: int,
+                              theta_scale: float, v, z, stream=None):
+    """z = P_k(A) v without any device allocation by the library (for callers
+    that cannot allocate; see include/nc_pcg.h).  Same arguments as
+    nc_matrix_csr + pcg_setup + pcg_apply_poly in one call."""
+    import torch
+    n = rowptr.numel() - 1
+    _check(lib.nc_apply_poly_csr_noalloc(n, _ptr(rowptr, torch.int32, what="rowptr"),
+                                         _ptr(col, torch.int32, what="col"), _ptr(val, torch.float64, what="val"),
+                                         float(lambda_min), float(lambda_max), int(degree_k), float(theta_scale),
+                                         _ptr(v, torch.float64, n, "v"), _ptr(z, torch.float64, n, "z"),
+                                         _stream(stream)), "nc_apply_poly_csr_noalloc")
 
 
 def pcg_destroy(S: Solver):

@@ -377,6 +377,7 @@ const char* nc_strerror(nc_status s) {
     case NC_ERR_MAXIT: return "maximum iterations reached";
     case NC_ERR_BREAKDOWN: return "NaN or Inf in a reduction";
     case NC_ERR_UNSUPPORTED: return "unsupported option for this matrix format";
+    case NC_ERR_SCRATCH_LIMIT: return "n exceeds the fixed scratch array of the no-allocation apply";
     }
     return "unknown status";
 }
