@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-modes", action="store_true", help="skip the other apply precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--oracle-iters", type=int, default=6, help="PCG iterations per oracle sample")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the PCG loop from the host instead of the device-side graph "
+                         "(same kernels; lets a profiler list every launch)")
     return ap.parse_args()
 
 
@@ -161,11 +164,32 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    def time_step_kernel(S, mode):
+        """Average duration of one fused-step launch: CUDA events around
+        `reps` applications of P_k (k launches each) on the launching stream."""
+        z = torch.empty(n, dtype=torch.float64, device=dev)
+        reps = 10
+        for _ in range(2):
+            nc.pcg_apply_poly(S, bs[0], z)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            nc.pcg_apply_poly(S, bs[0], z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_launch_s = e0.elapsed_time(e1) / 1e3 / (reps * max(args.k, 1))
+        sv = {"f64": 8, "f32": 4, "bf16": 2}[mode]
+        sx = 8 if mode == "f64" else 4
+        nbytes = algorithmic_step_bytes(n, nnz, sv, sx)
+        return per_launch_s, nbytes
+
     modes = [args.apply] + ([] if args.no_modes else [m for m in ("f64", "f32", "bf16") if m != args.apply])
     out_modes = {}
     main = None
     for mode in modes:
-        S = nc.pcg_setup(M, lo, hi, args.k, S_THETA, apply_dtype=mode, x0_is_zero=True)
+        S = nc.pcg_setup(M, lo, hi, args.k, S_THETA, apply_dtype=mode, x0_is_zero=True,
+                         use_graph=not args.host_loop)
         barrier()
         clk = None
         if mode == args.apply:
@@ -188,6 +212,9 @@ def run_ours(args, rank, world, local_rank):
                "iters": iters[0], "iters_range": [min(iters), max(iters)], "all_converged": ok,
                "max_relres": max(r["relres"] for r in results),
                "max_true_relres": max(r["true_relres"] for r in results)}
+        t_launch, nbytes = time_step_kernel(S, mode)
+        rec["step_us"] = round(t_launch * 1e6, 2)
+        rec["step_GBps"] = round(nbytes / t_launch / 1e9, 1)
         out_modes[mode] = rec
         if mode == args.apply:
             main = dict(rec=rec, S=S, clocks=clocks, results=results)
@@ -196,23 +223,9 @@ def run_ours(args, rank, world, local_rank):
 
     S = main["S"]
     rec = main["rec"]
-    # --- kernel timing: the fused step kernel, k launches per apply ---------------------
-    z = torch.empty(n, dtype=torch.float64, device=dev)
-    reps = 10
-    for _ in range(2):
-        nc.pcg_apply_poly(S, bs[0], z)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        nc.pcg_apply_poly(S, bs[0], z)
-    e1.record(stream)
-    torch.cuda.synchronize()
     k = max(args.k, 1)
-    per_launch_s = e0.elapsed_time(e1) / 1e3 / (reps * k)
-    sv = {"f64": 8, "f32": 4, "bf16": 2}[args.apply]
-    sx = 8 if args.apply == "f64" else 4
-    step_bytes = algorithmic_step_bytes(n, nnz, sv, sx)
+    # --- kernel timing: the fused step kernel, k launches per apply ---------------------
+    per_launch_s, step_bytes = time_step_kernel(S, args.apply)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:

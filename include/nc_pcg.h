@@ -56,6 +56,12 @@ typedef enum {
 /* Value type of the matrix inside P_k(A) (the outer CG stays float64). */
 typedef enum { NC_F64 = 0, NC_F32 = 1, NC_BF16 = 2 } nc_dtype;
 
+/* Layout the solver's product kernels read (built once by pcg_setup).
+ * SELL: slices of 32 rows stored slot-major, rows padded to the slice's
+ * longest row (coalesced thread-per-row access); AUTO picks SELL when the
+ * padding is at most 1.5x the nonzeros, else CSR. */
+typedef enum { NC_FORMAT_AUTO = 0, NC_FORMAT_CSR = 1, NC_FORMAT_SELL = 2 } nc_format;
+
 typedef struct {
     int apply_dtype;   /* nc_dtype: F64 = plain method; F32: float32 matrix and
                           vectors inside P_k; BF16: bfloat16 matrix values,
@@ -67,7 +73,18 @@ typedef struct {
     int use_graph;     /* 1 (default): one CUDA graph per solve with the
                           stopping test evaluated on the device; 0: host loop
                           reading the residual every iteration.                 */
+    int spmv_format;   /* nc_format of the solver's product kernels (AUTO).    */
 } nc_options;
+
+typedef struct {
+    int64_t n;
+    int32_t degree_k;
+    int32_t spmv_format;  /* NC_FORMAT_CSR or NC_FORMAT_SELL (after AUTO)      */
+    int32_t apply_dtype;
+    int32_t pad0;
+    double padding;       /* stored entries / nonzeros of the chosen layout    */
+    double theta, delta, sigma;   /* theta' = s(a+b)/2, delta, sigma (Sec. 3/4) */
+} nc_solver_info;
 
 typedef struct {
     int32_t iters;        /* PCG iterations                                      */
@@ -79,7 +96,7 @@ typedef struct {
 } nc_result;
 
 /* Fill `opt` with the defaults: F64, no residual replacement, x0 from x,
- * graph on. */
+ * graph on, AUTO layout. */
 NC_API void nc_options_default(nc_options* opt);
 NC_API const char* nc_strerror(nc_status s);
 NC_API const char* nc_version(void);
@@ -166,6 +183,9 @@ NC_API nc_status pcg_solve(nc_solver S, const double* b_dev, double* x_dev, doub
  * asynchronous copies; pageable memory works too. */
 NC_API nc_status pcg_solve_host(nc_solver S, const double* b_host, double* x_host, double tol,
                          int maxit, void* stream, nc_result* res);
+
+/* Layout and parameters the solver chose. */
+NC_API nc_status pcg_get_info(nc_solver S, nc_solver_info* info);
 
 NC_API nc_status pcg_destroy(nc_solver S);
 

@@ -43,6 +43,7 @@ from .binding import (  # noqa: F401
     nc_version,
     pcg_apply_poly,
     pcg_destroy,
+    pcg_get_info,
     pcg_setup,
     pcg_solve,
     pcg_solve_host,

@@ -29,9 +29,19 @@ _DTYPES = {"f64": NC_F64, "f32": NC_F32, "bf16": NC_BF16}
 SOLVE_STATUSES = (NC_OK, NC_ERR_MAXIT, NC_ERR_INDEFINITE, NC_ERR_BREAKDOWN)
 
 
+NC_FORMAT_AUTO, NC_FORMAT_CSR, NC_FORMAT_SELL = 0, 1, 2
+_FORMATS = {"auto": NC_FORMAT_AUTO, "csr": NC_FORMAT_CSR, "sell": NC_FORMAT_SELL}
+
+
 class nc_options(ctypes.Structure):
     _fields_ = [("apply_dtype", ctypes.c_int), ("rr_period", ctypes.c_int),
-                ("x0_is_zero", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("x0_is_zero", ctypes.c_int), ("use_graph", ctypes.c_int), ("spmv_format", ctypes.c_int)]
+
+
+class nc_solver_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("degree_k", ctypes.c_int32), ("spmv_format", ctypes.c_int32),
+                ("apply_dtype", ctypes.c_int32), ("pad0", ctypes.c_int32), ("padding", ctypes.c_double),
+                ("theta", ctypes.c_double), ("delta", ctypes.c_double), ("sigma", ctypes.c_double)]
 
 
 class nc_result(ctypes.Structure):
@@ -64,6 +74,7 @@ _SIGS = {
     "pcg_solve": (ctypes.c_int, [_vp, _vp, _vp, _dbl, ctypes.c_int, _vp, ctypes.POINTER(nc_result)]),
     "pcg_solve_host": (ctypes.c_int, [_vp, _vp, _vp, _dbl, ctypes.c_int, _vp, ctypes.POINTER(nc_result)]),
     "pcg_destroy": (ctypes.c_int, [_vp]),
+    "pcg_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(nc_solver_info)]),
     "nc_apply_poly_csr_noalloc": (ctypes.c_int, [_i64, _vp, _vp, _vp, _dbl, _dbl, ctypes.c_int, _dbl, _vp, _vp,
                                                  _vp]),
     "nc_apply_poly_noalloc_max_n": (_i64, []),
@@ -192,9 +203,10 @@ def nc_bounds_lanczos(A: Matrix, steps: int, v0, stream=None):
     return lo.value, hi.value, rmin.value, rmax.value
 
 
-def make_options(apply_dtype="f64", rr_period=0, x0_is_zero=False, use_graph=True) -> nc_options:
+def make_options(apply_dtype="f64", rr_period=0, x0_is_zero=False, use_graph=True, spmv_format="auto") -> nc_options:
     o = nc_options()
     lib.nc_options_default(ctypes.byref(o))
+    o.spmv_format = _FORMATS[spmv_format] if isinstance(spmv_format, str) else int(spmv_format)
     o.apply_dtype = _DTYPES[apply_dtype] if isinstance(apply_dtype, str) else int(apply_dtype)
     o.rr_period = int(rr_period)
     o.x0_is_zero = int(bool(x0_is_zero))
@@ -209,6 +221,15 @@ def pcg_setup(A: Matrix, lambda_min: float, lambda_max: float, degree_k: int, th
     _check(lib.pcg_setup(A.handle, float(lambda_min), float(lambda_max), int(degree_k), float(theta_scale),
                          ctypes.byref(opt), _stream(stream), ctypes.byref(h)), "pcg_setup")
     return Solver(h.value, A.n, A, int(degree_k))
+
+
+def pcg_get_info(S: Solver) -> dict:
+    info = nc_solver_info()
+    _check(lib.pcg_get_info(S.handle, ctypes.byref(info)), "pcg_get_info")
+    d = {f: getattr(info, f) for f, _ in info._fields_}
+    d.pop("pad0")
+    d["spmv_format"] = {NC_FORMAT_CSR: "csr", NC_FORMAT_SELL: "sell"}.get(d["spmv_format"], d["spmv_format"])
+    return d
 
 
 def pcg_apply_poly(S: Solver, v, z, stream=None):

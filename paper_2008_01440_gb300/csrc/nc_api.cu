@@ -31,6 +31,18 @@ struct nc_matrix_s {
     double* dis = nullptr;          // d^{-1/2} of the scaling, owned
 };
 
+// A matrix as the step kernels see it: CSR (the handle's arrays) or the
+// solver-owned SELL-32 layout, with float64 or low-precision values.
+enum OpKind : int { OP_CSR = 0, OP_SELL = 1 };
+struct OpView {
+    int kind = OP_CSR;
+    int n = 0;
+    const int32_t* ptr = nullptr;   // row pointers (CSR) or slice pointers (SELL)
+    const int32_t* col = nullptr;
+    const void* val = nullptr;
+    int vdt = NC_F64;
+};
+
 struct nc_solver_s {
     nc_matrix A = nullptr;
     int64_t n = 0;
@@ -41,8 +53,14 @@ struct nc_solver_s {
     std::vector<double> ca, cb, cc, cd;   // per Chebyshev step 1..k (index 0 unused)
     bool mixed = false;
     int vdt = NC_F64;
-    const void* pval = nullptr;           // matrix values inside P_k
-    void* lval = nullptr;                 // converted copy (F32/BF16), owned
+    OpView op64;                          // float64 operator (outer CG, true residual)
+    OpView opP;                           // operator inside P_k (apply precision)
+    double padding = 1.0;                 // SELL stored entries / nnz
+    void* lval = nullptr;                 // converted CSR values (F32/BF16), owned
+    int32_t* sell_ptr = nullptr;          // SELL-32 arrays, owned
+    int32_t* sell_col = nullptr;
+    double* sell_val64 = nullptr;
+    void* sell_valP = nullptr;
     double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     void* buf[3] = {nullptr, nullptr, nullptr};
     float* r32 = nullptr;
@@ -122,6 +140,16 @@ cudaError_t op_step_f64(nc_matrix A, const double* u, const double* w, const dou
                         const Reduce& R, const int* done, cudaStream_t st) {
     return launch_csr_step((int)A->n, A->rowptr, A->col, A->val, NC_F64, false, true, u, w, r, y, ca,
                            cb, cc, cd, dot, rdot, R, done, st);
+}
+
+cudaError_t op_step(const OpView& op, bool x_f32, bool y_f64, const void* u, const void* w, const void* r,
+                    void* y, double ca, double cb, double cc, double cd, int dot, const double* rdot,
+                    const Reduce& R, const int* done, cudaStream_t st) {
+    if (op.kind == OP_SELL)
+        return launch_sell_step(op.n, op.ptr, op.col, op.val, op.vdt, x_f32, y_f64, u, w, r, y, ca, cb, cc, cd,
+                                dot, rdot, R, done, st);
+    return launch_csr_step(op.n, op.ptr, op.col, op.val, op.vdt, x_f32, y_f64, u, w, r, y, ca, cb, cc, cd, dot,
+                           rdot, R, done, st);
 }
 
 // Cyclic Jacobi eigen-decomposition of a small symmetric matrix (row-major),
@@ -207,16 +235,14 @@ cudaError_t enqueue_poly(nc_solver S, const double* r64, double* z, int fin, con
     const Reduce R = make_reduce(S->partials, S->counter, S->S, nullptr, fin);
     if (S->k == 0) return launch_scale_dot(n, r64, 1.0 / S->theta, z, R, done, st);
     const void* rx = S->mixed ? static_cast<const void*>(S->r32) : static_cast<const void*>(r64);
-    nc_matrix A = S->A;
     for (int j = 1; j <= S->k; ++j) {
         const void* u = (j == 1) ? rx : S->buf[(j - 1) % 3];
         const void* w = (j >= 3) ? S->buf[(j - 2) % 3] : nullptr;
         const bool last = (j == S->k);
         void* y = last ? static_cast<void*>(z) : S->buf[j % 3];
         const int dot = (last && fin != FIN_NONE) ? 1 : 0;
-        cudaError_t e = launch_csr_step(n, A->rowptr, A->col, S->pval, S->vdt, S->mixed,
-                                        last || !S->mixed, u, w, rx, y, S->ca[j], S->cb[j], S->cc[j],
-                                        S->cd[j], dot, r64, R, done, st);
+        cudaError_t e = op_step(S->opP, S->mixed, last || !S->mixed, u, w, rx, y, S->ca[j], S->cb[j], S->cc[j],
+                                S->cd[j], dot, r64, R, done, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -232,7 +258,7 @@ cudaError_t enqueue_prologue(nc_solver S, cudaStream_t st) {
         e = launch_copy(n, S->b, S->r, nullptr, st);
     } else {
         const Reduce none = make_reduce(S->partials, S->counter, S->S, nullptr, FIN_NONE);
-        e = op_step_f64(S->A, S->x, nullptr, S->b, S->r, 0.0, 0.0, 1.0, -1.0, 0, nullptr, none, nullptr, st);
+        e = op_step(S->op64, false, true, S->x, nullptr, S->b, S->r, 0.0, 0.0, 1.0, -1.0, 0, nullptr, none, nullptr, st);
     }
     if (e) return e;
     if (S->mixed) {
@@ -250,8 +276,8 @@ cudaError_t enqueue_body(nc_solver S, cudaGraphConditionalHandle h, int use_cond
     const int n = (int)S->n;
     const int* done = &S->S->done;
     cudaError_t e;
-    e = op_step_f64(S->A, S->p, nullptr, nullptr, S->q, 0.0, 0.0, 0.0, 1.0, 2, nullptr,
-                    make_reduce(S->partials, S->counter, S->S, nullptr, FIN_ALPHA), done, st);
+    e = op_step(S->op64, false, true, S->p, nullptr, nullptr, S->q, 0.0, 0.0, 0.0, 1.0, 2, nullptr,
+                make_reduce(S->partials, S->counter, S->S, nullptr, FIN_ALPHA), done, st);
     if (e) return e;
     e = launch_axpy2_rr(n, S->x, S->r, S->p, S->q, S->mixed ? S->r32 : nullptr,
                         make_reduce(S->partials, S->counter, S->S, nullptr, FIN_RR), st);
@@ -336,7 +362,8 @@ nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
     }
     // true residual of the (scaled) system at exit
     const Reduce none = make_reduce(S->partials, S->counter, S->S, nullptr, FIN_NONE);
-    NC_CU(op_step_f64(S->A, S->x, nullptr, S->b, S->q, 0.0, 0.0, 1.0, -1.0, 0, nullptr, none, nullptr, st));
+    NC_CU(op_step(S->op64, false, true, S->x, nullptr, S->b, S->q, 0.0, 0.0, 1.0, -1.0, 0, nullptr, none, nullptr,
+                  st));
     NC_CU(launch_dot(n, S->q, S->q, make_reduce(S->partials, S->counter, S->S, nullptr, FIN_TRUE), nullptr, st));
     NC_CU(launch_copy_out(n, S->x, S->A->dis, S->S, x_dev, st));
     NC_CU(cudaMemcpyAsync(S->h_io, S->S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
@@ -354,6 +381,78 @@ nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
     return (nc_status)o.status;
 }
 
+// Choose and build the layout the step kernels read.  SELL-32 when its
+// padding is at most kSellMaxPadding (or when forced), else the CSR arrays.
+constexpr double kSellMaxPadding = 1.5;
+
+nc_status setup_operator(nc_solver S, cudaStream_t st) {
+    nc_matrix A = S->A;
+    const int n = (int)S->n;
+    const size_t eb = S->vdt == NC_F64 ? 8 : (S->vdt == NC_F32 ? 4 : 2);
+    bool sell = S->opt.spmv_format != NC_FORMAT_CSR && n > 0;
+    std::vector<int64_t> hptr;
+    if (sell) {
+        const int nslices = (n + 31) / 32;
+        int32_t* dlen = nullptr;
+        NC_TRY(dev_alloc_n(&dlen, nslices));
+        std::vector<int32_t> hlen(nslices);
+        cudaError_t e;
+        if ((e = launch_sell_lengths(n, A->rowptr, dlen, st)) ||
+            (e = cudaMemcpyAsync(hlen.data(), dlen, sizeof(int32_t) * nslices, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st))) {
+            dev_free(dlen);
+            g_last_cuda = e;
+            return NC_ERR_CUDA;
+        }
+        dev_free(dlen);
+        hptr.resize(nslices + 1);
+        hptr[0] = 0;
+        for (int i = 0; i < nslices; ++i) hptr[i + 1] = hptr[i] + 32 * (int64_t)hlen[i];
+        const int64_t total = hptr[nslices];
+        S->padding = A->nnz > 0 ? (double)total / (double)A->nnz : 1.0;
+        if (total >= ((int64_t)1 << 31)) sell = false;
+        if (S->opt.spmv_format == NC_FORMAT_AUTO && S->padding > kSellMaxPadding) sell = false;
+    }
+    if (!sell) {
+        S->padding = 1.0;
+        S->op64 = OpView{OP_CSR, n, A->rowptr, A->col, A->val, NC_F64};
+        S->opP = S->op64;
+        if (S->mixed) {
+            NC_TRY(dev_alloc(&S->lval, eb * (size_t)(A->nnz > 0 ? A->nnz : 1)));
+            cudaError_t e = launch_convert(A->nnz, A->val, S->vdt, S->lval, st);
+            if (e) { g_last_cuda = e; return NC_ERR_CUDA; }
+            S->opP = OpView{OP_CSR, n, A->rowptr, A->col, S->lval, S->vdt};
+        }
+        return NC_OK;
+    }
+    const int nslices = (n + 31) / 32;
+    const int64_t total = hptr[nslices];
+    std::vector<int32_t> hp32(nslices + 1);
+    for (int i = 0; i <= nslices; ++i) hp32[i] = (int32_t)hptr[i];
+    NC_TRY(dev_alloc_n(&S->sell_ptr, nslices + 1));
+    NC_TRY(dev_alloc_n(&S->sell_col, total));
+    NC_TRY(dev_alloc_n(&S->sell_val64, total));
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(S->sell_ptr, hp32.data(), sizeof(int32_t) * (nslices + 1), cudaMemcpyHostToDevice, st)) ||
+        (e = launch_sell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, NC_F64, S->sell_col, S->sell_val64, st))) {
+        g_last_cuda = e;
+        return NC_ERR_CUDA;
+    }
+    S->op64 = OpView{OP_SELL, n, S->sell_ptr, S->sell_col, S->sell_val64, NC_F64};
+    S->opP = S->op64;
+    if (S->mixed) {
+        NC_TRY(dev_alloc(&S->sell_valP, eb * (size_t)total));
+        if ((e = launch_sell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, S->vdt, S->sell_col, S->sell_valP, st))) {
+            g_last_cuda = e;
+            return NC_ERR_CUDA;
+        }
+        S->opP = OpView{OP_SELL, n, S->sell_ptr, S->sell_col, S->sell_valP, S->vdt};
+    }
+    // the host vector hp32 must outlive the copy
+    if ((e = cudaStreamSynchronize(st))) { g_last_cuda = e; return NC_ERR_CUDA; }
+    return NC_OK;
+}
+
 }  // namespace
 
 // =============================================================================
@@ -365,6 +464,7 @@ void nc_options_default(nc_options* opt) {
     opt->rr_period = 0;
     opt->x0_is_zero = 0;
     opt->use_graph = 1;
+    opt->spmv_format = NC_FORMAT_AUTO;
 }
 
 const char* nc_strerror(nc_status s) {
@@ -578,6 +678,7 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
     if (opt) o = *opt;
     if (o.apply_dtype != NC_F64 && o.apply_dtype != NC_F32 && o.apply_dtype != NC_BF16) return NC_ERR_ARG;
     if (o.rr_period < 0) return NC_ERR_ARG;
+    if (o.spmv_format < NC_FORMAT_AUTO || o.spmv_format > NC_FORMAT_SELL) return NC_ERR_ARG;
     if (o.rr_period > 0) return NC_ERR_UNSUPPORTED;
     cudaStream_t st = as_stream(stream);
     nc_solver S = new (std::nothrow) nc_solver_s();
@@ -603,16 +704,8 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
         const size_t vb = S->mixed ? sizeof(float) : sizeof(double);
         for (int i = 0; i < 3 && s == NC_OK; ++i) s = dev_alloc(&S->buf[i], vb * (size_t)(n > 0 ? n : 1));
         if (s) break;
-        if (S->mixed) {
-            if ((s = dev_alloc_n(&S->r32, n))) break;
-            const size_t eb = S->vdt == NC_F32 ? 4 : 2;
-            if ((s = dev_alloc(&S->lval, eb * (size_t)(A->nnz > 0 ? A->nnz : 1)))) break;
-            cudaError_t e = launch_convert(A->nnz, A->val, S->vdt, S->lval, st);
-            if (e) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
-            S->pval = S->lval;
-        } else {
-            S->pval = A->val;
-        }
+        if (S->mixed && (s = dev_alloc_n(&S->r32, n))) break;
+        if ((s = setup_operator(S, st)) != NC_OK) break;
         cudaError_t e;
         if ((e = cudaMemsetAsync(S->counter, 0, sizeof(unsigned int), st)) ||
             (e = cudaMemsetAsync(S->S, 0, sizeof(PcgScalars), st))) {
@@ -671,6 +764,19 @@ nc_status pcg_solve_host(nc_solver S, const double* b_host, double* x_host, doub
     return s;
 }
 
+nc_status pcg_get_info(nc_solver S, nc_solver_info* info) {
+    if (!S || !info) return NC_ERR_ARG;
+    info->n = S->n;
+    info->degree_k = S->k;
+    info->spmv_format = S->op64.kind == OP_SELL ? NC_FORMAT_SELL : NC_FORMAT_CSR;
+    info->apply_dtype = S->vdt;
+    info->padding = S->padding;
+    info->theta = S->theta;
+    info->delta = S->delta;
+    info->sigma = S->sigma;
+    return NC_OK;
+}
+
 nc_status pcg_destroy(nc_solver S) {
     if (!S) return NC_ERR_ARG;
     if (S->exec) cudaGraphExecDestroy(S->exec);
@@ -678,6 +784,7 @@ nc_status pcg_destroy(nc_solver S) {
     dev_free(S->b); dev_free(S->x); dev_free(S->r); dev_free(S->z); dev_free(S->p); dev_free(S->q);
     for (int i = 0; i < 3; ++i) dev_free(S->buf[i]);
     dev_free(S->r32); dev_free(S->lval); dev_free(S->partials); dev_free(S->counter); dev_free(S->S);
+    dev_free(S->sell_ptr); dev_free(S->sell_col); dev_free(S->sell_val64); dev_free(S->sell_valP);
     if (S->h_io) cudaFreeHost(S->h_io);
     delete S;
     return NC_OK;

@@ -158,6 +158,16 @@ cudaError_t launch_csr_step(int n, const int32_t* rowptr, const int32_t* col, co
                             int dot, const double* rdot, const Reduce& R, const int* done,
                             cudaStream_t st);
 
+// Same step for the SELL-32 layout (slice_ptr: nslices+1 int32 offsets).
+cudaError_t launch_sell_step(int n, const int32_t* slice_ptr, const int32_t* col, const void* val, int vdt,
+                             bool x_f32, bool y_f64, const void* u, const void* w, const void* r, void* y,
+                             double ca, double cb, double cc, double cd, int dot, const double* rdot,
+                             const Reduce& R, const int* done, cudaStream_t st);
+// SELL-32 construction from CSR: longest row per slice, then the slot-major fill
+cudaError_t launch_sell_lengths(int n, const int32_t* rowptr, int32_t* slice_len, cudaStream_t st);
+cudaError_t launch_sell_fill(int n, const int32_t* rowptr, const int32_t* col, const double* val,
+                             const int32_t* slice_ptr, int vdt, int32_t* scol, void* sval, cudaStream_t st);
+
 cudaError_t launch_csr_diag(int n, const int32_t* rowptr, const int32_t* col, const double* val,
                             double* dis, int* bad, cudaStream_t st);
 cudaError_t launch_csr_scale(int n, const int32_t* rowptr, const int32_t* col, const double* val,

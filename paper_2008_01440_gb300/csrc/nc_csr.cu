@@ -17,25 +17,17 @@
 // through the read-only cache.  Each row's sum is one fma chain in column
 // order, so a float64 row costs nnz_row + 4 floating-point instructions,
 // the minimum for this operation.
-#include "nc_common.cuh"
+#include "nc_step.cuh"
 
 namespace nc {
 namespace {
-
-template <typename T> struct AccOf { using type = float; };
-template <> struct AccOf<double> { using type = double; };
-
-__device__ __forceinline__ double ld_val(const double* p) { return *p; }
-__device__ __forceinline__ float ld_val(const float* p) { return *p; }
-__device__ __forceinline__ float ld_val(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 
 template <typename VT, typename XT, typename YT, int DOT>
 __global__ void __launch_bounds__(kBlock)
 csr_step_kernel(const int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                 const VT* __restrict__ val, const XT* __restrict__ u, const XT* __restrict__ w,
-                const XT* __restrict__ r, YT* __restrict__ y, const double ca, const double cb,
-                const double cc, const double cd, const double* __restrict__ rdot, const Reduce R,
-                const int* __restrict__ done) {
+                const XT* __restrict__ r, YT* __restrict__ y, const StepCoef<typename AccOf<XT>::type> c,
+                const double* __restrict__ rdot, const Reduce R, const int* __restrict__ done) {
     using AT = typename AccOf<XT>::type;
     if (done != nullptr && *done) return;
     __shared__ VT s_val[kChunk];
@@ -64,16 +56,7 @@ csr_step_kernel(const int n, const int32_t* __restrict__ rowptr, const int32_t* 
         __syncthreads();
     }
     double dv = 0.0;
-    if (row < n) {
-        AT o = (AT)cd * acc;
-        if (cc != 0.0) o = fma((AT)cc, (AT)r[row], o);
-        if (cb != 0.0) o = fma((AT)cb, (AT)w[row], o);
-        if (ca != 0.0) o = fma((AT)ca, (AT)u[row], o);
-        const YT yo = (YT)o;
-        y[row] = yo;
-        if (DOT == 1) dv = rdot[row] * (double)yo;
-        if (DOT == 2) dv = (double)u[row] * (double)yo;
-    }
+    if (row < n) dv = step_row_out<XT, YT, DOT, AT>(row, acc, c, u, w, r, y, rdot);
     if (DOT != 0) grid_reduce<kBlock>(dv, R);
 }
 
@@ -88,18 +71,19 @@ cudaError_t step_dispatch(int n, const int32_t* rowptr, const int32_t* col, cons
     const XT* ww = static_cast<const XT*>(w);
     const XT* rr = static_cast<const XT*>(r);
     YT* yy = static_cast<YT*>(y);
+    const StepCoef<typename AccOf<XT>::type> c = make_coef<typename AccOf<XT>::type>(ca, cb, cc, cd);
     switch (dot) {
     case 0:
-        csr_step_kernel<VT, XT, YT, 0><<<grid, kBlock, 0, st>>>(n, rowptr, col, v, uu, ww, rr, yy, ca,
-                                                                cb, cc, cd, rdot, R, done);
+        csr_step_kernel<VT, XT, YT, 0><<<grid, kBlock, 0, st>>>(n, rowptr, col, v, uu, ww, rr, yy, c,
+                                                                rdot, R, done);
         break;
     case 1:
-        csr_step_kernel<VT, XT, YT, 1><<<grid, kBlock, 0, st>>>(n, rowptr, col, v, uu, ww, rr, yy, ca,
-                                                                cb, cc, cd, rdot, R, done);
+        csr_step_kernel<VT, XT, YT, 1><<<grid, kBlock, 0, st>>>(n, rowptr, col, v, uu, ww, rr, yy, c,
+                                                                rdot, R, done);
         break;
     default:
-        csr_step_kernel<VT, XT, YT, 2><<<grid, kBlock, 0, st>>>(n, rowptr, col, v, uu, ww, rr, yy, ca,
-                                                                cb, cc, cd, rdot, R, done);
+        csr_step_kernel<VT, XT, YT, 2><<<grid, kBlock, 0, st>>>(n, rowptr, col, v, uu, ww, rr, yy, c,
+                                                                rdot, R, done);
         break;
     }
     return cudaGetLastError();
@@ -155,7 +139,7 @@ __global__ void convert_bf16_kernel(int64_t count, const double* __restrict__ in
                                     __nv_bfloat16* __restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = __float2bfloat16_rn((float)in[i]);
+        out[i] = __double2bfloat16(in[i]);
 }
 
 }  // namespace

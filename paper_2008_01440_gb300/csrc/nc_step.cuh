@@ -1,0 +1,65 @@
+// Epilogue shared by the fused step kernels of every matrix format:
+//     y = ca*u + cb*w + cc*r + cd*(A u)   (one Chebyshev step of Algorithm 2)
+// plus an optional dot product finished by the last CTA.
+#pragma once
+
+#include "nc_common.cuh"
+
+namespace nc {
+
+constexpr int kTermU = 1, kTermW = 2, kTermR = 4;
+
+template <typename T> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+__device__ __forceinline__ double ld_val(const double* p) { return *p; }
+__device__ __forceinline__ float ld_val(const float* p) { return *p; }
+__device__ __forceinline__ float ld_val(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// Streaming (evict-first) loads for matrix data that is read exactly once.
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const __nv_bfloat16* p) {
+    const unsigned short b = __ldcs(reinterpret_cast<const unsigned short*>(p));
+    return __uint_as_float(((unsigned int)b) << 16);
+}
+__device__ __forceinline__ int ld_stream(const int32_t* p) { return __ldcs(p); }
+
+// Coefficients of one step in the accumulation type (float coefficients for
+// the float path: a double->float conversion per thread would run on the
+// scarce FP64 pipe).  `terms` says which optional terms are present.
+template <typename AT>
+struct StepCoef {
+    AT ca, cb, cc, cd;
+    int terms;
+};
+
+template <typename AT>
+inline StepCoef<AT> make_coef(double ca, double cb, double cc, double cd) {
+    StepCoef<AT> c;
+    c.ca = (AT)ca;
+    c.cb = (AT)cb;
+    c.cc = (AT)cc;
+    c.cd = (AT)cd;
+    c.terms = (ca != 0.0 ? kTermU : 0) | (cb != 0.0 ? kTermW : 0) | (cc != 0.0 ? kTermR : 0);
+    return c;
+}
+
+// Row epilogue: returns the dot-product contribution of this row.
+template <typename XT, typename YT, int DOT, typename AT>
+__device__ __forceinline__ double step_row_out(int row, AT acc, const StepCoef<AT>& c,
+                                               const XT* __restrict__ u, const XT* __restrict__ w,
+                                               const XT* __restrict__ r, YT* __restrict__ y,
+                                               const double* __restrict__ rdot) {
+    AT o = c.cd * acc;
+    if (c.terms & kTermR) o = fma(c.cc, (AT)r[row], o);
+    if (c.terms & kTermW) o = fma(c.cb, (AT)w[row], o);
+    if (c.terms & kTermU) o = fma(c.ca, (AT)u[row], o);
+    const YT yo = (YT)o;
+    y[row] = yo;
+    if (DOT == 1) return rdot[row] * (double)yo;
+    if (DOT == 2) return (double)u[row] * (double)yo;
+    return 0.0;
+}
+
+}  // namespace nc

@@ -52,12 +52,17 @@ def test_matvec_and_jacobi_parity(env):
     assert g == gershgorin_np(As.rowptr, As.col, As.val, A.n) or abs(g - gershgorin_np(As.rowptr, As.col, As.val, A.n)) < 1e-14
 
 
+FORMATS = ["csr", "sell"]
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
 @pytest.mark.parametrize("k,s", [(0, 1.0), (1, 1.0), (2, 1.001), (3, 1.0), (8, 1.0), (8, 1.001), (31, 1.001)])
-def test_apply_poly_laplacian64(env, k, s):
+def test_apply_poly_laplacian64(env, k, s, fmt):
     torch, nc = env
     A, lo, hi = lap64()
     M = csr_to_gpu(torch, nc, A)
-    S = nc.pcg_setup(M, lo, hi, k, s)
+    S = nc.pcg_setup(M, lo, hi, k, s, spmv_format=fmt)
+    assert nc.pcg_get_info(S)["spmv_format"] == fmt
     v = W.uniform_vector(A.n, seed=k + 10)
     z = torch.empty(A.n, dtype=torch.float64, device="cuda")
     nc.pcg_apply_poly(S, to_dev(torch, v), z)
@@ -66,8 +71,9 @@ def test_apply_poly_laplacian64(env, k, s):
     assert rel_err(got, ref) <= TOL_APPLY and elem_err(got, ref) <= TOL_APPLY
 
 
+@pytest.mark.parametrize("fmt", FORMATS)
 @pytest.mark.parametrize("N,k", [(24, 10), (24, 20), (24, 40), (31, 20)])
-def test_apply_poly_diffusion_lanczos_bounds(env, N, k):
+def test_apply_poly_diffusion_lanczos_bounds(env, N, k, fmt):
     torch, nc = env
     A = W.diffusion_3d_7pt_lognormal(N, seed=N)
     As, _ = scaled(A)
@@ -78,7 +84,7 @@ def test_apply_poly_diffusion_lanczos_bounds(env, N, k):
     g = gershgorin_np(As.rowptr, As.col, As.val, A.n)
     lo_o, hi_o, info = O.lanczos_bounds(mv, v0, 20, gershgorin=g)
     assert abs(lo - lo_o) <= 1e-9 * lo_o and abs(hi - hi_o) <= 1e-9 * hi_o
-    S = nc.pcg_setup(M, lo, hi, k, 1.001)
+    S = nc.pcg_setup(M, lo, hi, k, 1.001, spmv_format=fmt)
     v = W.uniform_vector(A.n, seed=7)
     z = torch.empty(A.n, dtype=torch.float64, device="cuda")
     nc.pcg_apply_poly(S, to_dev(torch, v), z)
@@ -87,7 +93,26 @@ def test_apply_poly_diffusion_lanczos_bounds(env, N, k):
     assert rel_err(got, ref) <= TOL_APPLY and elem_err(got, ref) <= TOL_APPLY
 
 
-def test_apply_poly_ragged_rows_and_long_rows(env):
+def test_auto_layout_choice(env):
+    """AUTO picks SELL-32 for a grid operator (small padding) and CSR for a
+    matrix with one dense row (padding far above 1.5)."""
+    torch, nc = env
+    A = W.diffusion_3d_7pt_lognormal(20, seed=1)
+    S = nc.pcg_setup(csr_to_gpu(torch, nc, A), 0.1, 2.0, 4, 1.0)
+    info = nc.pcg_get_info(S)
+    assert info["spmv_format"] == "sell" and 1.0 <= info["padding"] < 1.2
+    n = 2000
+    rows = [np.array([i]) for i in range(n)]
+    rows[7] = np.arange(n)
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    B = W.CSR(n, rowptr, np.concatenate(rows).astype(np.int32), np.ones(rowptr[-1]))
+    S2 = nc.pcg_setup(csr_to_gpu(torch, nc, B), 0.1, 2.0, 4, 1.0)
+    assert nc.pcg_get_info(S2)["spmv_format"] == "csr"
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_apply_poly_ragged_rows_and_long_rows(env, fmt):
     """Empty rows, a row longer than one shared-memory chunk, n not a multiple
     of the 256-row tile: exercises every branch of the row kernel."""
     torch, nc = env
@@ -113,7 +138,7 @@ def test_apply_poly_ragged_rows_and_long_rows(env):
         val = rng.uniform(-1, 1, col.size)
         Ac = W.CSR(nn, rowptr, col, val)
         M = csr_to_gpu(torch, nc, Ac)
-        S = nc.pcg_setup(M, 0.5, 3.0, 5, 1.0)
+        S = nc.pcg_setup(M, 0.5, 3.0, 5, 1.0, spmv_format=fmt)
         v = rng.uniform(-1, 1, nn)
         z = torch.empty(nn, dtype=torch.float64, device="cuda")
         nc.pcg_apply_poly(S, to_dev(torch, v), z)
@@ -121,8 +146,9 @@ def test_apply_poly_ragged_rows_and_long_rows(env):
         assert rel_err(z.cpu().numpy(), ref) <= TOL_APPLY
 
 
-@pytest.mark.parametrize("n", [1, 2, 255, 256, 257])
-def test_apply_poly_tiny(env, n):
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 255, 256, 257])
+def test_apply_poly_tiny(env, n, fmt):
     torch, nc = env
     A = W.laplacian_1d(n)
     lo = 4 * np.sin(np.pi / (2 * (n + 1))) ** 2
@@ -130,7 +156,7 @@ def test_apply_poly_tiny(env, n):
     if hi <= lo:
         hi = lo * 1.5
     M = csr_to_gpu(torch, nc, A)
-    S = nc.pcg_setup(M, lo, hi, 6, 1.001)
+    S = nc.pcg_setup(M, lo, hi, 6, 1.001, spmv_format=fmt)
     v = W.uniform_vector(n, seed=n)
     z = torch.empty(n, dtype=torch.float64, device="cuda")
     nc.pcg_apply_poly(S, to_dev(torch, v), z)
@@ -157,13 +183,14 @@ def _solve_both(torch, nc, A, lo, hi, k, s, b, jacobi, tol=1e-8, maxit=5000, **o
     return res, ro, x.cpu().numpy(), xo
 
 
+@pytest.mark.parametrize("fmt", FORMATS)
 @pytest.mark.parametrize("k,s", [(8, 1.0), (8, 1.001), (0, 1.0), (15, 1.01)])
-def test_solve_laplacian64(env, k, s):
+def test_solve_laplacian64(env, k, s, fmt):
     """The 64x64 5-point Laplacian with b = A x*, x* ~ U[-1,1], exact bounds."""
     torch, nc = env
     A, lo, hi = lap64()
     b = W.rhs_from_solution(A, W.uniform_vector(A.n, seed=1))
-    res, ro, x, xo = _solve_both(torch, nc, A, lo, hi, k, s, b, jacobi=False)
+    res, ro, x, xo = _solve_both(torch, nc, A, lo, hi, k, s, b, jacobi=False, spmv_format=fmt)
     assert res["status"] == 0 and ro.status == 0
     assert abs(res["iters"] - ro.iters) <= 1, (res["iters"], ro.iters)
     assert res["relres"] <= 1e-8 and res["true_relres"] <= 2e-8
@@ -173,8 +200,9 @@ def test_solve_laplacian64(env, k, s):
     assert rel_err(x, xo) <= kappa * 1e-8
 
 
+@pytest.mark.parametrize("fmt", FORMATS)
 @pytest.mark.parametrize("k", [10, 20, 40])
-def test_solve_diffusion_reduced(env, k):
+def test_solve_diffusion_reduced(env, k, fmt):
     """Variable-coefficient 3D diffusion (log-normal, sigma=1) at 32^3, Jacobi
     scaled, 20-step Lanczos bounds, s = 1.001."""
     torch, nc = env
@@ -184,7 +212,7 @@ def test_solve_diffusion_reduced(env, k):
     lo, hi, _ = O.lanczos_bounds(O.csr_matvec(As.rowptr, As.col, As.val, A.n), W.uniform_vector(A.n, seed=3), 20,
                                  gershgorin=g)
     b = W.uniform_vector(A.n, seed=5)
-    res, ro, x, xo = _solve_both(torch, nc, A, lo, hi, k, 1.001, b, jacobi=True)
+    res, ro, x, xo = _solve_both(torch, nc, A, lo, hi, k, 1.001, b, jacobi=True, spmv_format=fmt)
     assert res["status"] == 0 and ro.status == 0
     assert abs(res["iters"] - ro.iters) <= 1, (res["iters"], ro.iters)
     assert res["relres"] <= 1e-8 and res["true_relres"] <= 1e-7
@@ -272,8 +300,9 @@ def test_edge_cases(env):
     assert nc.pcg_solve(SE, e, e.clone(), 1e-8, 10)["iters"] == 0
 
 
+@pytest.mark.parametrize("fmt", FORMATS)
 @pytest.mark.parametrize("dt,tol_apply", [("f32", 1e-5), ("bf16", 3e-2)])
-def test_mixed_precision_apply_and_solve(env, dt, tol_apply):
+def test_mixed_precision_apply_and_solve(env, dt, tol_apply, fmt):
     """F32 / BF16 matrix inside P_k with a float64 outer CG: the apply is
     reported against the FP64 oracle and the solve still reaches 1e-8."""
     torch, nc = env
@@ -283,7 +312,7 @@ def test_mixed_precision_apply_and_solve(env, dt, tol_apply):
     lo, hi, _ = O.lanczos_bounds(mv, W.uniform_vector(A.n, seed=3), 20,
                                  gershgorin=gershgorin_np(As.rowptr, As.col, As.val, A.n))
     M = nc.nc_matrix_jacobi(csr_to_gpu(torch, nc, A))
-    S = nc.pcg_setup(M, lo, hi, 20, 1.001, apply_dtype=dt)
+    S = nc.pcg_setup(M, lo, hi, 20, 1.001, apply_dtype=dt, spmv_format=fmt)
     v = W.uniform_vector(A.n, seed=7)
     z = torch.empty(A.n, dtype=torch.float64, device="cuda")
     nc.pcg_apply_poly(S, to_dev(torch, v), z)
