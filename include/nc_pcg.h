@@ -84,6 +84,9 @@ typedef struct {
     int32_t pad0;
     double padding;       /* stored entries / nonzeros of the chosen layout    */
     double theta, delta, sigma;   /* theta' = s(a+b)/2, delta, sigma (Sec. 3/4) */
+    double shift;         /* the stored operator is A - shift*I (theta' with
+                             SELL: the (1 - x/theta') factor of the p_k
+                             recursion, Sec. 3), 0 = A itself               */
 } nc_solver_info;
 
 typedef struct {

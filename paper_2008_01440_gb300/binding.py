@@ -41,7 +41,8 @@ class nc_options(ctypes.Structure):
 class nc_solver_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("degree_k", ctypes.c_int32), ("spmv_format", ctypes.c_int32),
                 ("apply_dtype", ctypes.c_int32), ("pad0", ctypes.c_int32), ("padding", ctypes.c_double),
-                ("theta", ctypes.c_double), ("delta", ctypes.c_double), ("sigma", ctypes.c_double)]
+                ("theta", ctypes.c_double), ("delta", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("shift", ctypes.c_double)]
 
 
 class nc_result(ctypes.Structure):

@@ -51,11 +51,13 @@ struct nc_solver_s {
     nc_options opt{};
     double theta = 0.0, delta = 0.0, sigma = 0.0;
     std::vector<double> ca, cb, cc, cd;   // per Chebyshev step 1..k (index 0 unused)
+    double ca1_shifted = 0.0;             // step-1 coefficient of u = r for the shifted operator
     bool mixed = false;
     int vdt = NC_F64;
     OpView op64;                          // float64 operator (outer CG, true residual)
     OpView opP;                           // operator inside P_k (apply precision)
     double padding = 1.0;                 // SELL stored entries / nnz
+    double shift = 0.0;                   // op values hold A - shift*I (theta' for SELL, else 0)
     void* lval = nullptr;                 // converted CSR values (F32/BF16), owned
     int32_t* sell_ptr = nullptr;          // SELL-32 arrays, owned
     int32_t* sell_col = nullptr;
@@ -195,6 +197,13 @@ void sym_eig(int m, std::vector<double>& a, std::vector<double>& V) {
 
 // ---- solver internals -------------------------------------------------------
 
+// y = cc*r + cd*(A u) with the solver's float64 operator.  When the stored
+// values are A' = A - shift*I, A u = A' u + shift*u: the u term carries it.
+cudaError_t op64_apply(nc_solver S, const double* u, const double* r, double* y, double cc, double cd, int dot,
+                       const Reduce& R, const int* done, cudaStream_t st) {
+    return op_step(S->op64, false, true, u, nullptr, r, y, cd * S->shift, 0.0, cc, cd, dot, nullptr, R, done, st);
+}
+
 // Coefficients of the fused steps from rho_k (Eq. rhocheb), theta' = s theta.
 void setup_coefficients(nc_solver S) {
     const double theta = S->s * (S->lmax + S->lmin) / 2.0;
@@ -214,6 +223,7 @@ void setup_coefficients(nc_solver S) {
     if (k >= 1) {   // x_1 = (2 rho_1/delta)(2 r - A r/theta), product applied to u = r
         S->ca[1] = 4.0 * rho[1] / delta;
         S->cd[1] = -2.0 * rho[1] / (delta * theta);
+        S->ca1_shifted = 2.0 * rho[1] / delta;
     }
     for (int j = 2; j <= k; ++j) {
         S->ca[j] = 2.0 * sigma * rho[j];
@@ -241,7 +251,12 @@ cudaError_t enqueue_poly(nc_solver S, const double* r64, double* z, int fin, con
         const bool last = (j == S->k);
         void* y = last ? static_cast<void*>(z) : S->buf[j % 3];
         const int dot = (last && fin != FIN_NONE) ? 1 : 0;
-        cudaError_t e = op_step(S->opP, S->mixed, last || !S->mixed, u, w, rx, y, S->ca[j], S->cb[j], S->cc[j],
+        // with the shifted operator A' = A - theta' I the x_{k-1} term of
+        // every step k >= 2 vanishes (a_k + d_k theta' = 0 exactly) and step 1
+        // keeps (4 rho_1 - 2 rho_1)/delta = 2 rho_1/delta on r
+        double ca = S->ca[j];
+        if (S->shift != 0.0) ca = (j == 1) ? S->ca1_shifted : 0.0;
+        cudaError_t e = op_step(S->opP, S->mixed, last || !S->mixed, u, w, rx, y, ca, S->cb[j], S->cc[j],
                                 S->cd[j], dot, r64, R, done, st);
         if (e != cudaSuccess) return e;
     }
@@ -258,7 +273,7 @@ cudaError_t enqueue_prologue(nc_solver S, cudaStream_t st) {
         e = launch_copy(n, S->b, S->r, nullptr, st);
     } else {
         const Reduce none = make_reduce(S->partials, S->counter, S->S, nullptr, FIN_NONE);
-        e = op_step(S->op64, false, true, S->x, nullptr, S->b, S->r, 0.0, 0.0, 1.0, -1.0, 0, nullptr, none, nullptr, st);
+        e = op64_apply(S, S->x, S->b, S->r, 1.0, -1.0, 0, none, nullptr, st);
     }
     if (e) return e;
     if (S->mixed) {
@@ -276,8 +291,8 @@ cudaError_t enqueue_body(nc_solver S, cudaGraphConditionalHandle h, int use_cond
     const int n = (int)S->n;
     const int* done = &S->S->done;
     cudaError_t e;
-    e = op_step(S->op64, false, true, S->p, nullptr, nullptr, S->q, 0.0, 0.0, 0.0, 1.0, 2, nullptr,
-                make_reduce(S->partials, S->counter, S->S, nullptr, FIN_ALPHA), done, st);
+    e = op64_apply(S, S->p, nullptr, S->q, 0.0, 1.0, 2, make_reduce(S->partials, S->counter, S->S, nullptr, FIN_ALPHA),
+                   done, st);
     if (e) return e;
     e = launch_axpy2_rr(n, S->x, S->r, S->p, S->q, S->mixed ? S->r32 : nullptr,
                         make_reduce(S->partials, S->counter, S->S, nullptr, FIN_RR), st);
@@ -362,8 +377,7 @@ nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
     }
     // true residual of the (scaled) system at exit
     const Reduce none = make_reduce(S->partials, S->counter, S->S, nullptr, FIN_NONE);
-    NC_CU(op_step(S->op64, false, true, S->x, nullptr, S->b, S->q, 0.0, 0.0, 1.0, -1.0, 0, nullptr, none, nullptr,
-                  st));
+    NC_CU(op64_apply(S, S->x, S->b, S->q, 1.0, -1.0, 0, none, nullptr, st));
     NC_CU(launch_dot(n, S->q, S->q, make_reduce(S->partials, S->counter, S->S, nullptr, FIN_TRUE), nullptr, st));
     NC_CU(launch_copy_out(n, S->x, S->A->dis, S->S, x_dev, st));
     NC_CU(cudaMemcpyAsync(S->h_io, S->S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
@@ -432,17 +446,38 @@ nc_status setup_operator(nc_solver S, cudaStream_t st) {
     NC_TRY(dev_alloc_n(&S->sell_ptr, nslices + 1));
     NC_TRY(dev_alloc_n(&S->sell_col, total));
     NC_TRY(dev_alloc_n(&S->sell_val64, total));
+    int* nodiag = nullptr;
+    NC_TRY(dev_alloc_n(&nodiag, 1));
+    int h_nodiag = 0;
+    // the shifted operator A - theta' I needs every row's diagonal entry;
+    // without one, store A itself (shift 0)
+    S->shift = S->k >= 1 ? S->theta : 0.0;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(S->sell_ptr, hp32.data(), sizeof(int32_t) * (nslices + 1), cudaMemcpyHostToDevice, st)) ||
-        (e = launch_sell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, NC_F64, S->sell_col, S->sell_val64, st))) {
+    if ((e = cudaMemsetAsync(nodiag, 0, sizeof(int), st)) ||
+        (e = cudaMemcpyAsync(S->sell_ptr, hp32.data(), sizeof(int32_t) * (nslices + 1), cudaMemcpyHostToDevice, st)) ||
+        (e = launch_sell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, NC_F64, S->shift, S->sell_col,
+                              S->sell_val64, nodiag, st)) ||
+        (e = cudaMemcpyAsync(&h_nodiag, nodiag, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st))) {
+        dev_free(nodiag);
         g_last_cuda = e;
         return NC_ERR_CUDA;
+    }
+    dev_free(nodiag);
+    if (h_nodiag) {
+        S->shift = 0.0;
+        if ((e = launch_sell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, NC_F64, 0.0, S->sell_col,
+                                  S->sell_val64, nullptr, st))) {
+            g_last_cuda = e;
+            return NC_ERR_CUDA;
+        }
     }
     S->op64 = OpView{OP_SELL, n, S->sell_ptr, S->sell_col, S->sell_val64, NC_F64};
     S->opP = S->op64;
     if (S->mixed) {
         NC_TRY(dev_alloc(&S->sell_valP, eb * (size_t)total));
-        if ((e = launch_sell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, S->vdt, S->sell_col, S->sell_valP, st))) {
+        if ((e = launch_sell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, S->vdt, S->shift, S->sell_col,
+                                  S->sell_valP, nullptr, st))) {
             g_last_cuda = e;
             return NC_ERR_CUDA;
         }
@@ -774,6 +809,7 @@ nc_status pcg_get_info(nc_solver S, nc_solver_info* info) {
     info->theta = S->theta;
     info->delta = S->delta;
     info->sigma = S->sigma;
+    info->shift = S->shift;
     return NC_OK;
 }
 

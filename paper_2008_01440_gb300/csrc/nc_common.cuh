@@ -165,8 +165,10 @@ cudaError_t launch_sell_step(int n, const int32_t* slice_ptr, const int32_t* col
                              const Reduce& R, const int* done, cudaStream_t st);
 // SELL-32 construction from CSR: longest row per slice, then the slot-major fill
 cudaError_t launch_sell_lengths(int n, const int32_t* rowptr, int32_t* slice_len, cudaStream_t st);
+// (diagonal entries stored as a_ii - shift; *nodiag set if a row lacks one)
 cudaError_t launch_sell_fill(int n, const int32_t* rowptr, const int32_t* col, const double* val,
-                             const int32_t* slice_ptr, int vdt, int32_t* scol, void* sval, cudaStream_t st);
+                             const int32_t* slice_ptr, int vdt, double shift, int32_t* scol, void* sval,
+                             int* nodiag, cudaStream_t st);
 
 cudaError_t launch_csr_diag(int n, const int32_t* rowptr, const int32_t* col, const double* val,
                             double* dis, int* bad, cudaStream_t st);

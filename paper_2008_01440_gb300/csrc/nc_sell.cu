@@ -14,11 +14,18 @@
 //
 // The layout is built once at solver setup from the CSR arrays; it is chosen
 // when its padding is small (grid and finite-element matrices), otherwise
-// the CSR kernel runs.
+// the CSR kernel runs.  The solver stores the shifted operator A - theta' I
+// (only diagonal entries change): the p_k recursion of Sec. 3 applies
+// 2 sigma (1 - A/theta') = -(2/delta)(A - theta' I), so with the shift every
+// Chebyshev step after the first needs no separate x_{k-1} term, one FP64
+// instruction less per row on GB300's narrow FP64 pipe; the outer products
+// add theta' u back (q = A' p + theta' p).
 #include "nc_step.cuh"
 
 namespace nc {
 namespace {
+
+constexpr int kSellGroup = 8;
 
 template <typename VT, typename XT, typename YT, int DOT>
 __global__ void __launch_bounds__(kBlock)
@@ -33,28 +40,59 @@ sell_step_kernel(const int n, const int32_t* __restrict__ slice_ptr, const int32
     if (row < n) {
         const int s = row >> 5;
         const int beg = slice_ptr[s];
-        const int len = (slice_ptr[s + 1] - beg) >> 5;
+        const int len = (slice_ptr[s + 1] - beg) >> 5;   // warp-uniform
         const VT* vp = val + beg + (row & 31);
         const int32_t* cp = col + beg + (row & 31);
         AT acc = AT(0);
-        int j = 0;
-        for (; j + 4 <= len; j += 4) {
-            const int c0 = ld_stream(cp), c1 = ld_stream(cp + 32), c2 = ld_stream(cp + 64), c3 = ld_stream(cp + 96);
-            const AT v0 = (AT)ld_stream(vp), v1 = (AT)ld_stream(vp + 32), v2 = (AT)ld_stream(vp + 64),
-                     v3 = (AT)ld_stream(vp + 96);
-            const AT x0 = (AT)__ldg(u + c0), x1 = (AT)__ldg(u + c1), x2 = (AT)__ldg(u + c2), x3 = (AT)__ldg(u + c3);
-            acc = fma(v0, x0, acc);
-            acc = fma(v1, x1, acc);
-            acc = fma(v2, x2, acc);
-            acc = fma(v3, x3, acc);
-            vp += 128;
-            cp += 128;
-        }
-        for (; j < len; ++j) {
-            const int c0 = ld_stream(cp);
-            acc = fma((AT)ld_stream(vp), (AT)__ldg(u + c0), acc);
-            vp += 32;
-            cp += 32;
+        if constexpr (sizeof(AT) == 8) {
+            // float64: the fma chain itself is long-latency on GB300's narrow
+            // FP64 pipe, so occupancy matters most: a 4-slot unroll keeps the
+            // kernel at 32 registers and 8 CTAs (2048 threads) per SM.
+            int j = 0;
+            for (; j + 4 <= len; j += 4) {
+                const int c0 = ld_stream(cp), c1 = ld_stream(cp + 32), c2 = ld_stream(cp + 64),
+                          c3 = ld_stream(cp + 96);
+                const AT v0 = (AT)ld_stream(vp), v1 = (AT)ld_stream(vp + 32), v2 = (AT)ld_stream(vp + 64),
+                         v3 = (AT)ld_stream(vp + 96);
+                const AT x0 = (AT)__ldg(u + c0), x1 = (AT)__ldg(u + c1), x2 = (AT)__ldg(u + c2),
+                         x3 = (AT)__ldg(u + c3);
+                acc = fma(v0, x0, acc);
+                acc = fma(v1, x1, acc);
+                acc = fma(v2, x2, acc);
+                acc = fma(v3, x3, acc);
+                vp += 128;
+                cp += 128;
+            }
+            for (; j < len; ++j) {
+                const int c0 = ld_stream(cp);
+                acc = fma((AT)ld_stream(vp), (AT)__ldg(u + c0), acc);
+                vp += 32;
+                cp += 32;
+            }
+        } else {
+            // float: memory latency is the limit, so every column and value
+            // load of a group of 8 slots is issued before the gathers, and all
+            // gathers before the fma chain: a grid row (<= 8 slots) costs two
+            // memory latencies in total.  The guards are warp-uniform.
+            constexpr int G = kSellGroup;
+            for (int j0 = 0; j0 < len; j0 += G) {
+                int cc_[G];
+                AT vv[G], xx[G];
+#pragma unroll
+                for (int t = 0; t < G; ++t)
+                    if (j0 + t < len) {
+                        cc_[t] = ld_stream(cp + 32 * t);
+                        vv[t] = (AT)ld_stream(vp + 32 * t);
+                    }
+#pragma unroll
+                for (int t = 0; t < G; ++t)
+                    if (j0 + t < len) xx[t] = (AT)__ldg(u + cc_[t]);
+#pragma unroll
+                for (int t = 0; t < G; ++t)
+                    if (j0 + t < len) acc = fma(vv[t], xx[t], acc);
+                vp += 32 * G;
+                cp += 32 * G;
+            }
         }
         dv = step_row_out<XT, YT, DOT, AT>(row, acc, c, u, w, r, y, rdot);
     }
@@ -76,10 +114,14 @@ __device__ __forceinline__ void put_val(double* p, double v) { *p = v; }
 __device__ __forceinline__ void put_val(float* p, double v) { *p = (float)v; }
 __device__ __forceinline__ void put_val(__nv_bfloat16* p, double v) { *p = __double2bfloat16(v); }
 
+// Slot-major fill.  The diagonal entry of every row is stored shifted,
+// a_ii - shift (shift = 0 stores A itself); *nodiag is set if some row has
+// no stored diagonal entry to shift.
 template <typename VT>
 __global__ void sell_fill_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                  const double* __restrict__ val, const int32_t* __restrict__ slice_ptr,
-                                 int32_t* __restrict__ scol, VT* __restrict__ sval) {
+                                 double shift, int32_t* __restrict__ scol, VT* __restrict__ sval,
+                                 int* __restrict__ nodiag) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     const int nslices = (n + 31) >> 5;
     if ((row >> 5) >= nslices) return;
@@ -92,16 +134,24 @@ __global__ void sell_fill_kernel(int n, const int32_t* __restrict__ rowptr, cons
         rl = rowptr[row + 1] - rs;
     }
     const int self = row < n ? row : n - 1;
+    bool has_diag = false;
     for (int j = 0; j < len; ++j) {
         const int idx = beg + 32 * j;
         if (j < rl) {
-            scol[idx] = col[rs + j];
-            put_val(&sval[idx], val[rs + j]);
+            const int cj = col[rs + j];
+            scol[idx] = cj;
+            double v = val[rs + j];
+            if (cj == row) {
+                v -= shift;
+                has_diag = true;
+            }
+            put_val(&sval[idx], v);
         } else {
             scol[idx] = self;
             put_val(&sval[idx], 0.0);
         }
     }
+    if (row < n && !has_diag && shift != 0.0 && nodiag != nullptr) atomicOr(nodiag, 1);
 }
 
 template <typename VT, typename XT, typename YT>
@@ -168,17 +218,20 @@ cudaError_t launch_sell_lengths(int n, const int32_t* rowptr, int32_t* slice_len
 }
 
 cudaError_t launch_sell_fill(int n, const int32_t* rowptr, const int32_t* col, const double* val,
-                             const int32_t* slice_ptr, int vdt, int32_t* scol, void* sval, cudaStream_t st) {
+                             const int32_t* slice_ptr, int vdt, double shift, int32_t* scol, void* sval,
+                             int* nodiag, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int threads = ((n + 31) / 32) * 32;
     const int grid = (threads + 255) / 256;
     if (vdt == NC_F64)
-        sell_fill_kernel<double><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, scol, static_cast<double*>(sval));
+        sell_fill_kernel<double><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, shift, scol,
+                                                       static_cast<double*>(sval), nodiag);
     else if (vdt == NC_F32)
-        sell_fill_kernel<float><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, scol, static_cast<float*>(sval));
+        sell_fill_kernel<float><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, shift, scol,
+                                                      static_cast<float*>(sval), nodiag);
     else if (vdt == NC_BF16)
-        sell_fill_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, scol,
-                                                              static_cast<__nv_bfloat16*>(sval));
+        sell_fill_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, shift, scol,
+                                                              static_cast<__nv_bfloat16*>(sval), nodiag);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

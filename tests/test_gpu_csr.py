@@ -101,6 +101,8 @@ def test_auto_layout_choice(env):
     S = nc.pcg_setup(csr_to_gpu(torch, nc, A), 0.1, 2.0, 4, 1.0)
     info = nc.pcg_get_info(S)
     assert info["spmv_format"] == "sell" and 1.0 <= info["padding"] < 1.2
+    # SELL stores the shifted operator A - theta' I (every row has a diagonal)
+    assert info["shift"] == info["theta"] == 1.0 * (0.1 + 2.0) / 2
     n = 2000
     rows = [np.array([i]) for i in range(n)]
     rows[7] = np.arange(n)
@@ -139,6 +141,8 @@ def test_apply_poly_ragged_rows_and_long_rows(env, fmt):
         Ac = W.CSR(nn, rowptr, col, val)
         M = csr_to_gpu(torch, nc, Ac)
         S = nc.pcg_setup(M, 0.5, 3.0, 5, 1.0, spmv_format=fmt)
+        # rows without a stored diagonal: no shifted operator
+        assert nc.pcg_get_info(S)["shift"] == 0.0
         v = rng.uniform(-1, 1, nn)
         z = torch.empty(nn, dtype=torch.float64, device="cuda")
         nc.pcg_apply_poly(S, to_dev(torch, v), z)
