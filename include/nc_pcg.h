@@ -66,8 +66,10 @@ typedef struct {
     int apply_dtype;   /* nc_dtype: F64 = plain method; F32: float32 matrix and
                           vectors inside P_k; BF16: bfloat16 matrix values,
                           float32 vectors and accumulation.                     */
-    int rr_period;     /* > 0: replace r by b - A x in float64 every rr_period
-                          iterations (mixed precision); 0 = never.              */
+    int rr_period;     /* > 0: replace the recurrence residual by the true one,
+                          r = b - A x in float64, after every rr_period-th
+                          iteration that does not stop (mixed precision); the
+                          search direction p is kept.  0 = never.              */
     int x0_is_zero;    /* 1: ignore x on input and start from x0 = 0 (saves the
                           initial product b - A x0).                            */
     int use_graph;     /* 1 (default): one CUDA graph per solve with the
@@ -94,8 +96,10 @@ typedef struct {
     int32_t status;       /* nc_status of the solve                              */
     double relres;        /* ||r_i|| / ||b||, recurrence residual, scaled system */
     double true_relres;   /* ||b - A x|| / ||b|| recomputed at exit, same system */
-    int64_t n_spmv;       /* products with A: (k+1) per iteration (Table 4)      */
+    int64_t n_spmv;       /* products with A: (k+1) per iteration (Table 4), plus
+                             one per residual replacement                        */
     int64_t n_dot;        /* dot products: 3 per iteration (Table 4)             */
+    int64_t n_replace;    /* residual replacements performed                     */
 } nc_result;
 
 /* Fill `opt` with the defaults: F64, no residual replacement, x0 from x,
@@ -119,6 +123,17 @@ NC_API const char* nc_last_cuda_error(void);
 NC_API nc_status nc_matrix_csr(int64_t n, int64_t nnz, const int32_t* rowptr_dev,
                         const int32_t* col_dev, const double* val_dev, nc_matrix* out);
 
+/* Matrix-free constant-coefficient 7-point operator on an nx x ny x nz grid
+ * (Sec. 1: only v -> A v is needed; Sec. 5.3: FD-3D Poisson), zero
+ * Dirichlet halo, unknown (i, j, k) at index i + nx (j + ny k):
+ *   (A u)_p = c0 u_p - cx (u_{p-ex} + u_{p+ex}) - cy (...) - cz (...).
+ * No device memory is involved; the handle holds only the coefficients.
+ * NC_ERR_ARG if a side is < 1, nx*ny*nz >= 2^31 or a coefficient is not
+ * finite.  The operator is SPD when c0 > 2 sum_a |c_a| cos(pi/(n_a + 1))
+ * (not checked). */
+NC_API nc_status nc_matrix_stencil7(int nx, int ny, int nz, double c0, double cx, double cy, double cz,
+                                    nc_matrix* out);
+
 /* Symmetric diagonal (Jacobi) scaling A_s = D^{-1/2} A D^{-1/2}, D = diag(A)
  * (Sec. 2, end: "symmetrically scaled by the diagonal"; Sec. 5: all matrices
  * are scaled before solving).  Returns a new handle that OWNS the scaled
@@ -126,7 +141,10 @@ NC_API nc_status nc_matrix_csr(int64_t n, int64_t nnz, const int32_t* rowptr_dev
  * outlive it.  pcg_solve on a solver built on this handle solves the
  * original system A x = b: it forms b_s = D^{-1/2} b, solves A_s y = b_s
  * (the stopping test is on this scaled system) and returns x = D^{-1/2} y.
- * NC_ERR_ARG if a diagonal entry is missing or not positive. */
+ * For a stencil handle the scaled operator is again a stencil (c0 = 1,
+ * c_a / c0) and D^{-1/2} = c0^{-1/2}; nothing is allocated.
+ * NC_ERR_ARG if a diagonal entry is missing or not positive, or if A is
+ * already a scaled handle. */
 NC_API nc_status nc_matrix_jacobi(nc_matrix A, void* stream, nc_matrix* out);
 
 /* y_dev = A x_dev for the handle's operator.  x_dev, y_dev: n float64,

@@ -31,8 +31,13 @@ class PCGResult:
 
 
 def pcg(matvec, b: np.ndarray, precond=None, m: int = 0, x0=None, tol: float = 1e-8,
-        maxit: int = 10000) -> PCGResult:
+        maxit: int = 10000, rr_period: int = 0) -> PCGResult:
     """Solve A x = b by PCG with preconditioner z = precond(r).
+
+    ``rr_period`` > 0: after every rr_period-th iteration that does not stop,
+    the recurrence residual is replaced by the true residual b - A x (the
+    search direction is kept).  This is not part of the paper's method; in
+    exact arithmetic it changes nothing, which is what pins it.
 
     ``m`` is the number of matrix-vector products one preconditioner call
     costs (the degree of P_m), used only for the counters.
@@ -84,6 +89,10 @@ def pcg(matvec, b: np.ndarray, precond=None, m: int = 0, x0=None, tol: float = 1
         if np.sqrt(rr) <= tol * bnorm:
             status = OK
             break
+        if it >= maxit:
+            break
+        if rr_period > 0 and it % rr_period == 0:
+            r = b - matvec(x)
         z = precond(r)
         n_pc += 1
         n_mv += m

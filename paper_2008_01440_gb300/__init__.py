@@ -39,6 +39,7 @@ from .binding import (  # noqa: F401
     nc_matrix_csr,
     nc_matrix_destroy,
     nc_matrix_jacobi,
+    nc_matrix_stencil7,
     nc_matvec,
     nc_version,
     pcg_apply_poly,

@@ -47,7 +47,8 @@ class nc_solver_info(ctypes.Structure):
 
 class nc_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("relres", ctypes.c_double),
-                ("true_relres", ctypes.c_double), ("n_spmv", ctypes.c_int64), ("n_dot", ctypes.c_int64)]
+                ("true_relres", ctypes.c_double), ("n_spmv", ctypes.c_int64), ("n_dot", ctypes.c_int64),
+                ("n_replace", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -65,6 +66,8 @@ _SIGS = {
     "nc_last_cuda_error": (ctypes.c_char_p, []),
     "nc_matrix_csr": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "nc_matrix_jacobi": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "nc_matrix_stencil7": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dbl, _dbl, _dbl, _dbl,
+                                          ctypes.POINTER(_vp)]),
     "nc_matvec": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "nc_bounds_lanczos": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _pd, _pd, _pd, _pd]),
     "nc_gershgorin": (ctypes.c_int, [_vp, _vp, _pd]),
@@ -174,6 +177,13 @@ def nc_matrix_csr(rowptr, col, val) -> Matrix:
                              _ptr(col, torch.int32, what="col"), _ptr(val, torch.float64, nnz, "val"),
                              ctypes.byref(h)), "nc_matrix_csr")
     return Matrix(h.value, n, (rowptr, col, val))
+
+
+def nc_matrix_stencil7(nx: int, ny: int, nz: int, c0: float, cx: float, cy: float, cz: float) -> Matrix:
+    h = _vp()
+    _check(lib.nc_matrix_stencil7(int(nx), int(ny), int(nz), float(c0), float(cx), float(cy), float(cz),
+                                  ctypes.byref(h)), "nc_matrix_stencil7")
+    return Matrix(h.value, int(nx) * int(ny) * int(nz), ())
 
 
 def nc_matrix_jacobi(A: Matrix, stream=None) -> Matrix:

@@ -19,7 +19,7 @@
 
 using namespace nc;
 
-enum MatKind : int { MAT_CSR = 0 };
+enum MatKind : int { MAT_CSR = 0, MAT_STENCIL7 = 1 };
 
 struct nc_matrix_s {
     int kind = MAT_CSR;
@@ -28,12 +28,16 @@ struct nc_matrix_s {
     const int32_t* col = nullptr;
     const double* val = nullptr;    // values used by products (borrowed or owned_val)
     double* owned_val = nullptr;    // scaled copy (nc_matrix_jacobi)
-    double* dis = nullptr;          // d^{-1/2} of the scaling, owned
+    double* dis = nullptr;          // d^{-1/2} of the scaling, owned (CSR)
+    bool scaled = false;            // built by nc_matrix_jacobi
+    double dis_scalar = 1.0;        // constant d^{-1/2} (stencil)
+    StencilGeom geom{0, 0, 0};      // stencil grid
+    double c4[4] = {0, 0, 0, 0};    // stencil coefficients c0, cx, cy, cz
 };
 
 // A matrix as the step kernels see it: CSR (the handle's arrays) or the
 // solver-owned SELL-32 layout, with float64 or low-precision values.
-enum OpKind : int { OP_CSR = 0, OP_SELL = 1 };
+enum OpKind : int { OP_CSR = 0, OP_SELL = 1, OP_STENCIL = 2 };
 struct OpView {
     int kind = OP_CSR;
     int n = 0;
@@ -41,6 +45,8 @@ struct OpView {
     const int32_t* col = nullptr;
     const void* val = nullptr;
     int vdt = NC_F64;
+    StencilGeom geom{0, 0, 0};      // OP_STENCIL
+    double c4[4] = {0, 0, 0, 0};
 };
 
 struct nc_solver_s {
@@ -126,6 +132,34 @@ int64_t max_partials(int64_t n) {
     return (rows > kVecGrid ? rows : kVecGrid) + 1;
 }
 
+// partial-sum slots any reduction kernel on this matrix may need
+int64_t partials_for(nc_matrix A) {
+    int64_t p = max_partials(A->n);
+    if (A->kind == MAT_STENCIL7) {
+        const int64_t sb = stencil_nblocks(A->geom) + 1;
+        if (sb > p) p = sb;
+    }
+    return p;
+}
+
+// float64 operator view of a matrix handle
+OpView mat_view(nc_matrix A) {
+    OpView v;
+    v.n = (int)A->n;
+    if (A->kind == MAT_STENCIL7) {
+        v.kind = OP_STENCIL;
+        v.geom = A->geom;
+        for (int i = 0; i < 4; ++i) v.c4[i] = A->c4[i];
+    } else {
+        v.kind = OP_CSR;
+        v.ptr = A->rowptr;
+        v.col = A->col;
+        v.val = A->val;
+    }
+    v.vdt = NC_F64;
+    return v;
+}
+
 Reduce make_reduce(double* partials, unsigned int* counter, PcgScalars* S, double* out, int fin) {
     Reduce R;
     R.partials = partials;
@@ -136,22 +170,24 @@ Reduce make_reduce(double* partials, unsigned int* counter, PcgScalars* S, doubl
     return R;
 }
 
-// y = ca u + cb w + cc r + cd (A u) with the handle's float64 values
-cudaError_t op_step_f64(nc_matrix A, const double* u, const double* w, const double* r, double* y,
-                        double ca, double cb, double cc, double cd, int dot, const double* rdot,
-                        const Reduce& R, const int* done, cudaStream_t st) {
-    return launch_csr_step((int)A->n, A->rowptr, A->col, A->val, NC_F64, false, true, u, w, r, y, ca,
-                           cb, cc, cd, dot, rdot, R, done, st);
-}
-
 cudaError_t op_step(const OpView& op, bool x_f32, bool y_f64, const void* u, const void* w, const void* r,
                     void* y, double ca, double cb, double cc, double cd, int dot, const double* rdot,
                     const Reduce& R, const int* done, cudaStream_t st) {
     if (op.kind == OP_SELL)
         return launch_sell_step(op.n, op.ptr, op.col, op.val, op.vdt, x_f32, y_f64, u, w, r, y, ca, cb, cc, cd,
                                 dot, rdot, R, done, st);
+    if (op.kind == OP_STENCIL)
+        return launch_stencil_step(op.geom, op.c4, x_f32, y_f64, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done,
+                                   st);
     return launch_csr_step(op.n, op.ptr, op.col, op.val, op.vdt, x_f32, y_f64, u, w, r, y, ca, cb, cc, cd, dot,
                            rdot, R, done, st);
+}
+
+// y = ca u + cb w + cc r + cd (A u) with the handle's float64 operator
+cudaError_t op_step_f64(nc_matrix A, const double* u, const double* w, const double* r, double* y,
+                        double ca, double cb, double cc, double cd, int dot, const double* rdot,
+                        const Reduce& R, const int* done, cudaStream_t st) {
+    return op_step(mat_view(A), false, true, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done, st);
 }
 
 // Cyclic Jacobi eigen-decomposition of a small symmetric matrix (row-major),
@@ -297,6 +333,18 @@ cudaError_t enqueue_body(nc_solver S, cudaGraphConditionalHandle h, int use_cond
     e = launch_axpy2_rr(n, S->x, S->r, S->p, S->q, S->mixed ? S->r32 : nullptr,
                         make_reduce(S->partials, S->counter, S->S, nullptr, FIN_RR), st);
     if (e) return e;
+    if (S->opt.rr_period > 0) {
+        // residual replacement: r = b - A x in float64 (kernels skip unless
+        // this iteration is a multiple of rr_period and the solve goes on)
+        const int* skip = &S->S->rr_skip;
+        const Reduce none = make_reduce(S->partials, S->counter, S->S, nullptr, FIN_NONE);
+        e = op64_apply(S, S->x, S->b, S->r, 1.0, -1.0, 0, none, skip, st);
+        if (e) return e;
+        if (S->mixed) {
+            e = launch_refresh_r32(n, S->r, S->r32, skip, st);
+            if (e) return e;
+        }
+    }
     e = enqueue_poly(S, S->r, S->z, FIN_BETA, done, st);
     if (e) return e;
     return launch_p_update(n, S->p, S->z, S->S, h, use_cond, st);
@@ -352,11 +400,13 @@ nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
     init.tol2 = tol * tol;
     init.maxit = maxit;
     init.status = NC_ERR_MAXIT;
+    init.rr_period = S->opt.rr_period;
+    init.rr_skip = 1;
     // the pinned staging block is reused by every solve; the previous solve
     // synchronised the stream, so it is free
     *S->h_io = init;
     NC_CU(cudaMemcpyAsync(S->S, S->h_io, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
-    NC_CU(launch_copy_in(n, b_dev, x_dev, S->A->dis, S->opt.x0_is_zero, S->b, S->x, st));
+    NC_CU(launch_copy_in(n, b_dev, x_dev, S->A->dis, S->A->dis_scalar, S->opt.x0_is_zero, S->b, S->x, st));
     bool graph = S->opt.use_graph && !S->graph_failed;
     if (graph && S->exec == nullptr) {
         if (build_graph(S) != NC_OK) {
@@ -379,7 +429,7 @@ nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
     const Reduce none = make_reduce(S->partials, S->counter, S->S, nullptr, FIN_NONE);
     NC_CU(op64_apply(S, S->x, S->b, S->q, 1.0, -1.0, 0, none, nullptr, st));
     NC_CU(launch_dot(n, S->q, S->q, make_reduce(S->partials, S->counter, S->S, nullptr, FIN_TRUE), nullptr, st));
-    NC_CU(launch_copy_out(n, S->x, S->A->dis, S->S, x_dev, st));
+    NC_CU(launch_copy_out(n, S->x, S->A->dis, S->A->dis_scalar, S->S, x_dev, st));
     NC_CU(cudaMemcpyAsync(S->h_io, S->S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
     NC_CU(cudaStreamSynchronize(st));
     const PcgScalars& o = *S->h_io;
@@ -390,7 +440,8 @@ nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
     rr.relres = bnorm > 0 ? std::sqrt(o.rr) / bnorm : 0.0;
     rr.true_relres = bnorm > 0 ? std::sqrt(o.rr_true) / bnorm : 0.0;
     rr.n_dot = o.n_dot;
-    rr.n_spmv = (int64_t)o.iter + (int64_t)S->k * o.n_prec;
+    rr.n_spmv = (int64_t)o.iter + (int64_t)S->k * o.n_prec + o.n_replace;
+    rr.n_replace = o.n_replace;
     if (res) *res = rr;
     return (nc_status)o.status;
 }
@@ -402,6 +453,14 @@ constexpr double kSellMaxPadding = 1.5;
 nc_status setup_operator(nc_solver S, cudaStream_t st) {
     nc_matrix A = S->A;
     const int n = (int)S->n;
+    if (A->kind == MAT_STENCIL7) {   // matrix-free: nothing to build
+        S->op64 = mat_view(A);
+        S->opP = S->op64;
+        S->opP.vdt = S->vdt;
+        S->padding = 1.0;
+        S->shift = 0.0;
+        return NC_OK;
+    }
     const size_t eb = S->vdt == NC_F64 ? 8 : (S->vdt == NC_F32 ? 4 : 2);
     bool sell = S->opt.spmv_format != NC_FORMAT_CSR && n > 0;
     std::vector<int64_t> hptr;
@@ -539,10 +598,43 @@ nc_status nc_matrix_csr(int64_t n, int64_t nnz, const int32_t* rowptr_dev, const
     return NC_OK;
 }
 
+nc_status nc_matrix_stencil7(int nx, int ny, int nz, double c0, double cx, double cy, double cz, nc_matrix* out) {
+    if (!out) return NC_ERR_ARG;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return NC_ERR_ARG;
+    const int64_t n = (int64_t)nx * ny * nz;
+    if (n >= ((int64_t)1 << 31)) return NC_ERR_ARG;
+    if (!std::isfinite(c0) || !std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(cz)) return NC_ERR_ARG;
+    nc_matrix A = new (std::nothrow) nc_matrix_s();
+    if (!A) return NC_ERR_OOM;
+    A->kind = MAT_STENCIL7;
+    A->n = n;
+    A->nnz = 0;
+    A->geom = StencilGeom{nx, ny, nz};
+    A->c4[0] = c0;
+    A->c4[1] = cx;
+    A->c4[2] = cy;
+    A->c4[3] = cz;
+    *out = A;
+    return NC_OK;
+}
+
 nc_status nc_matrix_jacobi(nc_matrix A, void* stream, nc_matrix* out) {
     if (!A || !out) return NC_ERR_ARG;
     *out = nullptr;
-    if (A->dis) return NC_ERR_ARG;   // already scaled
+    if (A->scaled) return NC_ERR_ARG;   // already scaled
+    if (A->kind == MAT_STENCIL7) {      // constant diagonal c0: D^{-1/2} = c0^{-1/2} I
+        if (!(A->c4[0] > 0.0)) return NC_ERR_ARG;
+        nc_matrix B = new (std::nothrow) nc_matrix_s(*A);
+        if (!B) return NC_ERR_OOM;
+        const double d = std::sqrt(A->c4[0]);
+        B->c4[0] = 1.0;
+        for (int i = 1; i < 4; ++i) B->c4[i] = A->c4[i] / A->c4[0];
+        B->dis_scalar = 1.0 / d;
+        B->scaled = true;
+        *out = B;
+        return NC_OK;
+    }
     cudaStream_t st = as_stream(stream);
     nc_matrix B = new (std::nothrow) nc_matrix_s(*A);
     if (!B) return NC_ERR_OOM;
@@ -575,6 +667,7 @@ nc_status nc_matrix_jacobi(nc_matrix A, void* stream, nc_matrix* out) {
         return s;
     }
     B->val = B->owned_val;
+    B->scaled = true;
     *out = B;
     return NC_OK;
 }
@@ -589,6 +682,13 @@ nc_status nc_matvec(nc_matrix A, const double* x_dev, double* y_dev, void* strea
 
 nc_status nc_gershgorin(nc_matrix A, void* stream, double* bound) {
     if (!A || !bound) return NC_ERR_ARG;
+    if (A->kind == MAT_STENCIL7) {   // the fullest row: |c0| + sum_a (neighbours along a) |c_a|
+        const int dims[3] = {A->geom.nx, A->geom.ny, A->geom.nz};
+        double g = std::fabs(A->c4[0]);
+        for (int a = 0; a < 3; ++a) g += (dims[a] >= 3 ? 2.0 : (dims[a] == 2 ? 1.0 : 0.0)) * std::fabs(A->c4[1 + a]);
+        *bound = g;
+        return NC_OK;
+    }
     cudaStream_t st = as_stream(stream);
     unsigned long long* d = nullptr;
     unsigned long long h = 0;
@@ -620,7 +720,7 @@ nc_status nc_bounds_lanczos(nc_matrix A, int steps, const double* v0_dev, void* 
     std::vector<double> al, be;
     do {
         if ((s = dev_alloc_n(&vp, n)) || (s = dev_alloc_n(&v, n)) || (s = dev_alloc_n(&w, n)) ||
-            (s = dev_alloc_n(&part, max_partials(n))) || (s = dev_alloc_n(&sc, 4)) ||
+            (s = dev_alloc_n(&part, partials_for(A))) || (s = dev_alloc_n(&sc, 4)) ||
             (s = dev_alloc_n(&cnt, 1)))
             break;
         cudaError_t e = cudaSuccess;
@@ -714,7 +814,6 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
     if (o.apply_dtype != NC_F64 && o.apply_dtype != NC_F32 && o.apply_dtype != NC_BF16) return NC_ERR_ARG;
     if (o.rr_period < 0) return NC_ERR_ARG;
     if (o.spmv_format < NC_FORMAT_AUTO || o.spmv_format > NC_FORMAT_SELL) return NC_ERR_ARG;
-    if (o.rr_period > 0) return NC_ERR_UNSUPPORTED;
     cudaStream_t st = as_stream(stream);
     nc_solver S = new (std::nothrow) nc_solver_s();
     if (!S) return NC_ERR_OOM;
@@ -733,7 +832,7 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
     do {
         if ((s = dev_alloc_n(&S->b, n)) || (s = dev_alloc_n(&S->x, n)) || (s = dev_alloc_n(&S->r, n)) ||
             (s = dev_alloc_n(&S->z, n)) || (s = dev_alloc_n(&S->p, n)) || (s = dev_alloc_n(&S->q, n)) ||
-            (s = dev_alloc_n(&S->partials, max_partials(n))) || (s = dev_alloc_n(&S->counter, 1)) ||
+            (s = dev_alloc_n(&S->partials, partials_for(A))) || (s = dev_alloc_n(&S->counter, 1)) ||
             (s = dev_alloc_n(&S->S, 1)))
             break;
         const size_t vb = S->mixed ? sizeof(float) : sizeof(double);
@@ -771,7 +870,7 @@ nc_status pcg_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
                     nc_result* res) {
     if (!S || !(tol >= 0.0) || maxit < 0) return NC_ERR_ARG;
     if (S->n == 0) {
-        if (res) *res = nc_result{0, NC_OK, 0.0, 0.0, 0, 0};
+        if (res) *res = nc_result{0, NC_OK, 0.0, 0.0, 0, 0, 0};
         return NC_OK;
     }
     if (!b_dev || !x_dev || b_dev == x_dev) return NC_ERR_ARG;
@@ -782,7 +881,7 @@ nc_status pcg_solve_host(nc_solver S, const double* b_host, double* x_host, doub
                          void* stream, nc_result* res) {
     if (!S || !(tol >= 0.0) || maxit < 0) return NC_ERR_ARG;
     if (S->n == 0) {
-        if (res) *res = nc_result{0, NC_OK, 0.0, 0.0, 0, 0};
+        if (res) *res = nc_result{0, NC_OK, 0.0, 0.0, 0, 0, 0};
         return NC_OK;
     }
     if (!b_host || !x_host) return NC_ERR_ARG;

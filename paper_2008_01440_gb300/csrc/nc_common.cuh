@@ -36,7 +36,9 @@ enum Fin : int {
 struct PcgScalars {
     double rz, pq, alpha, beta, rr, bb, tol2, rr_true;
     int iter, maxit, done, status;
-    int n_dot, n_prec, pad0, pad1;
+    int n_dot, n_prec, rr_period, rr_skip;   // residual replacement: period, and
+                                             // "skip it this iteration" flag
+    int n_replace, pad0, pad1, pad2;
 };
 
 struct Reduce {
@@ -53,13 +55,13 @@ struct Reduce {
 // The butterfly gives identical values in all lanes and a fixed order, so the
 // reduction is deterministic.
 template <int BS>
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ double block_sum(double v, double* sh, int tid) {
+    const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) sh[warp] = v;
     __syncthreads();
-    v = (threadIdx.x < BS / 32) ? sh[threadIdx.x] : 0.0;
+    v = (tid < BS / 32) ? sh[tid] : 0.0;
     if (warp == 0) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -102,6 +104,9 @@ __device__ __forceinline__ void finalize(const Reduce& R, double s) {
         if (!finite) { S->status = NC_ERR_BREAKDOWN; S->done = 1; }
         else if (s <= S->tol2 * S->bb) { S->status = NC_OK; S->done = 1; }
         else if (S->iter >= S->maxit) { S->status = NC_ERR_MAXIT; S->done = 1; }
+        // residual replacement r = b - A x after every rr_period-th iteration
+        S->rr_skip = S->done || S->rr_period <= 0 || (S->iter % S->rr_period) != 0;
+        if (!S->rr_skip) S->n_replace += 1;
         break;
     case FIN_BETA:
         S->n_dot += 1; S->n_prec += 1;
@@ -120,27 +125,33 @@ __device__ __forceinline__ void finalize(const Reduce& R, double s) {
 // the per-CTA partials in a fixed order and applies R.fin.  Must be reached
 // by every thread of every CTA of the grid.
 template <int BS>
-__device__ __forceinline__ void grid_reduce(double v, const Reduce& R) {
+__device__ __forceinline__ void grid_reduce_ex(double v, const Reduce& R, int bid, int nblocks) {
     __shared__ double sh[32];
     __shared__ int is_last;
-    v = block_sum<BS>(v, sh);
-    if (threadIdx.x == 0) {
-        R.partials[blockIdx.x] = v;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    v = block_sum<BS>(v, sh, tid);
+    if (tid == 0) {
+        R.partials[bid] = v;
         __threadfence();
         const unsigned int t = atomicAdd(R.counter, 1u);
-        is_last = (t == gridDim.x - 1);
+        is_last = (t == (unsigned int)nblocks - 1u);
     }
     __syncthreads();
     if (is_last) {
         __threadfence();
         double s = 0.0;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += BS) s += __ldcg(&R.partials[i]);
-        s = block_sum<BS>(s, sh);
-        if (threadIdx.x == 0) {
+        for (int i = tid; i < nblocks; i += BS) s += __ldcg(&R.partials[i]);
+        s = block_sum<BS>(s, sh, tid);
+        if (tid == 0) {
             finalize(R, s);
             *R.counter = 0u;
         }
     }
+}
+
+template <int BS>
+__device__ __forceinline__ void grid_reduce(double v, const Reduce& R) {
+    grid_reduce_ex<BS>(v, R, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // ---- host-side launchers (defined in nc_csr.cu / nc_vec.cu) ---------------
@@ -170,6 +181,17 @@ cudaError_t launch_sell_fill(int n, const int32_t* rowptr, const int32_t* col, c
                              const int32_t* slice_ptr, int vdt, double shift, int32_t* scol, void* sval,
                              int* nodiag, cudaStream_t st);
 
+// Matrix-free 7-point stencil (c4 = {c0, cx, cy, cz}, host array).
+struct StencilGeom {
+    int nx, ny, nz;
+};
+int stencil_zchunk(const StencilGeom& g);
+dim3 stencil_grid(const StencilGeom& g);
+long long stencil_nblocks(const StencilGeom& g);
+cudaError_t launch_stencil_step(const StencilGeom& g, const double* c4, bool x_f32, bool y_f64, const void* u,
+                                const void* w, const void* r, void* y, double ca, double cb, double cc, double cd,
+                                int dot, const double* rdot, const Reduce& R, const int* done, cudaStream_t st);
+
 cudaError_t launch_csr_diag(int n, const int32_t* rowptr, const int32_t* col, const double* val,
                             double* dis, int* bad, cudaStream_t st);
 cudaError_t launch_csr_scale(int n, const int32_t* rowptr, const int32_t* col, const double* val,
@@ -194,15 +216,17 @@ cudaError_t launch_dot(int n, const double* a, const double* b, const Reduce& R,
                        cudaStream_t st);
 // y = x (skip if *done)
 cudaError_t launch_copy(int n, const double* x, double* y, const int* done, cudaStream_t st);
-// b_s = dis .* b (or b); x_s = 0 if zero else x ./ dis (or x)
-cudaError_t launch_copy_in(int n, const double* b, const double* x, const double* dis, int zero,
+// b_s = d .* b; x_s = 0 if zero else x ./ d, with d = dis (vector) or ds (constant)
+cudaError_t launch_copy_in(int n, const double* b, const double* x, const double* dis, double ds, int zero,
                            double* bs, double* xs, cudaStream_t st);
-// x = dis .* x_s (or x_s); x = 0 when S->bb == 0
-cudaError_t launch_copy_out(int n, const double* xs, const double* dis, const PcgScalars* S,
+// x = d .* x_s; x = 0 when S->bb == 0
+cudaError_t launch_copy_out(int n, const double* xs, const double* dis, double ds, const PcgScalars* S,
                             double* x, cudaStream_t st);
 // y = y + a x and (y, y) -> R
 cudaError_t launch_axpy_dot(int n, double a, const double* x, double* y, const Reduce& R,
                             cudaStream_t st);
+// r32 = (float) r unless *skip
+cudaError_t launch_refresh_r32(int n, const double* r, float* r32, const int* skip, cudaStream_t st);
 // y = x / d
 cudaError_t launch_div(int n, const double* x, double d, double* y, cudaStream_t st);
 

@@ -1,0 +1,152 @@
+// Matrix-free 7-point stencil: the fused Chebyshev step with no matrix in
+// memory (Sec. 1: polynomial preconditioners need only v -> A v; Sec. 5.3's
+// FD-3D Poisson operator).
+//
+//   (A u)_p = c0 u_p - cx (u_{p-ex} + u_{p+ex}) - cy (...) - cz (...),
+//   zero Dirichlet halo, unknown (i, j, k) at i + nx (j + ny k).
+//
+// One Chebyshev step y = ca u + cb w + cc r + cd A u becomes
+//   y = e0 u + ex (u_{i-1} + u_{i+1}) + ey (u_{j-1} + u_{j+1})
+//            + ez (u_{k-1} + u_{k+1}) + cb w + cc r,
+// e0 = ca + cd c0, e_a = -cd c_a (the x_{k-1} term folds into the centre
+// coefficient for free).
+//
+// Layout: a CTA owns a 32 x 8 tile of an (x, y) plane and marches along z
+// over a chunk of planes, keeping u at planes k-1, k, k+1 in registers, so
+// every u value is read from memory once per chunk.  x-neighbours come from
+// the adjacent lanes by warp shuffle (lane 0 and 31 read across the tile
+// edge), y-neighbours through the read-only cache (the adjacent warps loaded
+// them as their own centre values).  Each point reads u, w, r and writes y
+// once: 4 vector accesses, the minimum.
+#include "nc_step.cuh"
+
+namespace nc {
+namespace {
+
+constexpr int kTX = 32, kTY = 8;
+
+template <typename AT>
+struct StencilCoef {
+    AT e0, ex, ey, ez, cb, cc;
+    int terms;   // kTermW / kTermR
+};
+
+template <typename XT, typename YT, int DOT>
+__global__ void __launch_bounds__(kTX * kTY)
+stencil7_step_kernel(const int nx, const int ny, const int nz, const int zchunk, const XT* __restrict__ u,
+                     const XT* __restrict__ w, const XT* __restrict__ r, YT* __restrict__ y,
+                     const StencilCoef<typename AccOf<XT>::type> c, const double* __restrict__ rdot,
+                     const Reduce R, const int* __restrict__ done) {
+    using AT = typename AccOf<XT>::type;
+    if (done != nullptr && *done) return;
+    const int lane = threadIdx.x;
+    const int i = blockIdx.x * kTX + lane;
+    const int j = blockIdx.y * kTY + threadIdx.y;
+    const int k0 = blockIdx.z * zchunk;
+    const int k1 = min(k0 + zchunk, nz);
+    const bool in = i < nx && j < ny;
+    const long long plane = (long long)nx * ny;
+    long long idx = ((long long)k0 * ny + j) * nx + i;
+    const AT zero = AT(0);
+    AT u_prev = (in && k0 > 0) ? (AT)__ldg(u + idx - plane) : zero;
+    AT u_cur = (in && k0 < nz) ? (AT)__ldg(u + idx) : zero;
+    double dv = 0.0;
+    for (int k = k0; k < k1; ++k) {
+        const AT u_next = (in && k + 1 < nz) ? (AT)__ldg(u + idx + plane) : zero;
+        AT xm = __shfl_up_sync(0xffffffffu, u_cur, 1);
+        AT xp = __shfl_down_sync(0xffffffffu, u_cur, 1);
+        if (lane == 0) xm = (in && i > 0) ? (AT)__ldg(u + idx - 1) : zero;
+        if (lane == kTX - 1) xp = (in && i + 1 < nx) ? (AT)__ldg(u + idx + 1) : zero;
+        if (in) {
+            const AT ym = j > 0 ? (AT)__ldg(u + idx - nx) : zero;
+            const AT yp = j + 1 < ny ? (AT)__ldg(u + idx + nx) : zero;
+            AT o = c.e0 * u_cur;
+            o = fma(c.ex, xm + xp, o);
+            o = fma(c.ey, ym + yp, o);
+            o = fma(c.ez, u_prev + u_next, o);
+            if (c.terms & kTermR) o = fma(c.cc, (AT)r[idx], o);
+            if (c.terms & kTermW) o = fma(c.cb, (AT)w[idx], o);
+            const YT yo = (YT)o;
+            y[idx] = yo;
+            if (DOT == 1) dv += rdot[idx] * (double)yo;
+            if (DOT == 2) dv += (double)u_cur * (double)yo;
+        }
+        u_prev = u_cur;
+        u_cur = u_next;
+        idx += plane;
+    }
+    if (DOT != 0) {
+        const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+        const int nb = gridDim.x * gridDim.y * gridDim.z;
+        grid_reduce_ex<kTX * kTY>(dv, R, bid, nb);
+    }
+}
+
+template <typename XT, typename YT>
+cudaError_t stencil_dispatch(const StencilGeom& g, const double* c4, const void* u, const void* w, const void* r,
+                             void* y, double ca, double cb, double cc, double cd, int dot, const double* rdot,
+                             const Reduce& R, const int* done, cudaStream_t st) {
+    using AT = typename AccOf<XT>::type;
+    StencilCoef<AT> c;
+    c.e0 = (AT)(ca + cd * c4[0]);
+    c.ex = (AT)(-cd * c4[1]);
+    c.ey = (AT)(-cd * c4[2]);
+    c.ez = (AT)(-cd * c4[3]);
+    c.cb = (AT)cb;
+    c.cc = (AT)cc;
+    c.terms = (cb != 0.0 ? kTermW : 0) | (cc != 0.0 ? kTermR : 0);
+    const dim3 grid = stencil_grid(g);
+    const dim3 block(kTX, kTY);
+    const int zc = stencil_zchunk(g);
+    const XT* uu = static_cast<const XT*>(u);
+    const XT* ww = static_cast<const XT*>(w);
+    const XT* rr = static_cast<const XT*>(r);
+    YT* yy = static_cast<YT*>(y);
+    switch (dot) {
+    case 0:
+        stencil7_step_kernel<XT, YT, 0><<<grid, block, 0, st>>>(g.nx, g.ny, g.nz, zc, uu, ww, rr, yy, c, rdot, R, done);
+        break;
+    case 1:
+        stencil7_step_kernel<XT, YT, 1><<<grid, block, 0, st>>>(g.nx, g.ny, g.nz, zc, uu, ww, rr, yy, c, rdot, R, done);
+        break;
+    default:
+        stencil7_step_kernel<XT, YT, 2><<<grid, block, 0, st>>>(g.nx, g.ny, g.nz, zc, uu, ww, rr, yy, c, rdot, R, done);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// z-chunk length: enough CTAs to fill the GPU about twice (8 resident CTAs of
+// 256 threads per SM), chunks of at least 4 planes so the two extra plane
+// loads at a chunk's start stay a small overhead.
+int stencil_zchunk(const StencilGeom& g) {
+    const long long tiles = (long long)((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY);
+    const long long want_chunks = (2LL * kSMs * 8 + tiles - 1) / tiles;
+    long long zc = (g.nz + want_chunks - 1) / (want_chunks > 0 ? want_chunks : 1);
+    if (zc < 4) zc = 4;
+    if (zc > g.nz) zc = g.nz > 0 ? g.nz : 1;
+    return (int)zc;
+}
+
+dim3 stencil_grid(const StencilGeom& g) {
+    const int zc = stencil_zchunk(g);
+    return dim3((g.nx + kTX - 1) / kTX, (g.ny + kTY - 1) / kTY, (g.nz + zc - 1) / zc);
+}
+
+long long stencil_nblocks(const StencilGeom& g) {
+    const dim3 d = stencil_grid(g);
+    return (long long)d.x * d.y * d.z;
+}
+
+cudaError_t launch_stencil_step(const StencilGeom& g, const double* c4, bool x_f32, bool y_f64, const void* u,
+                                const void* w, const void* r, void* y, double ca, double cb, double cc, double cd,
+                                int dot, const double* rdot, const Reduce& R, const int* done, cudaStream_t st) {
+    if ((long long)g.nx * g.ny * g.nz <= 0) return cudaSuccess;
+    if (!x_f32) return stencil_dispatch<double, double>(g, c4, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done, st);
+    if (y_f64) return stencil_dispatch<float, double>(g, c4, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done, st);
+    return stencil_dispatch<float, float>(g, c4, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done, st);
+}
+
+}  // namespace nc

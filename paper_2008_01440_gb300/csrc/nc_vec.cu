@@ -68,20 +68,23 @@ __global__ void copy_kernel(int n, const double* __restrict__ x, double* __restr
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = x[i];
 }
 
+// The scaling is a vector d^{-1/2} (dis) or, when dis is null, the constant ds
+// (1 for an unscaled matrix: the copies are then exact).
 __global__ void copy_in_kernel(int n, const double* __restrict__ b, const double* __restrict__ x,
-                               const double* __restrict__ dis, int zero, double* __restrict__ bs,
+                               const double* __restrict__ dis, double ds, int zero, double* __restrict__ bs,
                                double* __restrict__ xs) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        bs[i] = dis ? b[i] * dis[i] : b[i];
-        xs[i] = zero ? 0.0 : (dis ? x[i] / dis[i] : x[i]);
+        const double d = dis ? dis[i] : ds;
+        bs[i] = b[i] * d;
+        xs[i] = zero ? 0.0 : x[i] / d;
     }
 }
 
-__global__ void copy_out_kernel(int n, const double* __restrict__ xs, const double* __restrict__ dis,
+__global__ void copy_out_kernel(int n, const double* __restrict__ xs, const double* __restrict__ dis, double ds,
                                 const PcgScalars* __restrict__ S, double* __restrict__ x) {
     const bool zero = S->bb == 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        x[i] = zero ? 0.0 : (dis ? xs[i] * dis[i] : xs[i]);
+        x[i] = zero ? 0.0 : xs[i] * (dis ? dis[i] : ds);
 }
 
 __global__ void __launch_bounds__(kBlock)
@@ -93,6 +96,12 @@ axpy_dot_kernel(int n, double a, const double* __restrict__ x, double* __restric
         acc = fma(yi, yi, acc);
     }
     grid_reduce<kBlock>(acc, R);
+}
+
+__global__ void refresh_r32_kernel(int n, const double* __restrict__ r, float* __restrict__ r32,
+                                   const int* __restrict__ skip) {
+    if (*skip) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r32[i] = (float)r[i];
 }
 
 __global__ void div_kernel(int n, const double* __restrict__ x, double d, double* __restrict__ y) {
@@ -135,21 +144,26 @@ cudaError_t launch_copy(int n, const double* x, double* y, const int* done, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_copy_in(int n, const double* b, const double* x, const double* dis, int zero,
+cudaError_t launch_copy_in(int n, const double* b, const double* x, const double* dis, double ds, int zero,
                            double* bs, double* xs, cudaStream_t st) {
-    copy_in_kernel<<<vec_grid(n), kBlock, 0, st>>>(n, b, x, dis, zero, bs, xs);
+    copy_in_kernel<<<vec_grid(n), kBlock, 0, st>>>(n, b, x, dis, ds, zero, bs, xs);
     return cudaGetLastError();
 }
 
-cudaError_t launch_copy_out(int n, const double* xs, const double* dis, const PcgScalars* S,
+cudaError_t launch_copy_out(int n, const double* xs, const double* dis, double ds, const PcgScalars* S,
                             double* x, cudaStream_t st) {
-    copy_out_kernel<<<vec_grid(n), kBlock, 0, st>>>(n, xs, dis, S, x);
+    copy_out_kernel<<<vec_grid(n), kBlock, 0, st>>>(n, xs, dis, ds, S, x);
     return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_dot(int n, double a, const double* x, double* y, const Reduce& R,
                             cudaStream_t st) {
     axpy_dot_kernel<<<vec_grid(n), kBlock, 0, st>>>(n, a, x, y, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_r32(int n, const double* r, float* r32, const int* skip, cudaStream_t st) {
+    refresh_r32_kernel<<<vec_grid(n), kBlock, 0, st>>>(n, r, r32, skip);
     return cudaGetLastError();
 }
 

@@ -326,3 +326,25 @@ def test_mixed_precision_apply_and_solve(env, dt, tol_apply, fmt):
     x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
     res = nc.pcg_solve(S, to_dev(torch, b), x, 1e-8, 2000)
     assert res["status"] == 0 and res["relres"] <= 1e-8 and res["true_relres"] <= 1e-7
+
+
+@pytest.mark.parametrize("dt,period", [("f64", 5), ("f32", 5), ("f32", 50), ("bf16", 7)])
+def test_residual_replacement(env, dt, period):
+    """FP64 residual replacement every `period` iterations (the mixed-precision
+    safeguard): same iteration count as the FP64 oracle with the same
+    replacement schedule (within +-1 for f64, 10% for reduced precision)."""
+    torch, nc = env
+    A = W.diffusion_3d_7pt_lognormal(32, seed=11)
+    As, dis = scaled(A)
+    mv = O.csr_matvec(As.rowptr, As.col, As.val, A.n)
+    lo, hi, _ = O.lanczos_bounds(mv, W.uniform_vector(A.n, seed=3), 20,
+                                 gershgorin=gershgorin_np(As.rowptr, As.col, As.val, A.n))
+    b = W.uniform_vector(A.n, seed=5)
+    k = 10
+    res, ro, x, xo = _solve_both(torch, nc, A, lo, hi, k, 1.001, b, jacobi=True, apply_dtype=dt, rr_period=period)
+    ro2 = O.pcg(mv, dis * b, lambda r: O.cheb_apply(mv, r, O.cheb_params(lo, hi, 1.001), k), m=k, tol=1e-8,
+                rr_period=period)
+    assert res["status"] == 0 and res["true_relres"] <= 2e-8
+    tol_it = 1 if dt == "f64" else max(2, 0.1 * ro2.iters)
+    assert abs(res["iters"] - ro2.iters) <= tol_it
+    assert res["n_replace"] == (res["iters"] - 1) // period

@@ -101,6 +101,24 @@ def test_scaled_theta_beats_exact_at_high_degree():
         assert it[1] < it[0]
 
 
+@pytest.mark.parametrize("period", [1, 3, 10])
+def test_residual_replacement_is_a_no_op_in_exact_arithmetic(period):
+    """Replacing r by b - A x changes nothing in exact arithmetic: iterations
+    and solution agree with the plain recurrence to rounding."""
+    A = W.diffusion_3d_7pt_lognormal(16, seed=2)
+    val, _ = O.jacobi_scale_csr(A.rowptr, A.col, A.val, A.n)
+    mv = O.csr_matvec(A.rowptr, A.col, val, A.n)
+    lo, hi, _ = O.lanczos_bounds(mv, W.uniform_vector(A.n, seed=1), 20)
+    prm = O.cheb_params(lo, hi, 1.001)
+    b = W.uniform_vector(A.n, seed=3)
+    pc = lambda r: O.cheb_apply(mv, r, prm, 6)  # noqa: E731
+    r0 = O.pcg(mv, b, pc, m=6, tol=1e-10)
+    r1 = O.pcg(mv, b, pc, m=6, tol=1e-10, rr_period=period)
+    assert abs(r0.iters - r1.iters) <= 1
+    assert np.linalg.norm(r0.x - r1.x) <= 1e-8 * np.linalg.norm(r0.x)
+    assert r1.true_relres <= 2e-10
+
+
 def test_pcg_zero_rhs_and_initial_guess():
     A, lam = spd(10, 10.0, seed=1)
     mv = lambda u: A @ u  # noqa: E731
