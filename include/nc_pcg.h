@@ -57,9 +57,10 @@ typedef enum {
 typedef enum { NC_F64 = 0, NC_F32 = 1, NC_BF16 = 2 } nc_dtype;
 
 /* Layout the solver's product kernels read (built once by pcg_setup).
- * SELL: slices of 32 rows stored slot-major, rows padded to the slice's
- * longest row (coalesced thread-per-row access); AUTO picks SELL when the
- * padding is at most 1.5x the nonzeros, else CSR. */
+ * SELL: slices of 32 rows (block rows for BSR3) stored slot-major, rows
+ * padded to the slice's longest row (coalesced thread-per-row access); AUTO
+ * picks SELL when the padding is at most 1.5x the nonzeros, else CSR (plain
+ * block CSR for BSR3).  Stencil handles ignore the option. */
 typedef enum { NC_FORMAT_AUTO = 0, NC_FORMAT_CSR = 1, NC_FORMAT_SELL = 2 } nc_format;
 
 typedef struct {
@@ -122,6 +123,15 @@ NC_API const char* nc_last_cuda_error(void);
  * nnz < 0, nnz >= 2^31 or a null pointer with n > 0. */
 NC_API nc_status nc_matrix_csr(int64_t n, int64_t nnz, const int32_t* rowptr_dev,
                         const int32_t* col_dev, const double* val_dev, nc_matrix* out);
+
+/* 3x3-block CSR, float64 values (three dofs per node, as in the paper's
+ * finite-element structural matrices, Sec. 5).  browptr_dev: nb+1 int32
+ * block-row pointers; bcol_dev: nnzb int32 block columns in [0, nb); val_dev:
+ * 9*nnzb float64, block p's entry (r, c) at val[9p + 3r + c].  Scalar
+ * unknown 3*node + component; n = 3*nb.  Borrowed.  NC_ERR_ARG on negative
+ * sizes, 3*nb or nnzb >= 2^31, or a null pointer with nb > 0. */
+NC_API nc_status nc_matrix_bsr3(int64_t nb, int64_t nnzb, const int32_t* browptr_dev, const int32_t* bcol_dev,
+                                const double* val_dev, nc_matrix* out);
 
 /* Matrix-free constant-coefficient 7-point operator on an nx x ny x nz grid
  * (Sec. 1: only v -> A v is needed; Sec. 5.3: FD-3D Poisson), zero

@@ -36,6 +36,7 @@ from .binding import (  # noqa: F401
     nc_apply_poly_noalloc_max_n,
     nc_bounds_lanczos,
     nc_gershgorin,
+    nc_matrix_bsr3,
     nc_matrix_csr,
     nc_matrix_destroy,
     nc_matrix_jacobi,

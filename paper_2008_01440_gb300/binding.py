@@ -66,6 +66,7 @@ _SIGS = {
     "nc_last_cuda_error": (ctypes.c_char_p, []),
     "nc_matrix_csr": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "nc_matrix_jacobi": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "nc_matrix_bsr3": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "nc_matrix_stencil7": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dbl, _dbl, _dbl, _dbl,
                                           ctypes.POINTER(_vp)]),
     "nc_matvec": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -177,6 +178,17 @@ def nc_matrix_csr(rowptr, col, val) -> Matrix:
                              _ptr(col, torch.int32, what="col"), _ptr(val, torch.float64, nnz, "val"),
                              ctypes.byref(h)), "nc_matrix_csr")
     return Matrix(h.value, n, (rowptr, col, val))
+
+
+def nc_matrix_bsr3(browptr, bcol, val) -> Matrix:
+    """val: float64, 9 entries per block (row-major 3x3), shape (nnzb, 3, 3) or flat."""
+    import torch
+    nb = browptr.numel() - 1
+    nnzb = bcol.numel()
+    h = _vp()
+    _check(lib.nc_matrix_bsr3(nb, nnzb, _ptr(browptr, torch.int32, what="browptr"), _ptr(bcol, torch.int32, what="bcol"),
+                              _ptr(val, torch.float64, 9 * nnzb, "val"), ctypes.byref(h)), "nc_matrix_bsr3")
+    return Matrix(h.value, 3 * nb, (browptr, bcol, val))
 
 
 def nc_matrix_stencil7(nx: int, ny: int, nz: int, c0: float, cx: float, cy: float, cz: float) -> Matrix:

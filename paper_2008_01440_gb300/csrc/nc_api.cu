@@ -19,14 +19,14 @@
 
 using namespace nc;
 
-enum MatKind : int { MAT_CSR = 0, MAT_STENCIL7 = 1 };
+enum MatKind : int { MAT_CSR = 0, MAT_STENCIL7 = 1, MAT_BSR3 = 2 };
 
 struct nc_matrix_s {
     int kind = MAT_CSR;
     int64_t n = 0, nnz = 0;
-    const int32_t* rowptr = nullptr;
-    const int32_t* col = nullptr;
-    const double* val = nullptr;    // values used by products (borrowed or owned_val)
+    const int32_t* rowptr = nullptr;   // CSR row pointers, or BSR3 block-row pointers
+    const int32_t* col = nullptr;      // CSR columns, or BSR3 block columns
+    const double* val = nullptr;    // values used by products (borrowed or owned_val); BSR3: 9 per block
     double* owned_val = nullptr;    // scaled copy (nc_matrix_jacobi)
     double* dis = nullptr;          // d^{-1/2} of the scaling, owned (CSR)
     bool scaled = false;            // built by nc_matrix_jacobi
@@ -37,7 +37,7 @@ struct nc_matrix_s {
 
 // A matrix as the step kernels see it: CSR (the handle's arrays) or the
 // solver-owned SELL-32 layout, with float64 or low-precision values.
-enum OpKind : int { OP_CSR = 0, OP_SELL = 1, OP_STENCIL = 2 };
+enum OpKind : int { OP_CSR = 0, OP_SELL = 1, OP_STENCIL = 2, OP_BSR3 = 3, OP_BSELL3 = 4 };
 struct OpView {
     int kind = OP_CSR;
     int n = 0;
@@ -150,6 +150,11 @@ OpView mat_view(nc_matrix A) {
         v.kind = OP_STENCIL;
         v.geom = A->geom;
         for (int i = 0; i < 4; ++i) v.c4[i] = A->c4[i];
+    } else if (A->kind == MAT_BSR3) {
+        v.kind = OP_BSR3;
+        v.ptr = A->rowptr;
+        v.col = A->col;
+        v.val = A->val;
     } else {
         v.kind = OP_CSR;
         v.ptr = A->rowptr;
@@ -179,6 +184,9 @@ cudaError_t op_step(const OpView& op, bool x_f32, bool y_f64, const void* u, con
     if (op.kind == OP_STENCIL)
         return launch_stencil_step(op.geom, op.c4, x_f32, y_f64, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done,
                                    st);
+    if (op.kind == OP_BSR3 || op.kind == OP_BSELL3)
+        return launch_bsr3_step(op.kind == OP_BSELL3, op.n / 3, op.ptr, op.col, op.val, op.vdt, x_f32, y_f64, u, w,
+                                r, y, ca, cb, cc, cd, dot, rdot, R, done, st);
     return launch_csr_step(op.n, op.ptr, op.col, op.val, op.vdt, x_f32, y_f64, u, w, r, y, ca, cb, cc, cd, dot,
                            rdot, R, done, st);
 }
@@ -450,6 +458,94 @@ nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
 // padding is at most kSellMaxPadding (or when forced), else the CSR arrays.
 constexpr double kSellMaxPadding = 1.5;
 
+// Block counterpart of the SELL setup: BSELL-32 over block rows when its
+// padding is at most kSellMaxPadding (or forced), else the plain block CSR.
+nc_status setup_operator_bsr3(nc_solver S, cudaStream_t st, size_t eb) {
+    nc_matrix A = S->A;
+    const int nb = (int)(A->n / 3);
+    const int n = (int)A->n;
+    bool sliced = S->opt.spmv_format != NC_FORMAT_CSR && nb > 0;
+    std::vector<int64_t> hptr;
+    if (sliced) {
+        const int nslices = (nb + 31) / 32;
+        int32_t* dlen = nullptr;
+        NC_TRY(dev_alloc_n(&dlen, nslices));
+        std::vector<int32_t> hlen(nslices);
+        cudaError_t e;
+        if ((e = launch_bsell3_lengths(nb, A->rowptr, dlen, st)) ||
+            (e = cudaMemcpyAsync(hlen.data(), dlen, sizeof(int32_t) * nslices, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st))) {
+            dev_free(dlen);
+            g_last_cuda = e;
+            return NC_ERR_CUDA;
+        }
+        dev_free(dlen);
+        hptr.resize(nslices + 1);
+        hptr[0] = 0;
+        for (int i = 0; i < nslices; ++i) hptr[i + 1] = hptr[i] + 32 * (int64_t)hlen[i];
+        S->padding = A->nnz > 0 ? (double)hptr[nslices] / (double)A->nnz : 1.0;
+        if (hptr[nslices] >= ((int64_t)1 << 31)) sliced = false;
+        if (S->opt.spmv_format == NC_FORMAT_AUTO && S->padding > kSellMaxPadding) sliced = false;
+    }
+    if (!sliced) {
+        S->padding = 1.0;
+        S->shift = 0.0;
+        S->op64 = OpView{OP_BSR3, n, A->rowptr, A->col, A->val, NC_F64};
+        S->opP = S->op64;
+        if (S->mixed) {
+            NC_TRY(dev_alloc(&S->lval, eb * 9 * (size_t)(A->nnz > 0 ? A->nnz : 1)));
+            cudaError_t e = launch_convert(9 * A->nnz, A->val, S->vdt, S->lval, st);
+            if (e) { g_last_cuda = e; return NC_ERR_CUDA; }
+            S->opP = OpView{OP_BSR3, n, A->rowptr, A->col, S->lval, S->vdt};
+        }
+        return NC_OK;
+    }
+    const int nslices = (nb + 31) / 32;
+    const int64_t total = hptr[nslices];
+    std::vector<int32_t> hp32(nslices + 1);
+    for (int i = 0; i <= nslices; ++i) hp32[i] = (int32_t)hptr[i];
+    NC_TRY(dev_alloc_n(&S->sell_ptr, nslices + 1));
+    NC_TRY(dev_alloc_n(&S->sell_col, total));
+    NC_TRY(dev_alloc_n(&S->sell_val64, 9 * total));
+    int* nodiag = nullptr;
+    NC_TRY(dev_alloc_n(&nodiag, 1));
+    int h_nodiag = 0;
+    S->shift = S->k >= 1 ? S->theta : 0.0;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(nodiag, 0, sizeof(int), st)) ||
+        (e = cudaMemcpyAsync(S->sell_ptr, hp32.data(), sizeof(int32_t) * (nslices + 1), cudaMemcpyHostToDevice, st)) ||
+        (e = launch_bsell3_fill(nb, A->rowptr, A->col, A->val, S->sell_ptr, NC_F64, S->shift, S->sell_col,
+                                S->sell_val64, nodiag, st)) ||
+        (e = cudaMemcpyAsync(&h_nodiag, nodiag, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st))) {
+        dev_free(nodiag);
+        g_last_cuda = e;
+        return NC_ERR_CUDA;
+    }
+    dev_free(nodiag);
+    if (h_nodiag) {
+        S->shift = 0.0;
+        if ((e = launch_bsell3_fill(nb, A->rowptr, A->col, A->val, S->sell_ptr, NC_F64, 0.0, S->sell_col,
+                                    S->sell_val64, nullptr, st))) {
+            g_last_cuda = e;
+            return NC_ERR_CUDA;
+        }
+    }
+    S->op64 = OpView{OP_BSELL3, n, S->sell_ptr, S->sell_col, S->sell_val64, NC_F64};
+    S->opP = S->op64;
+    if (S->mixed) {
+        NC_TRY(dev_alloc(&S->sell_valP, eb * 9 * (size_t)total));
+        if ((e = launch_bsell3_fill(nb, A->rowptr, A->col, A->val, S->sell_ptr, S->vdt, S->shift, S->sell_col,
+                                    S->sell_valP, nullptr, st))) {
+            g_last_cuda = e;
+            return NC_ERR_CUDA;
+        }
+        S->opP = OpView{OP_BSELL3, n, S->sell_ptr, S->sell_col, S->sell_valP, S->vdt};
+    }
+    if ((e = cudaStreamSynchronize(st))) { g_last_cuda = e; return NC_ERR_CUDA; }
+    return NC_OK;
+}
+
 nc_status setup_operator(nc_solver S, cudaStream_t st) {
     nc_matrix A = S->A;
     const int n = (int)S->n;
@@ -462,6 +558,7 @@ nc_status setup_operator(nc_solver S, cudaStream_t st) {
         return NC_OK;
     }
     const size_t eb = S->vdt == NC_F64 ? 8 : (S->vdt == NC_F32 ? 4 : 2);
+    if (A->kind == MAT_BSR3) return setup_operator_bsr3(S, st, eb);
     bool sell = S->opt.spmv_format != NC_FORMAT_CSR && n > 0;
     std::vector<int64_t> hptr;
     if (sell) {
@@ -598,6 +695,24 @@ nc_status nc_matrix_csr(int64_t n, int64_t nnz, const int32_t* rowptr_dev, const
     return NC_OK;
 }
 
+nc_status nc_matrix_bsr3(int64_t nb, int64_t nnzb, const int32_t* browptr_dev, const int32_t* bcol_dev,
+                         const double* val_dev, nc_matrix* out) {
+    if (!out) return NC_ERR_ARG;
+    *out = nullptr;
+    if (nb < 0 || nnzb < 0 || 3 * nb >= ((int64_t)1 << 31) || nnzb >= ((int64_t)1 << 31)) return NC_ERR_ARG;
+    if (nb > 0 && (!browptr_dev || (nnzb > 0 && (!bcol_dev || !val_dev)))) return NC_ERR_ARG;
+    nc_matrix A = new (std::nothrow) nc_matrix_s();
+    if (!A) return NC_ERR_OOM;
+    A->kind = MAT_BSR3;
+    A->n = 3 * nb;
+    A->nnz = nnzb;
+    A->rowptr = browptr_dev;
+    A->col = bcol_dev;
+    A->val = val_dev;
+    *out = A;
+    return NC_OK;
+}
+
 nc_status nc_matrix_stencil7(int nx, int ny, int nz, double c0, double cx, double cy, double cz, nc_matrix* out) {
     if (!out) return NC_ERR_ARG;
     *out = nullptr;
@@ -643,14 +758,18 @@ nc_status nc_matrix_jacobi(nc_matrix A, void* stream, nc_matrix* out) {
     int* bad = nullptr;
     int h_bad = 0;
     nc_status s = NC_OK;
+    const bool bsr = A->kind == MAT_BSR3;
+    const int nb = (int)(A->n / 3);
     do {
         if ((s = dev_alloc_n(&B->dis, A->n)) != NC_OK) break;
-        if ((s = dev_alloc_n(&B->owned_val, A->nnz)) != NC_OK) break;
+        if ((s = dev_alloc_n(&B->owned_val, (bsr ? 9 : 1) * A->nnz)) != NC_OK) break;
         if ((s = dev_alloc_n(&bad, 1)) != NC_OK) break;
         cudaError_t e;
         if ((e = cudaMemsetAsync(bad, 0, sizeof(int), st)) ||
-            (e = launch_csr_diag((int)A->n, A->rowptr, A->col, A->val, B->dis, bad, st)) ||
-            (e = launch_csr_scale((int)A->n, A->rowptr, A->col, A->val, B->dis, B->owned_val, st)) ||
+            (e = bsr ? launch_bsr3_diag(nb, A->rowptr, A->col, A->val, B->dis, bad, st)
+                     : launch_csr_diag((int)A->n, A->rowptr, A->col, A->val, B->dis, bad, st)) ||
+            (e = bsr ? launch_bsr3_scale(nb, A->rowptr, A->col, A->val, B->dis, B->owned_val, st)
+                     : launch_csr_scale((int)A->n, A->rowptr, A->col, A->val, B->dis, B->owned_val, st)) ||
             (e = cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
             (e = cudaStreamSynchronize(st))) {
             g_last_cuda = e;
@@ -695,7 +814,8 @@ nc_status nc_gershgorin(nc_matrix A, void* stream, double* bound) {
     NC_TRY(dev_alloc_n(&d, 1));
     cudaError_t e;
     if ((e = cudaMemsetAsync(d, 0, sizeof(*d), st)) ||
-        (e = launch_csr_gershgorin((int)A->n, A->rowptr, A->val, d, st)) ||
+        (e = A->kind == MAT_BSR3 ? launch_bsr3_gershgorin((int)(A->n / 3), A->rowptr, A->val, d, st)
+                                 : launch_csr_gershgorin((int)A->n, A->rowptr, A->val, d, st)) ||
         (e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st)) ||
         (e = cudaStreamSynchronize(st))) {
         g_last_cuda = e;
@@ -902,7 +1022,7 @@ nc_status pcg_get_info(nc_solver S, nc_solver_info* info) {
     if (!S || !info) return NC_ERR_ARG;
     info->n = S->n;
     info->degree_k = S->k;
-    info->spmv_format = S->op64.kind == OP_SELL ? NC_FORMAT_SELL : NC_FORMAT_CSR;
+    info->spmv_format = (S->op64.kind == OP_SELL || S->op64.kind == OP_BSELL3) ? NC_FORMAT_SELL : NC_FORMAT_CSR;
     info->apply_dtype = S->vdt;
     info->padding = S->padding;
     info->theta = S->theta;

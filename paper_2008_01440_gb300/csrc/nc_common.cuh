@@ -192,6 +192,23 @@ cudaError_t launch_stencil_step(const StencilGeom& g, const double* c4, bool x_f
                                 const void* w, const void* r, void* y, double ca, double cb, double cc, double cd,
                                 int dot, const double* rdot, const Reduce& R, const int* done, cudaStream_t st);
 
+// 3x3-block matrices: plain block CSR (sliced = false, ptr = block row
+// pointers) or BSELL-32 (sliced = true, ptr = slice pointers in blocks).
+cudaError_t launch_bsr3_step(bool sliced, int nb, const int32_t* ptr, const int32_t* bcol, const void* val, int vdt,
+                             bool x_f32, bool y_f64, const void* u, const void* w, const void* r, void* y, double ca,
+                             double cb, double cc, double cd, int dot, const double* rdot, const Reduce& R,
+                             const int* done, cudaStream_t st);
+cudaError_t launch_bsr3_diag(int nb, const int32_t* browptr, const int32_t* bcol, const double* val, double* dis,
+                             int* bad, cudaStream_t st);
+cudaError_t launch_bsr3_scale(int nb, const int32_t* browptr, const int32_t* bcol, const double* val,
+                              const double* dis, double* out, cudaStream_t st);
+cudaError_t launch_bsr3_gershgorin(int nb, const int32_t* browptr, const double* val, unsigned long long* out_bits,
+                                   cudaStream_t st);
+cudaError_t launch_bsell3_lengths(int nb, const int32_t* browptr, int32_t* slice_len, cudaStream_t st);
+cudaError_t launch_bsell3_fill(int nb, const int32_t* browptr, const int32_t* bcol, const double* val,
+                               const int32_t* slice_ptr, int vdt, double shift, int32_t* scol, void* sval,
+                               int* nodiag, cudaStream_t st);
+
 cudaError_t launch_csr_diag(int n, const int32_t* rowptr, const int32_t* col, const double* val,
                             double* dis, int* bad, cudaStream_t st);
 cudaError_t launch_csr_scale(int n, const int32_t* rowptr, const int32_t* col, const double* val,
