@@ -40,6 +40,7 @@ extern "C" {
 
 typedef struct nc_matrix_s* nc_matrix;
 typedef struct nc_solver_s* nc_solver;
+typedef struct nc_batch_s* nc_batch;
 
 typedef enum {
     NC_OK = 0,
@@ -50,7 +51,8 @@ typedef enum {
     NC_ERR_MAXIT = 5,        /* maxit reached before ||r|| <= tol ||b||               */
     NC_ERR_BREAKDOWN = 6,    /* NaN or Inf in a reduction                             */
     NC_ERR_UNSUPPORTED = 7,  /* option combination not implemented for this format    */
-    NC_ERR_SCRATCH_LIMIT = 8 /* n above the fixed scratch of nc_apply_poly_csr_noalloc */
+    NC_ERR_SCRATCH_LIMIT = 8, /* n above the fixed scratch of nc_apply_poly_csr_noalloc */
+    NC_ERR_ADMISSION = 9     /* batch engine: no free slot or not enough pooled memory */
 } nc_status;
 
 /* Value type of the matrix inside P_k(A) (the outer CG stays float64). */
@@ -219,6 +221,46 @@ NC_API nc_status pcg_solve_host(nc_solver S, const double* b_host, double* x_hos
 NC_API nc_status pcg_get_info(nc_solver S, nc_solver_info* info);
 
 NC_API nc_status pcg_destroy(nc_solver S);
+
+/* ---- Batched and continuous-batching engine --------------------------------
+ * Many independent systems (matrix-free constant 7-point stencils of any
+ * size, each with its own bounds, degree k and theta scale; one slot per
+ * right-hand side) solved together: every PCG iteration of every slot is one
+ * pass of a fixed sequence of persistent kernels over device-side work lists
+ * (stencil tiles and vector chunks of all slots), captured once as a CUDA
+ * graph with a device-evaluated WHILE loop.  Precision: float32 matrix-free
+ * P_k(A) (Algorithm 2, theta' = s theta) inside a float64 PCG (residual,
+ * dot products and stopping test in float64, Sec. 5: ||r|| <= tol ||b||).
+ * Each slot is Jacobi scaled (c0 -> 1) and lambda_min/lambda_max refer to the
+ * scaled operator; x0 = 0.  Every slot reduces its own dot products in a
+ * fixed order, so its result does not depend on the other slots.
+ *
+ * pcg_batch_create: capacity of max_slots slots and max_unknowns pooled
+ *   unknowns (6 float64 + 4 float32 vectors each: 64 bytes per unknown,
+ *   allocated once -- the HBM budget); kmax = largest degree accepted.
+ * pcg_batch_add: admit one system with right-hand side b_dev (n float64,
+ *   read during the call).  NC_ERR_ADMISSION when no slot or pool space is
+ *   free (retry after releasing finished slots).  The slot starts with the
+ *   next pcg_batch_run.
+ * pcg_batch_run: advance every admitted slot by up to iter_limit PCG
+ *   iterations (<= 0: until all slots have stopped) in one graph launch;
+ *   synchronises the stream; *active_left = slots not yet finished.
+ * pcg_batch_status: done flag and result of a slot (as of the last run).
+ * pcg_batch_collect: x_dev (n float64) = the slot's solution of the original
+ *   (unscaled) system; only for finished slots.
+ * pcg_batch_release: free a finished slot and its memory.
+ * pcg_batch_free_units: largest contiguous and total free pooled unknowns. */
+NC_API nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, void* stream, nc_batch* out);
+NC_API nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx, double cy, double cz,
+                               double lambda_min, double lambda_max, int degree_k, double theta_scale,
+                               const double* b_dev, void* stream, int* slot);
+NC_API nc_status pcg_batch_run(nc_batch B, double tol, int maxit, int iter_limit, void* stream, int* active_left);
+NC_API nc_status pcg_batch_status(nc_batch B, int slot, int* done, nc_result* res);
+NC_API nc_status pcg_batch_collect(nc_batch B, int slot, double* x_dev, void* stream);
+NC_API nc_status pcg_batch_release(nc_batch B, int slot, void* stream);
+NC_API nc_status pcg_batch_free_units(nc_batch B, int64_t* largest, int64_t* total);
+NC_API nc_status pcg_batch_destroy(nc_batch B);
+NC_API const char* nc_batch_last_cuda_error(void);
 
 /* ---- No-allocation apply ---------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

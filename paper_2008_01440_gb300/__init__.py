@@ -43,7 +43,17 @@ from .binding import (  # noqa: F401
     nc_matrix_stencil7,
     nc_matvec,
     nc_version,
+    Batch,
+    NC_ERR_ADMISSION,
     pcg_apply_poly,
+    pcg_batch_add,
+    pcg_batch_collect,
+    pcg_batch_create,
+    pcg_batch_destroy,
+    pcg_batch_free_units,
+    pcg_batch_release,
+    pcg_batch_run,
+    pcg_batch_status,
     pcg_destroy,
     pcg_get_info,
     pcg_setup,

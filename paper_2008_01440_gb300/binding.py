@@ -22,7 +22,7 @@ if not os.path.exists(LIB_PATH):
 lib = ctypes.CDLL(LIB_PATH)
 
 NC_OK, NC_ERR_ARG, NC_ERR_CUDA, NC_ERR_OOM, NC_ERR_INDEFINITE, NC_ERR_MAXIT, NC_ERR_BREAKDOWN, \
-    NC_ERR_UNSUPPORTED, NC_ERR_SCRATCH_LIMIT = range(9)
+    NC_ERR_UNSUPPORTED, NC_ERR_SCRATCH_LIMIT, NC_ERR_ADMISSION = range(10)
 NC_F64, NC_F32, NC_BF16 = 0, 1, 2
 _DTYPES = {"f64": NC_F64, "f32": NC_F32, "bf16": NC_BF16}
 # statuses a solve may end with while still returning a meaningful iterate
@@ -83,6 +83,16 @@ _SIGS = {
     "nc_apply_poly_csr_noalloc": (ctypes.c_int, [_i64, _vp, _vp, _vp, _dbl, _dbl, ctypes.c_int, _dbl, _vp, _vp,
                                                  _vp]),
     "nc_apply_poly_noalloc_max_n": (_i64, []),
+    "pcg_batch_create": (ctypes.c_int, [ctypes.c_int, _i64, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "pcg_batch_add": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dbl, _dbl, _dbl, _dbl, _dbl,
+                                     _dbl, ctypes.c_int, _dbl, _vp, _vp, ctypes.POINTER(ctypes.c_int)]),
+    "pcg_batch_run": (ctypes.c_int, [_vp, _dbl, ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int)]),
+    "pcg_batch_status": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(nc_result)]),
+    "pcg_batch_collect": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "pcg_batch_release": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "pcg_batch_free_units": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "pcg_batch_destroy": (ctypes.c_int, [_vp]),
+    "nc_batch_last_cuda_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -94,7 +104,8 @@ class NcError(RuntimeError):
     def __init__(self, status: int, where: str):
         msg = lib.nc_strerror(status).decode()
         if status == NC_ERR_CUDA:
-            msg += ": " + lib.nc_last_cuda_error().decode()
+            src = lib.nc_batch_last_cuda_error if where.startswith("pcg_batch") else lib.nc_last_cuda_error
+            msg += ": " + src().decode()
         super().__init__(f"{where}: {msg} (status {status})")
         self.status = status
 
@@ -320,3 +331,78 @@ def pcg_destroy(S: Solver):
 
 def nc_matrix_destroy(A: Matrix):
     A.close()
+
+
+class Batch:
+    """Owning wrapper of an nc_batch engine (see include/nc_pcg.h)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            lib.pcg_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pcg_batch_create(max_slots: int, max_unknowns: int, kmax: int, stream=None) -> Batch:
+    h = _vp()
+    _check(lib.pcg_batch_create(int(max_slots), int(max_unknowns), int(kmax), _stream(stream), ctypes.byref(h)),
+           "pcg_batch_create")
+    return Batch(h.value)
+
+
+def pcg_batch_add(B: Batch, nx: int, ny: int, nz: int, c0: float, cx: float, cy: float, cz: float,
+                  lambda_min: float, lambda_max: float, degree_k: int, theta_scale: float, b, stream=None):
+    """Admit one system; returns the slot id, or None when the engine is full
+    (NC_ERR_ADMISSION)."""
+    import torch
+    slot = ctypes.c_int(-1)
+    n = int(nx) * int(ny) * int(nz)
+    st = lib.pcg_batch_add(B.handle, int(nx), int(ny), int(nz), float(c0), float(cx), float(cy), float(cz),
+                           float(lambda_min), float(lambda_max), int(degree_k), float(theta_scale),
+                           _ptr(b, torch.float64, n, "b"), _stream(stream), ctypes.byref(slot))
+    if st == NC_ERR_ADMISSION:
+        return None
+    _check(st, "pcg_batch_add")
+    return slot.value
+
+
+def pcg_batch_run(B: Batch, tol: float, maxit: int, iter_limit: int = 0, stream=None) -> int:
+    left = ctypes.c_int(0)
+    _check(lib.pcg_batch_run(B.handle, float(tol), int(maxit), int(iter_limit), _stream(stream), ctypes.byref(left)),
+           "pcg_batch_run")
+    return left.value
+
+
+def pcg_batch_status(B: Batch, slot: int):
+    done = ctypes.c_int(0)
+    res = nc_result()
+    _check(lib.pcg_batch_status(B.handle, int(slot), ctypes.byref(done), ctypes.byref(res)), "pcg_batch_status")
+    return bool(done.value), res.as_dict()
+
+
+def pcg_batch_collect(B: Batch, slot: int, x, stream=None):
+    import torch
+    _check(lib.pcg_batch_collect(B.handle, int(slot), _ptr(x, torch.float64, what="x"), _stream(stream)),
+           "pcg_batch_collect")
+
+
+def pcg_batch_release(B: Batch, slot: int, stream=None):
+    _check(lib.pcg_batch_release(B.handle, int(slot), _stream(stream)), "pcg_batch_release")
+
+
+def pcg_batch_free_units(B: Batch):
+    lg, tt = _i64(0), _i64(0)
+    _check(lib.pcg_batch_free_units(B.handle, ctypes.byref(lg), ctypes.byref(tt)), "pcg_batch_free_units")
+    return lg.value, tt.value
+
+
+def pcg_batch_destroy(B: Batch):
+    B.close()

@@ -669,6 +669,7 @@ const char* nc_strerror(nc_status s) {
     case NC_ERR_BREAKDOWN: return "NaN or Inf in a reduction";
     case NC_ERR_UNSUPPORTED: return "unsupported option for this matrix format";
     case NC_ERR_SCRATCH_LIMIT: return "n exceeds the fixed scratch array of the no-allocation apply";
+    case NC_ERR_ADMISSION: return "batch engine: no free slot or not enough pooled memory";
     }
     return "unknown status";
 }

@@ -1,0 +1,742 @@
+// Batched / continuous-batching PCG engine for many independent matrix-free
+// 7-point systems of uneven size, each with its own degree k, bounds and
+// right-hand side (one "slot" per (system, right-hand side) pair).
+//
+// All slots advance together: one PCG iteration for every slot is a fixed
+// sequence of persistent grid-stride kernels over two work lists held in
+// device memory -- stencil tiles (32 x 8 x ZC points of one slot) and vector
+// chunks (kVch entries of one slot):
+//   opq      q = A p and (p, q) -> alpha              (float64, tiles)
+//   axpy     x += alpha p, r -= alpha q, ||r||^2, stop? (float64, chunks);
+//            slots being admitted instead start r = b, x = 0, ||b||^2
+//   cheb(j)  Chebyshev step j = 1..kmax, float32 vectors, float64 z at
+//            j = k_slot with (r, z) -> beta (or the initial (r, z))  (tiles)
+//   pupd     p = z + beta p (or p = z for admitted slots)   (chunks)
+//   true     r_true = b - A x, ||r_true||^2 for slots that just stopped
+//   cond     loop condition: slots left and iterations this call < limit
+// Every slot reduces its own dot products: each tile / chunk writes a
+// partial sum; the CTA that completes a slot's last partial sums that slot's
+// partials in order (deterministic, independent of the other slots, so a
+// slot's result is the same alone and in any mix) and updates its scalars.
+//
+// The sequence is captured once as the body of a conditional WHILE node; the
+// work lists, slot descriptors and coefficients live in device tables that
+// the host rewrites between launches (admission, retirement) without
+// re-capturing.  A launch runs up to `iter_limit` iterations: the whole
+// batch in one launch, or a few iterations per serving tick.
+//
+// Memory: every slot owns 6 float64 and 4 float32 vectors of its length in
+// two pools allocated once (first-fit free list on the host); a slot is
+// refused when the pools have no room (the HBM budget).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "nc_stencil.cuh"
+
+namespace nc {
+namespace {
+
+constexpr int kVch = 8192;    // vector-chunk length
+constexpr int kZC = 8;        // planes per stencil tile
+constexpr int kBatchGrid = kSMs * 8;
+
+enum Phase : int { PH_FREE = 0, PH_INIT = 1, PH_RUN = 2, PH_FINISH = 3, PH_DONE = 4 };
+
+enum BFin : int { BF_ALPHA = 1, BF_RR = 2, BF_INIT = 3, BF_RZ = 4, BF_START = 5, BF_TRUE = 6 };
+
+struct BDesc {
+    int nx, ny, nz, n;
+    int k, coef0;
+    int tile0, tile1, vch0, vch1;
+    double c0, cx, cy, cz;
+    double *b, *x, *r, *z, *p, *q;
+    float *t0, *t1, *t2, *r32;
+};
+
+struct BState {
+    double rz, pq, alpha, beta, rr, bb, rr_true;
+    int iter, phase, status, n_dot, n_prec;
+    unsigned int counter;
+};
+
+struct BCoef {
+    float e0, ex, ey, ez, cb, cc;
+    int terms, pad;
+};
+
+struct BTile {
+    int pair, bx, by, bz;
+};
+
+struct BVch {
+    int pair, start;
+};
+
+struct BCtl {
+    double tol2;
+    int maxit, ntiles, nvch, active;
+    int iters_this_call, iter_limit, pad0, pad1;
+};
+
+__device__ void bfinalize(BState* st, BCtl* ctl, int kind, double s) {
+    const bool finite = isfinite(s);
+    switch (kind) {
+    case BF_ALPHA:
+        st->n_dot += 1;
+        st->pq = s;
+        if (!(s > 0.0) || !finite) {
+            st->status = finite ? NC_ERR_INDEFINITE : NC_ERR_BREAKDOWN;
+            st->phase = PH_FINISH;
+        } else {
+            st->alpha = st->rz / s;
+        }
+        break;
+    case BF_RR:
+        st->n_dot += 1;
+        st->rr = s;
+        st->iter += 1;
+        if (!finite) { st->status = NC_ERR_BREAKDOWN; st->phase = PH_FINISH; }
+        else if (s <= ctl->tol2 * st->bb) { st->status = NC_OK; st->phase = PH_FINISH; }
+        else if (st->iter >= ctl->maxit) { st->status = NC_ERR_MAXIT; st->phase = PH_FINISH; }
+        break;
+    case BF_INIT:   // r = b: ||r0||^2 = ||b||^2
+        st->bb = s;
+        st->rr = s;
+        if (!finite) { st->status = NC_ERR_BREAKDOWN; st->phase = PH_FINISH; }
+        else if (s == 0.0) { st->status = NC_OK; st->phase = PH_FINISH; }
+        else if (ctl->maxit <= 0) { st->status = NC_ERR_MAXIT; st->phase = PH_FINISH; }
+        break;
+    case BF_RZ:
+        st->n_dot += 1;
+        st->n_prec += 1;
+        if (!(s > 0.0) || !finite) {
+            st->status = finite ? NC_ERR_INDEFINITE : NC_ERR_BREAKDOWN;
+            st->phase = PH_FINISH;
+        } else if (st->phase == PH_INIT) {
+            st->rz = s;
+        } else {
+            st->beta = s / st->rz;
+            st->rz = s;
+        }
+        break;
+    case BF_START:
+        if (st->phase == PH_INIT) st->phase = PH_RUN;
+        break;
+    case BF_TRUE:
+        st->rr_true = s;
+        st->phase = PH_DONE;
+        atomicSub(&ctl->active, 1);
+        break;
+    default:
+        break;
+    }
+}
+
+// Per-slot reduction: this CTA's partial goes to partials[slotidx]; the CTA
+// completing the slot's count-th partial sums partials[first, first+count)
+// in order and finalizes.  All threads of the CTA call it (uniform).
+__device__ void reduce_slot(double v, double* partials, int slotidx, int first, int count, BState* st, BCtl* ctl,
+                            int kind) {
+    __shared__ double sh[256];
+    __shared__ int is_last;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    v = block_sum<256>(v, sh, tid);
+    if (tid == 0) {
+        partials[slotidx] = v;
+        __threadfence();
+        const unsigned int t = atomicAdd(&st->counter, 1u);
+        is_last = (t == (unsigned int)count - 1u);
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        double s = 0.0;
+        for (int i = tid; i < count; i += 256) s += __ldcg(&partials[first + i]);
+        s = block_sum<256>(s, sh, tid);
+        if (tid == 0) {
+            bfinalize(st, ctl, kind, s);
+            st->counter = 0u;
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) bk_opq(const BDesc* __restrict__ D, BState* S, const BTile* __restrict__ T,
+                                              BCtl* ctl, double* partials) {
+    const int nt = ctl->ntiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const BTile tl = T[t];
+        BState* st = S + tl.pair;
+        if (st->phase != PH_RUN) continue;
+        const BDesc& d = D[tl.pair];
+        StencilCoef<double> c;
+        c.e0 = d.c0;
+        c.ex = -d.cx;
+        c.ey = -d.cy;
+        c.ez = -d.cz;
+        c.cb = 0.0;
+        c.cc = 0.0;
+        c.terms = 0;
+        const int k0 = tl.bz * kZC, k1 = min(k0 + kZC, d.nz);
+        const double dv = stencil_tile<double, double, 2>(d.nx, d.ny, d.nz, tl.bx, tl.by, k0, k1, d.p, nullptr,
+                                                          nullptr, d.q, c, nullptr, threadIdx.x, threadIdx.y);
+        reduce_slot(dv, partials, t, d.tile0, d.tile1 - d.tile0, st, ctl, BF_ALPHA);
+    }
+}
+
+__global__ void __launch_bounds__(256) bk_axpy(const BDesc* __restrict__ D, BState* S, const BVch* __restrict__ V,
+                                               BCtl* ctl, double* partials) {
+    const int nv = ctl->nvch;
+    for (int c = blockIdx.x; c < nv; c += gridDim.x) {
+        const BVch ch = V[c];
+        BState* st = S + ch.pair;
+        const int ph = st->phase;
+        if (ph != PH_RUN && ph != PH_INIT) continue;
+        const BDesc& d = D[ch.pair];
+        const int e = min(ch.start + kVch, d.n);
+        double acc = 0.0;
+        if (ph == PH_RUN) {
+            const double a = st->alpha;
+            for (int i = ch.start + threadIdx.x; i < e; i += 256) {
+                d.x[i] = fma(a, d.p[i], d.x[i]);
+                const double ri = fma(-a, d.q[i], d.r[i]);
+                d.r[i] = ri;
+                d.r32[i] = (float)ri;
+                acc = fma(ri, ri, acc);
+            }
+        } else {
+            for (int i = ch.start + threadIdx.x; i < e; i += 256) {
+                const double bi = d.b[i];
+                d.x[i] = 0.0;
+                d.r[i] = bi;
+                d.r32[i] = (float)bi;
+                acc = fma(bi, bi, acc);
+            }
+        }
+        reduce_slot(acc, partials, c, d.vch0, d.vch1 - d.vch0, st, ctl, ph == PH_RUN ? BF_RR : BF_INIT);
+    }
+}
+
+__global__ void __launch_bounds__(256) bk_cheb(const BDesc* __restrict__ D, BState* S, const BTile* __restrict__ T,
+                                               const BCoef* __restrict__ C, BCtl* ctl, double* partials, int j) {
+    const int nt = ctl->ntiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const BTile tl = T[t];
+        BState* st = S + tl.pair;
+        const int ph = st->phase;
+        if (ph != PH_RUN && ph != PH_INIT) continue;
+        const BDesc& d = D[tl.pair];
+        if (j > d.k) continue;
+        const BCoef bc = C[d.coef0 + j - 1];
+        StencilCoef<float> c;
+        c.e0 = bc.e0;
+        c.ex = bc.ex;
+        c.ey = bc.ey;
+        c.ez = bc.ez;
+        c.cb = bc.cb;
+        c.cc = bc.cc;
+        c.terms = bc.terms;
+        float* tb[3] = {d.t0, d.t1, d.t2};
+        const float* u = (j == 1) ? d.r32 : tb[(j - 1) % 3];
+        const float* w = (j >= 3) ? tb[(j - 2) % 3] : nullptr;
+        const int k0 = tl.bz * kZC, k1 = min(k0 + kZC, d.nz);
+        if (j == d.k) {
+            const double dv = stencil_tile<float, double, 1>(d.nx, d.ny, d.nz, tl.bx, tl.by, k0, k1, u, w, d.r32, d.z,
+                                                             c, d.r, threadIdx.x, threadIdx.y);
+            reduce_slot(dv, partials, t, d.tile0, d.tile1 - d.tile0, st, ctl, BF_RZ);
+        } else {
+            stencil_tile<float, float, 0>(d.nx, d.ny, d.nz, tl.bx, tl.by, k0, k1, u, w, d.r32, tb[j % 3], c, nullptr,
+                                          threadIdx.x, threadIdx.y);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) bk_pupd(const BDesc* __restrict__ D, BState* S, const BVch* __restrict__ V,
+                                               BCtl* ctl, double* partials) {
+    const int nv = ctl->nvch;
+    for (int c = blockIdx.x; c < nv; c += gridDim.x) {
+        const BVch ch = V[c];
+        BState* st = S + ch.pair;
+        const int ph = st->phase;
+        if (ph != PH_RUN && ph != PH_INIT) continue;
+        const BDesc& d = D[ch.pair];
+        const int e = min(ch.start + kVch, d.n);
+        if (ph == PH_RUN) {
+            const double beta = st->beta;
+            for (int i = ch.start + threadIdx.x; i < e; i += 256) d.p[i] = fma(beta, d.p[i], d.z[i]);
+        } else {
+            for (int i = ch.start + threadIdx.x; i < e; i += 256) d.p[i] = d.z[i];
+            // the last chunk of an admitted slot moves it to the running phase
+            reduce_slot(0.0, partials, c, d.vch0, d.vch1 - d.vch0, st, ctl, BF_START);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) bk_true(const BDesc* __restrict__ D, BState* S, const BTile* __restrict__ T,
+                                               BCtl* ctl, double* partials) {
+    const int nt = ctl->ntiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const BTile tl = T[t];
+        BState* st = S + tl.pair;
+        if (st->phase != PH_FINISH) continue;
+        const BDesc& d = D[tl.pair];
+        StencilCoef<double> c;   // q = b - A x
+        c.e0 = -d.c0;
+        c.ex = d.cx;
+        c.ey = d.cy;
+        c.ez = d.cz;
+        c.cb = 0.0;
+        c.cc = 1.0;
+        c.terms = kTermR;
+        const int k0 = tl.bz * kZC, k1 = min(k0 + kZC, d.nz);
+        const double dv = stencil_tile<double, double, 3>(d.nx, d.ny, d.nz, tl.bx, tl.by, k0, k1, d.x, nullptr, d.b,
+                                                          d.q, c, nullptr, threadIdx.x, threadIdx.y);
+        reduce_slot(dv, partials, t, d.tile0, d.tile1 - d.tile0, st, ctl, BF_TRUE);
+    }
+}
+
+__global__ void bk_cond(BCtl* ctl, cudaGraphConditionalHandle h) {
+    ctl->iters_this_call += 1;
+    const int go = ctl->active > 0 && ctl->iters_this_call < ctl->iter_limit;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void bk_scale(int n, const double* __restrict__ in, double s, double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = in[i] * s;
+}
+
+}  // namespace
+}  // namespace nc
+
+using namespace nc;
+
+struct nc_batch_s {
+    int cap_slots = 0;
+    int64_t cap_units = 0;        // unknowns the pools hold
+    int kmax = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // device
+    BDesc* d_desc = nullptr;
+    BState* d_state = nullptr;
+    BCtl* d_ctl = nullptr;
+    BTile* d_tiles = nullptr;
+    BVch* d_vch = nullptr;
+    BCoef* d_coef = nullptr;
+    double* d_partials = nullptr;
+    double* pool64 = nullptr;
+    float* pool32 = nullptr;
+    int cap_tiles = 0, cap_vch = 0, cap_coef = 0;
+    // host
+    std::vector<BDesc> desc;
+    std::vector<int> used;        // slot in use
+    std::vector<int> kdeg;
+    std::vector<double> dis;      // d^{-1/2} constant per slot
+    std::vector<std::vector<BCoef>> coefs;
+    std::vector<int64_t> off;     // pool offset (unknowns) per slot
+    std::map<int64_t, int64_t> free_list;   // offset -> length
+    bool dirty = true;
+    BState* h_state = nullptr;    // pinned
+    BCtl* h_ctl = nullptr;        // pinned
+};
+
+namespace {
+
+thread_local cudaError_t g_batch_err = cudaSuccess;
+
+#define NB_CU(call)                                 \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) {                    \
+            g_batch_err = e_;                       \
+            return NC_ERR_CUDA;                     \
+        }                                           \
+    } while (0)
+
+nc_status balloc(void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        *p = nullptr;
+        return NC_ERR_OOM;
+    }
+    if (e != cudaSuccess) {
+        g_batch_err = e;
+        *p = nullptr;
+        return NC_ERR_CUDA;
+    }
+    return NC_OK;
+}
+
+int64_t pool_alloc(nc_batch B, int64_t len) {   // first fit; -1 if none
+    for (auto it = B->free_list.begin(); it != B->free_list.end(); ++it) {
+        if (it->second >= len) {
+            const int64_t o = it->first, rest = it->second - len;
+            B->free_list.erase(it);
+            if (rest > 0) B->free_list[o + len] = rest;
+            return o;
+        }
+    }
+    return -1;
+}
+
+void pool_free(nc_batch B, int64_t o, int64_t len) {
+    auto it = B->free_list.emplace(o, len).first;
+    auto nx = std::next(it);
+    if (nx != B->free_list.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        B->free_list.erase(nx);
+    }
+    if (it != B->free_list.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            B->free_list.erase(it);
+        }
+    }
+}
+
+nc_status grow(void** p, int* cap, int need, size_t elem) {
+    if (need <= *cap) return NC_OK;
+    int nc_ = std::max(need, *cap * 2);
+    if (nc_ < 64) nc_ = 64;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    nc_status s = balloc(p, elem * (size_t)nc_);
+    if (s != NC_OK) {
+        *cap = 0;
+        return s;
+    }
+    *cap = nc_;
+    return NC_OK;
+}
+
+nc_status build_batch_graph(nc_batch B) {
+    if (B->exec) {
+        cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaGraphNode_t nw = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    nc_status out = NC_ERR_CUDA;
+    cudaError_t e;
+    do {
+        if ((e = cudaGraphCreate(&g, 0))) break;
+        if ((e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault))) break;
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if ((e = cudaGraphAddNode(&nw, g, nullptr, nullptr, 0, &cp))) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(B->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+            break;
+        const dim3 tb(kTX, kTY);
+        bk_opq<<<kBatchGrid, tb, 0, B->cap>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
+        bk_axpy<<<kBatchGrid, 256, 0, B->cap>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
+        for (int j = 1; j <= B->kmax; ++j)
+            bk_cheb<<<kBatchGrid, tb, 0, B->cap>>>(B->d_desc, B->d_state, B->d_tiles, B->d_coef, B->d_ctl,
+                                                   B->d_partials, j);
+        bk_pupd<<<kBatchGrid, 256, 0, B->cap>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
+        bk_true<<<kBatchGrid, tb, 0, B->cap>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
+        bk_cond<<<1, 1, 0, B->cap>>>(B->d_ctl, h);
+        cudaError_t e1 = cudaGetLastError();
+        cudaGraph_t tmp = nullptr;
+        e = cudaStreamEndCapture(B->cap, &tmp);
+        if (e1) { e = e1; break; }
+        if (e) break;
+        if ((e = cudaGraphInstantiate(&B->exec, g, 0))) break;
+        out = NC_OK;
+    } while (0);
+    if (out != NC_OK) {
+        g_batch_err = e;
+        cudaGetLastError();
+    }
+    if (g) cudaGraphDestroy(g);
+    return out;
+}
+
+// Rebuild the work lists and descriptors of all slots in use and upload them.
+nc_status sync_tables(nc_batch B, cudaStream_t st) {
+    std::vector<BTile> tiles;
+    std::vector<BVch> vch;
+    std::vector<BCoef> coef;
+    for (int s = 0; s < B->cap_slots; ++s) {
+        if (!B->used[s]) continue;
+        BDesc& d = B->desc[s];
+        d.tile0 = (int)tiles.size();
+        const int tx = (d.nx + kTX - 1) / kTX, ty = (d.ny + kTY - 1) / kTY, tz = (d.nz + kZC - 1) / kZC;
+        for (int bz = 0; bz < tz; ++bz)
+            for (int by = 0; by < ty; ++by)
+                for (int bx = 0; bx < tx; ++bx) tiles.push_back(BTile{s, bx, by, bz});
+        d.tile1 = (int)tiles.size();
+        d.vch0 = (int)vch.size();
+        for (int i = 0; i < d.n; i += kVch) vch.push_back(BVch{s, i});
+        d.vch1 = (int)vch.size();
+        d.coef0 = (int)coef.size();
+        coef.insert(coef.end(), B->coefs[s].begin(), B->coefs[s].end());
+    }
+    const int cap_t = B->cap_tiles, cap_v = B->cap_vch;
+    nc_status s;
+    if ((s = grow(reinterpret_cast<void**>(&B->d_tiles), &B->cap_tiles, (int)tiles.size(), sizeof(BTile)))) return s;
+    if ((s = grow(reinterpret_cast<void**>(&B->d_vch), &B->cap_vch, (int)vch.size(), sizeof(BVch)))) return s;
+    int cap_c = B->cap_coef;
+    if ((s = grow(reinterpret_cast<void**>(&B->d_coef), &B->cap_coef, (int)coef.size(), sizeof(BCoef)))) return s;
+    const bool realloc_ = cap_t != B->cap_tiles || cap_v != B->cap_vch || cap_c != B->cap_coef;
+    if (realloc_) {
+        if (B->d_partials) cudaFree(B->d_partials);
+        B->d_partials = nullptr;
+        const int np = std::max(B->cap_tiles, B->cap_vch);
+        if ((s = balloc(reinterpret_cast<void**>(&B->d_partials), sizeof(double) * (size_t)np))) return s;
+        if ((s = build_batch_graph(B))) return s;
+    }
+    if (!tiles.empty())
+        NB_CU(cudaMemcpyAsync(B->d_tiles, tiles.data(), sizeof(BTile) * tiles.size(), cudaMemcpyHostToDevice, st));
+    if (!vch.empty())
+        NB_CU(cudaMemcpyAsync(B->d_vch, vch.data(), sizeof(BVch) * vch.size(), cudaMemcpyHostToDevice, st));
+    if (!coef.empty())
+        NB_CU(cudaMemcpyAsync(B->d_coef, coef.data(), sizeof(BCoef) * coef.size(), cudaMemcpyHostToDevice, st));
+    NB_CU(cudaMemcpyAsync(B->d_desc, B->desc.data(), sizeof(BDesc) * B->cap_slots, cudaMemcpyHostToDevice, st));
+    B->h_ctl->ntiles = (int)tiles.size();
+    B->h_ctl->nvch = (int)vch.size();
+    // the host vectors must outlive the copies
+    NB_CU(cudaStreamSynchronize(st));
+    B->dirty = false;
+    return NC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nc_batch_last_cuda_error(void) { return cudaGetErrorString(g_batch_err); }
+
+nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, void* stream, nc_batch* out) {
+    if (!out) return NC_ERR_ARG;
+    *out = nullptr;
+    if (max_slots < 1 || max_unknowns < 1 || kmax < 1 || kmax > 4096) return NC_ERR_ARG;
+    nc_batch B = new (std::nothrow) nc_batch_s();
+    if (!B) return NC_ERR_OOM;
+    B->cap_slots = max_slots;
+    B->cap_units = max_unknowns;
+    B->kmax = kmax;
+    B->desc.assign(max_slots, BDesc{});
+    B->used.assign(max_slots, 0);
+    B->kdeg.assign(max_slots, 0);
+    B->dis.assign(max_slots, 1.0);
+    B->coefs.assign(max_slots, {});
+    B->off.assign(max_slots, -1);
+    B->free_list[0] = max_unknowns;
+    nc_status s = NC_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    do {
+        if ((s = balloc(reinterpret_cast<void**>(&B->d_desc), sizeof(BDesc) * max_slots))) break;
+        if ((s = balloc(reinterpret_cast<void**>(&B->d_state), sizeof(BState) * max_slots))) break;
+        if ((s = balloc(reinterpret_cast<void**>(&B->d_ctl), sizeof(BCtl)))) break;
+        if ((s = balloc(reinterpret_cast<void**>(&B->pool64), sizeof(double) * 6 * (size_t)max_unknowns))) break;
+        if ((s = balloc(reinterpret_cast<void**>(&B->pool32), sizeof(float) * 4 * (size_t)max_unknowns))) break;
+        cudaError_t e;
+        if ((e = cudaMallocHost(&B->h_state, sizeof(BState) * max_slots)) ||
+            (e = cudaMallocHost(&B->h_ctl, sizeof(BCtl))) ||
+            (e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking)) ||
+            (e = cudaMemsetAsync(B->d_state, 0, sizeof(BState) * max_slots, st)) ||
+            (e = cudaMemsetAsync(B->d_ctl, 0, sizeof(BCtl), st)) || (e = cudaStreamSynchronize(st))) {
+            g_batch_err = e;
+            s = NC_ERR_CUDA;
+            break;
+        }
+        std::memset(B->h_ctl, 0, sizeof(BCtl));
+        if ((s = sync_tables(B, st))) break;   // allocates the tables and captures the graph
+    } while (0);
+    if (s != NC_OK) {
+        pcg_batch_destroy(B);
+        return s;
+    }
+    *out = B;
+    return NC_OK;
+}
+
+nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx, double cy, double cz,
+                        double lambda_min, double lambda_max, int degree_k, double theta_scale, const double* b_dev,
+                        void* stream, int* slot) {
+    if (!B || !slot || !b_dev) return NC_ERR_ARG;
+    *slot = -1;
+    if (nx < 1 || ny < 1 || nz < 1 || degree_k < 1 || degree_k > B->kmax || !(c0 > 0.0) ||
+        !(lambda_min > 0.0) || !(lambda_max > lambda_min) || !(theta_scale > 0.0))
+        return NC_ERR_ARG;
+    const int64_t n = (int64_t)nx * ny * nz;
+    if (n >= ((int64_t)1 << 31)) return NC_ERR_ARG;
+    int s = -1;
+    for (int i = 0; i < B->cap_slots; ++i)
+        if (!B->used[i]) { s = i; break; }
+    if (s < 0) return NC_ERR_ADMISSION;
+    const int64_t o = pool_alloc(B, n);
+    if (o < 0) return NC_ERR_ADMISSION;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // symmetric diagonal scaling of the constant stencil: c0 -> 1, c_a -> c_a/c0;
+    // the bounds refer to the scaled operator
+    const double dsc = 1.0 / std::sqrt(c0);
+    BDesc d{};
+    d.nx = nx; d.ny = ny; d.nz = nz; d.n = (int)n; d.k = degree_k;
+    d.c0 = 1.0; d.cx = cx / c0; d.cy = cy / c0; d.cz = cz / c0;
+    double* base64 = B->pool64 + 6 * o;
+    float* base32 = B->pool32 + 4 * o;
+    d.b = base64; d.x = base64 + n; d.r = base64 + 2 * n; d.z = base64 + 3 * n; d.p = base64 + 4 * n;
+    d.q = base64 + 5 * n;
+    d.t0 = base32; d.t1 = base32 + n; d.t2 = base32 + 2 * n; d.r32 = base32 + 3 * n;
+    // Chebyshev step coefficients (Eq. rhocheb, theta' = s theta) folded into
+    // the stencil form: e0 = a_j + d_j c0, e_a = -d_j c_a
+    const double theta = theta_scale * (lambda_max + lambda_min) / 2.0;
+    const double delta = (lambda_max - lambda_min) / 2.0;
+    const double sigma = theta / delta;
+    std::vector<BCoef> cf(degree_k);
+    double rho_prev = 1.0 / sigma;
+    for (int j = 1; j <= degree_k; ++j) {
+        const double rho = 1.0 / (2.0 * sigma - rho_prev);
+        double ca, cb, cc, cd;
+        if (j == 1) {
+            ca = 4.0 * rho / delta; cb = 0.0; cc = 0.0; cd = -2.0 * rho / (delta * theta);
+        } else {
+            ca = 2.0 * sigma * rho; cb = -rho * rho_prev; cc = 2.0 * rho / delta; cd = -2.0 * rho / delta;
+            if (j == 2) { cc += cb / theta; cb = 0.0; }
+        }
+        BCoef c{};
+        c.e0 = (float)(ca + cd * d.c0);
+        c.ex = (float)(-cd * d.cx);
+        c.ey = (float)(-cd * d.cy);
+        c.ez = (float)(-cd * d.cz);
+        c.cb = (float)cb;
+        c.cc = (float)cc;
+        c.terms = (cb != 0.0 ? kTermW : 0) | (cc != 0.0 ? kTermR : 0);
+        cf[j - 1] = c;
+        rho_prev = rho;
+    }
+    B->desc[s] = d;
+    B->used[s] = 1;
+    B->kdeg[s] = degree_k;
+    B->dis[s] = dsc;
+    B->coefs[s] = cf;
+    B->off[s] = o;
+    B->dirty = true;
+    // b_s = D^{-1/2} b into the slot; state: admitted (prologue runs with the next iteration)
+    bk_scale<<<std::min<int64_t>(4096, (n + 255) / 256), 256, 0, st>>>((int)n, b_dev, dsc, d.b);
+    NB_CU(cudaGetLastError());
+    BState init{};
+    init.phase = PH_INIT;
+    init.status = NC_ERR_MAXIT;
+    B->h_state[s] = init;
+    NB_CU(cudaMemcpyAsync(B->d_state + s, &B->h_state[s], sizeof(BState), cudaMemcpyHostToDevice, st));
+    NB_CU(cudaStreamSynchronize(st));
+    B->h_ctl->active += 1;
+    *slot = s;
+    return NC_OK;
+}
+
+nc_status pcg_batch_run(nc_batch B, double tol, int maxit, int iter_limit, void* stream, int* active_left) {
+    if (!B || !(tol >= 0.0) || maxit < 0) return NC_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (B->dirty) {
+        nc_status s = sync_tables(B, st);
+        if (s) return s;
+    }
+    if (B->h_ctl->active > 0) {
+        BCtl* c = B->h_ctl;
+        c->tol2 = tol * tol;
+        c->maxit = maxit;
+        c->iters_this_call = 0;
+        c->iter_limit = iter_limit > 0 ? iter_limit : 0x7fffffff;
+        NB_CU(cudaMemcpyAsync(B->d_ctl, c, sizeof(BCtl), cudaMemcpyHostToDevice, st));
+        NB_CU(cudaGraphLaunch(B->exec, st));
+        NB_CU(cudaMemcpyAsync(c, B->d_ctl, sizeof(BCtl), cudaMemcpyDeviceToHost, st));
+        NB_CU(cudaMemcpyAsync(B->h_state, B->d_state, sizeof(BState) * B->cap_slots, cudaMemcpyDeviceToHost, st));
+        NB_CU(cudaStreamSynchronize(st));
+    }
+    if (active_left) *active_left = B->h_ctl->active;
+    return NC_OK;
+}
+
+nc_status pcg_batch_status(nc_batch B, int slot, int* done, nc_result* res) {
+    if (!B || slot < 0 || slot >= B->cap_slots || !B->used[slot]) return NC_ERR_ARG;
+    const BState& s = B->h_state[slot];
+    if (done) *done = s.phase == PH_DONE;
+    if (res) {
+        const double bn = std::sqrt(s.bb);
+        res->iters = s.iter;
+        res->status = s.status;
+        res->relres = bn > 0 ? std::sqrt(s.rr) / bn : 0.0;
+        res->true_relres = bn > 0 ? std::sqrt(s.rr_true) / bn : 0.0;
+        res->n_dot = s.n_dot;
+        res->n_spmv = (int64_t)s.iter + (int64_t)B->kdeg[slot] * s.n_prec;
+        res->n_replace = 0;
+    }
+    return NC_OK;
+}
+
+nc_status pcg_batch_collect(nc_batch B, int slot, double* x_dev, void* stream) {
+    if (!B || slot < 0 || slot >= B->cap_slots || !B->used[slot] || !x_dev) return NC_ERR_ARG;
+    if (B->h_state[slot].phase != PH_DONE) return NC_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const BDesc& d = B->desc[slot];
+    const double scale = B->h_state[slot].bb == 0.0 ? 0.0 : B->dis[slot];
+    bk_scale<<<std::min<int64_t>(4096, ((int64_t)d.n + 255) / 256), 256, 0, st>>>(d.n, d.x, scale, x_dev);
+    NB_CU(cudaGetLastError());
+    return NC_OK;
+}
+
+nc_status pcg_batch_release(nc_batch B, int slot, void* stream) {
+    if (!B || slot < 0 || slot >= B->cap_slots || !B->used[slot]) return NC_ERR_ARG;
+    const int ph = B->h_state[slot].phase;
+    if (ph != PH_DONE) return NC_ERR_ARG;   // only finished slots can be released
+    // make sure pending collects on `stream` finished before the memory is reused
+    NB_CU(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    pool_free(B, B->off[slot], B->desc[slot].n);
+    B->used[slot] = 0;
+    B->off[slot] = -1;
+    B->desc[slot] = BDesc{};
+    B->coefs[slot].clear();
+    B->h_state[slot] = BState{};
+    B->dirty = true;
+    NB_CU(cudaMemcpyAsync(B->d_state + slot, &B->h_state[slot], sizeof(BState), cudaMemcpyHostToDevice,
+                          static_cast<cudaStream_t>(stream)));
+    NB_CU(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return NC_OK;
+}
+
+nc_status pcg_batch_free_units(nc_batch B, int64_t* largest, int64_t* total) {
+    if (!B) return NC_ERR_ARG;
+    int64_t lg = 0, tt = 0;
+    for (auto& kv : B->free_list) {
+        lg = std::max(lg, kv.second);
+        tt += kv.second;
+    }
+    if (largest) *largest = lg;
+    if (total) *total = tt;
+    return NC_OK;
+}
+
+nc_status pcg_batch_destroy(nc_batch B) {
+    if (!B) return NC_ERR_ARG;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    cudaFree(B->d_desc);
+    cudaFree(B->d_state);
+    cudaFree(B->d_ctl);
+    cudaFree(B->d_tiles);
+    cudaFree(B->d_vch);
+    cudaFree(B->d_coef);
+    cudaFree(B->d_partials);
+    cudaFree(B->pool64);
+    cudaFree(B->pool32);
+    if (B->h_state) cudaFreeHost(B->h_state);
+    if (B->h_ctl) cudaFreeHost(B->h_ctl);
+    delete B;
+    return NC_OK;
+}
+
+}  // extern "C"

@@ -52,22 +52,28 @@ struct Reduce {
 // ---- device helpers -------------------------------------------------------
 
 // Sum over a CTA of BS threads; the result is valid in every lane of warp 0.
-// The butterfly gives identical values in all lanes and a fixed order, so the
-// reduction is deterministic.
+// A shared-memory halving tree with full warps (BS/2, BS/4, ... 32 adds),
+// then a butterfly inside warp 0: every FP64 add is one warp instruction on
+// GB300's narrow FP64 pipe whatever the number of active lanes, and this
+// order needs about a quarter of the instructions of a per-warp shuffle tree.
+// The order is fixed, so the sum is deterministic.
 template <int BS>
 __device__ __forceinline__ double block_sum(double v, double* sh, int tid) {
-    const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[warp] = v;
+    sh[tid] = v;
     __syncthreads();
-    v = (tid < BS / 32) ? sh[tid] : 0.0;
-    if (warp == 0) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int s = BS / 2; s >= 32; s >>= 1) {
+        if (tid < s) sh[tid] += sh[tid + s];
+        __syncthreads();
+    }
+    double r = 0.0;
+    if (tid < 32) {
+        r = sh[tid];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
     }
     __syncthreads();
-    return v;
+    return r;
 }
 
 __device__ __forceinline__ void finalize(const Reduce& R, double s) {
@@ -126,7 +132,7 @@ __device__ __forceinline__ void finalize(const Reduce& R, double s) {
 // by every thread of every CTA of the grid.
 template <int BS>
 __device__ __forceinline__ void grid_reduce_ex(double v, const Reduce& R, int bid, int nblocks) {
-    __shared__ double sh[32];
+    __shared__ double sh[BS];
     __shared__ int is_last;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     v = block_sum<BS>(v, sh, tid);

@@ -18,18 +18,10 @@
 // edge), y-neighbours through the read-only cache (the adjacent warps loaded
 // them as their own centre values).  Each point reads u, w, r and writes y
 // once: 4 vector accesses, the minimum.
-#include "nc_step.cuh"
+#include "nc_stencil.cuh"
 
 namespace nc {
 namespace {
-
-constexpr int kTX = 32, kTY = 8;
-
-template <typename AT>
-struct StencilCoef {
-    AT e0, ex, ey, ez, cb, cc;
-    int terms;   // kTermW / kTermR
-};
 
 template <typename XT, typename YT, int DOT>
 __global__ void __launch_bounds__(kTX * kTY)
@@ -37,44 +29,11 @@ stencil7_step_kernel(const int nx, const int ny, const int nz, const int zchunk,
                      const XT* __restrict__ w, const XT* __restrict__ r, YT* __restrict__ y,
                      const StencilCoef<typename AccOf<XT>::type> c, const double* __restrict__ rdot,
                      const Reduce R, const int* __restrict__ done) {
-    using AT = typename AccOf<XT>::type;
     if (done != nullptr && *done) return;
-    const int lane = threadIdx.x;
-    const int i = blockIdx.x * kTX + lane;
-    const int j = blockIdx.y * kTY + threadIdx.y;
     const int k0 = blockIdx.z * zchunk;
     const int k1 = min(k0 + zchunk, nz);
-    const bool in = i < nx && j < ny;
-    const long long plane = (long long)nx * ny;
-    long long idx = ((long long)k0 * ny + j) * nx + i;
-    const AT zero = AT(0);
-    AT u_prev = (in && k0 > 0) ? (AT)__ldg(u + idx - plane) : zero;
-    AT u_cur = (in && k0 < nz) ? (AT)__ldg(u + idx) : zero;
-    double dv = 0.0;
-    for (int k = k0; k < k1; ++k) {
-        const AT u_next = (in && k + 1 < nz) ? (AT)__ldg(u + idx + plane) : zero;
-        AT xm = __shfl_up_sync(0xffffffffu, u_cur, 1);
-        AT xp = __shfl_down_sync(0xffffffffu, u_cur, 1);
-        if (lane == 0) xm = (in && i > 0) ? (AT)__ldg(u + idx - 1) : zero;
-        if (lane == kTX - 1) xp = (in && i + 1 < nx) ? (AT)__ldg(u + idx + 1) : zero;
-        if (in) {
-            const AT ym = j > 0 ? (AT)__ldg(u + idx - nx) : zero;
-            const AT yp = j + 1 < ny ? (AT)__ldg(u + idx + nx) : zero;
-            AT o = c.e0 * u_cur;
-            o = fma(c.ex, xm + xp, o);
-            o = fma(c.ey, ym + yp, o);
-            o = fma(c.ez, u_prev + u_next, o);
-            if (c.terms & kTermR) o = fma(c.cc, (AT)r[idx], o);
-            if (c.terms & kTermW) o = fma(c.cb, (AT)w[idx], o);
-            const YT yo = (YT)o;
-            y[idx] = yo;
-            if (DOT == 1) dv += rdot[idx] * (double)yo;
-            if (DOT == 2) dv += (double)u_cur * (double)yo;
-        }
-        u_prev = u_cur;
-        u_cur = u_next;
-        idx += plane;
-    }
+    const double dv = stencil_tile<XT, YT, DOT>(nx, ny, nz, blockIdx.x, blockIdx.y, k0, k1, u, w, r, y, c, rdot,
+                                                threadIdx.x, threadIdx.y);
     if (DOT != 0) {
         const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
         const int nb = gridDim.x * gridDim.y * gridDim.z;

@@ -1,0 +1,66 @@
+// Device-side 7-point stencil tile: the fused Chebyshev step over one
+// 32 x 8 tile of (x, y) and a chunk of z planes (see nc_stencil.cu for the
+// layout).  Shared by the single-system kernel and the batched engine.
+#pragma once
+
+#include "nc_step.cuh"
+
+namespace nc {
+
+constexpr int kTX = 32, kTY = 8;
+
+template <typename AT>
+struct StencilCoef {
+    AT e0, ex, ey, ez, cb, cc;
+    int terms;   // kTermW / kTermR
+};
+
+// y = e0 u + ex (u_{i-1}+u_{i+1}) + ey (u_{j-1}+u_{j+1}) + ez (u_{k-1}+u_{k+1})
+//     + cb w + cc r over planes [k0, k1) of tile (bx, by).  DOT 1: returns
+// this thread's sum of rdot*y, DOT 2: u*y, DOT 3: y*y.  Must be called by all
+// 32 lanes of a warp together (shuffles).
+template <typename XT, typename YT, int DOT>
+__device__ __forceinline__ double stencil_tile(const int nx, const int ny, const int nz, const int bx, const int by,
+                                               const int k0, const int k1, const XT* __restrict__ u,
+                                               const XT* __restrict__ w, const XT* __restrict__ r,
+                                               YT* __restrict__ y, const StencilCoef<typename AccOf<XT>::type>& c,
+                                               const double* __restrict__ rdot, const int lane, const int ty) {
+    using AT = typename AccOf<XT>::type;
+    const int i = bx * kTX + lane;
+    const int j = by * kTY + ty;
+    const bool in = i < nx && j < ny;
+    const long long plane = (long long)nx * ny;
+    long long idx = ((long long)k0 * ny + j) * nx + i;
+    const AT zero = AT(0);
+    AT u_prev = (in && k0 > 0) ? (AT)__ldg(u + idx - plane) : zero;
+    AT u_cur = (in && k0 < nz) ? (AT)__ldg(u + idx) : zero;
+    double dv = 0.0;
+    for (int k = k0; k < k1; ++k) {
+        const AT u_next = (in && k + 1 < nz) ? (AT)__ldg(u + idx + plane) : zero;
+        AT xm = __shfl_up_sync(0xffffffffu, u_cur, 1);
+        AT xp = __shfl_down_sync(0xffffffffu, u_cur, 1);
+        if (lane == 0) xm = (in && i > 0) ? (AT)__ldg(u + idx - 1) : zero;
+        if (lane == kTX - 1) xp = (in && i + 1 < nx) ? (AT)__ldg(u + idx + 1) : zero;
+        if (in) {
+            const AT ym = j > 0 ? (AT)__ldg(u + idx - nx) : zero;
+            const AT yp = j + 1 < ny ? (AT)__ldg(u + idx + nx) : zero;
+            AT o = c.e0 * u_cur;
+            o = fma(c.ex, xm + xp, o);
+            o = fma(c.ey, ym + yp, o);
+            o = fma(c.ez, u_prev + u_next, o);
+            if (c.terms & kTermR) o = fma(c.cc, (AT)r[idx], o);
+            if (c.terms & kTermW) o = fma(c.cb, (AT)w[idx], o);
+            const YT yo = (YT)o;
+            y[idx] = yo;
+            if (DOT == 1) dv += rdot[idx] * (double)yo;
+            if (DOT == 2) dv += (double)u_cur * (double)yo;
+            if (DOT == 3) dv += (double)yo * (double)yo;
+        }
+        u_prev = u_cur;
+        u_cur = u_next;
+        idx += plane;
+    }
+    return dv;
+}
+
+}  // namespace nc
