@@ -1,7 +1,7 @@
 #!/usr/bin/env python3
 """Benchmark of Newton-Chebyshev preconditioned CG on one GB300.
 
-Workload (one "step" = one full PCG solve to ||r||/||b|| <= 1e-8):
+Default workload (one "step" = one full PCG solve to ||r||/||b|| <= 1e-8):
 3D 7-point variable-coefficient diffusion on a 128^3 grid (n = 2,097,152,
 nnz = 14,581,760), per-point log-normal coefficients (sigma = 1),
 harmonic face averages, Dirichlet boundary; CSR float64; Jacobi scaled;
@@ -15,12 +15,22 @@ fused SpMV + Chebyshev step kernel and the FP64 oracle timed on the host.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--k 20] [--apply f64|f32|bf16]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the same workload
+  python bench.py --workload c1|c3|c4|c5 # the other workloads (one JSON line each):
+      c1  64x64 5-point Laplacian, CSR, k = 8, exact bounds, plain FP64 (latency)
+      c3  Q1-hex elasticity 100^3 nodes x 3 dofs, 3x3 BSR, FP64 vs FP32 apply
+          with FP64 residual replacement every 50 iterations
+      c4  256 anisotropic 7-point systems, sides U{16..96}, 1-8 RHS, k in
+          [8, 32], all in one batched launch (FP32 apply, FP64 CG) vs the
+          plain FP64 solver one system at a time
+      c5  serving: Poisson arrivals of 7-point Poisson systems 16^3..320^3
+          (1% 512^3), continuous batching vs plain FP64 one at a time
 N > 1 runs independent replicas (one per GPU, launched by torchrun).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -41,12 +51,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--k", type=int, default=20)
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--k", type=int, default=None, help="polynomial degree (default: the workload's)")
     ap.add_argument("--apply", default="f64", choices=["f64", "f32", "bf16"])
-    ap.add_argument("--grid", type=int, default=GRID)
+    ap.add_argument("--grid", type=int, default=None, help="grid side (c2) or nodes per side (c3)")
+    ap.add_argument("--requests", type=int, default=120, help="c5: number of requests")
     ap.add_argument("--no-modes", action="store_true", help="skip the other apply precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--oracle-iters", type=int, default=6, help="PCG iterations per oracle sample")
+    ap.add_argument("--gpu-iters", type=int, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the PCG loop from the host instead of the device-side graph "
                          "(same kernels; lets a profiler list every launch)")
@@ -60,6 +73,7 @@ def dist_env():
 
 # ---------------------------------------------------------------- clocks ----
 class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -98,43 +112,116 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-# ------------------------------------------------------------ workload ------
-def make_system(grid):
-    import workloads as W
-    A = W.diffusion_3d_7pt_lognormal(grid, seed=SEED_A)
-    return A
+def start_clocks(torch, dev):
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    return Clocks(uuid)
 
 
-def algorithmic_step_bytes(n, nnz, sv=8, sx=8):
-    """Bytes one fused Chebyshev step must move: A once (values + int32
-    columns + int32 row pointers), x_{k-1}, x_{k-2}, r read once, x_k written."""
+def peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ byte models ---
+def csr_step_bytes(n, nnz, sv=8, sx=8):
+    """One fused Chebyshev step, CSR: A once (values + int32 columns + int32
+    row pointers), x_{k-1}, x_{k-2}, r read once, x_k written."""
     return nnz * (sv + 4) + 4 * (n + 1) + 4 * n * sx
 
 
-# ---------------------------------------------------------------- ours ------
-def run_ours(args, rank, world, local_rank):
+def bsr3_step_bytes(n, nnzb, sv=8, sx=8):
+    """One fused Chebyshev step, 3x3 BSR: blocks once (9 values + int32 block
+    column), block-row pointers, 4 vector passes."""
+    return nnzb * (9 * sv + 4) + 4 * (n // 3 + 1) + 4 * n * sx
+
+
+SV = {"f64": 8, "f32": 4, "bf16": 2}
+
+
+# ------------------------------------------------------ workload specs ------
+def spec_c2(args):
+    import workloads as W
+    grid = args.grid or GRID
+    A = W.diffusion_3d_7pt_lognormal(grid, seed=SEED_A)
+    rhs = [W.uniform_vector(A.n, seed=SEED_B + i) for i in range(4)]
+    return dict(kind="csr", A=A, n=A.n, nnz=A.nnz, jacobi=True, bounds="lanczos", k=args.k or 20, s=S_THETA,
+                rhs=rhs, rr_mixed=0,
+                bytes=lambda mode: csr_step_bytes(A.n, A.nnz, SV[mode], 8 if mode == "f64" else 4),
+                workload=f"diffusion3d-7pt lognormal {grid}^3 CSR (n={A.n}, nnz={A.nnz}), Jacobi-scaled",
+                key=f"c2:{A.n}", l2=f"inputs larger than L2 (A = {A.nnz * 12 / 1e6:.0f} MB)")
+
+
+def spec_c1(args):
+    import workloads as W
+    A = W.laplacian_2d_5pt(64, 64)
+    lo, hi = W.laplacian_2d_bounds(64, 64)
+    rhs = [W.rhs_from_solution(A, W.uniform_vector(A.n, seed=1 + i)) for i in range(4)]
+    return dict(kind="csr", A=A, n=A.n, nnz=A.nnz, jacobi=False, bounds=(lo, hi), k=args.k or 8, s=1.0, rhs=rhs,
+                rr_mixed=0, bytes=lambda mode: csr_step_bytes(A.n, A.nnz, SV[mode], 8 if mode == "f64" else 4),
+                workload="laplacian2d-5pt 64x64 CSR (n=4096, nnz=20224), exact bounds 4sin^2(pi i/130) sums, b=A x*",
+                key=f"c1:{A.n}", l2="L2-resident system (0.4 MB); latency-bound by construction")
+
+
+def spec_c3(args):
+    import workloads as W
+    N = args.grid or 100
+    A, b = W.elasticity_q1_bsr3(N, seed=SEED_A)
+    return dict(kind="bsr3", A=A, n=A.n, nnz=A.nnzb, jacobi=True, bounds="lanczos", k=args.k or 20, s=S_THETA,
+                rhs=[b], rr_mixed=50,
+                bytes=lambda mode: bsr3_step_bytes(A.n, A.nnzb, SV[mode], 8 if mode == "f64" else 4),
+                workload=f"elasticity Q1-hex {N}^3 nodes x 3 dofs 3x3-BSR (n={A.n}, blocks={A.nnzb}), "
+                         "nu~U[0.25,0.45], bottom clamped, unit body load, Jacobi-scaled",
+                key=f"c3:{A.n}", l2=f"inputs larger than L2 (A = {A.nnzb * 76 / 1e6:.0f} MB)")
+
+
+# -------------------------------------------------- single-system runner ----
+def run_system(args, spec, rank, world, local_rank):
     import numpy as np
     import torch
     torch.cuda.set_device(local_rank)
-    from paper_2008_01440_gb300.build import build
-    build()
     import paper_2008_01440_gb300 as nc
     import workloads as W
 
-    A = make_system(args.grid)
-    n, nnz = A.n, A.nnz
     dev = torch.device("cuda", local_rank)
-    rp = torch.from_numpy(A.rowptr).to(dev)
-    cl = torch.from_numpy(A.col).to(dev)
-    vl = torch.from_numpy(A.val).to(dev)
-    M0 = nc.nc_matrix_csr(rp, cl, vl)
-    M = nc.nc_matrix_jacobi(M0)
-    v0 = torch.from_numpy(W.uniform_vector(n, seed=SEED_V0)).to(dev)
-    lo, hi, rmin, rmax = nc.nc_bounds_lanczos(M, 20, v0)
-    n_rhs = 4
-    bs = [torch.from_numpy(W.uniform_vector(n, seed=SEED_B + i)).to(dev) for i in range(n_rhs)]
+    A = spec["A"]
+    n = spec["n"]
+    k = spec["k"]
+    if spec["kind"] == "csr":
+        M0 = nc.nc_matrix_csr(torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.col).to(dev),
+                              torch.from_numpy(A.val).to(dev))
+    else:
+        M0 = nc.nc_matrix_bsr3(torch.from_numpy(A.browptr).to(dev), torch.from_numpy(A.bcol).to(dev),
+                               torch.from_numpy(A.val.reshape(-1)).to(dev))
+    M = nc.nc_matrix_jacobi(M0) if spec["jacobi"] else M0
+    if spec["bounds"] == "lanczos":
+        v0 = torch.from_numpy(W.uniform_vector(n, seed=SEED_V0)).to(dev)
+        lo, hi, _, _ = nc.nc_bounds_lanczos(M, 20, v0)
+    else:
+        lo, hi = spec["bounds"]
+    bs = [torch.from_numpy(np.ascontiguousarray(b)).to(dev) for b in spec["rhs"]]
+    n_rhs = len(bs)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def allmax(v):
+        if world == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
 
     def timed_solves(S, steps, warmup):
         for i in range(warmup):
@@ -151,19 +238,6 @@ def run_ours(args, rank, world, local_rank):
         total = ev[0][0].elapsed_time(ev[-1][1])
         return lat, total, results
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def allmax(v):
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     def time_step_kernel(S, mode):
         """Average duration of one fused-step launch: CUDA events around
         `reps` applications of P_k (k launches each) on the launching stream."""
@@ -178,27 +252,18 @@ def run_ours(args, rank, world, local_rank):
             nc.pcg_apply_poly(S, bs[0], z)
         e1.record(stream)
         torch.cuda.synchronize()
-        per_launch_s = e0.elapsed_time(e1) / 1e3 / (reps * max(args.k, 1))
-        sv = {"f64": 8, "f32": 4, "bf16": 2}[mode]
-        sx = 8 if mode == "f64" else 4
-        nbytes = algorithmic_step_bytes(n, nnz, sv, sx)
-        return per_launch_s, nbytes
+        per_launch_s = e0.elapsed_time(e1) / 1e3 / (reps * max(k, 1))
+        return per_launch_s, spec["bytes"](mode)
 
     modes = [args.apply] + ([] if args.no_modes else [m for m in ("f64", "f32", "bf16") if m != args.apply])
     out_modes = {}
     main = None
     for mode in modes:
-        S = nc.pcg_setup(M, lo, hi, args.k, S_THETA, apply_dtype=mode, x0_is_zero=True,
+        rr = spec["rr_mixed"] if mode != "f64" else 0
+        S = nc.pcg_setup(M, lo, hi, k, spec["s"], apply_dtype=mode, x0_is_zero=True, rr_period=rr,
                          use_graph=not args.host_loop)
         barrier()
-        clk = None
-        if mode == args.apply:
-            uuid = None
-            try:
-                uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-            except Exception:
-                uuid = None
-            clk = Clocks(uuid)
+        clk = start_clocks(torch, dev) if mode == args.apply else None
         torch.cuda.synchronize()
         barrier()
         lat, total_ms, results = timed_solves(S, args.steps, args.warmup)
@@ -206,39 +271,33 @@ def run_ours(args, rank, world, local_rank):
         clocks = clk.stop() if clk else None
         total_ms = allmax(total_ms)
         iters = [r["iters"] for r in results]
-        ok = all(r["status"] == 0 for r in results)
         rec = {"solves_per_s": world * args.steps / (total_ms / 1e3), "ms_per_solve": total_ms / args.steps,
                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-               "iters": iters[0], "iters_range": [min(iters), max(iters)], "all_converged": ok,
+               "iters": iters[0], "iters_range": [min(iters), max(iters)],
+               "all_converged": all(r["status"] == 0 for r in results),
                "max_relres": max(r["relres"] for r in results),
-               "max_true_relres": max(r["true_relres"] for r in results)}
+               "max_true_relres": max(r["true_relres"] for r in results), "rr_period": rr,
+               "layout": nc.pcg_get_info(S)["spmv_format"]}
         t_launch, nbytes = time_step_kernel(S, mode)
         rec["step_us"] = round(t_launch * 1e6, 2)
         rec["step_GBps"] = round(nbytes / t_launch / 1e9, 1)
         out_modes[mode] = rec
         if mode == args.apply:
-            main = dict(rec=rec, S=S, clocks=clocks, results=results)
+            main = dict(rec=rec, S=S, clocks=clocks)
         else:
             S.close()
 
     S = main["S"]
     rec = main["rec"]
-    k = max(args.k, 1)
-    # --- kernel timing: the fused step kernel, k launches per apply ---------------------
     per_launch_s, step_bytes = time_step_kernel(S, args.apply)
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    peak, peak_src = peak_hbm()
     achieved = step_bytes / per_launch_s / 1e9
+    kname = {"csr": "sell_step_kernel (fused SpMV + Chebyshev recurrence, SELL-32)",
+             "bsr3": "bsell3_step_kernel (fused 3x3-block SpMV + Chebyshev recurrence, BSELL-32)"}[spec["kind"]]
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
-                "kernel": "csr_step_kernel (fused SpMV + Chebyshev recurrence)",
-                "bytes_per_launch": step_bytes, "us_per_launch": round(per_launch_s * 1e6, 2)}
+                "frac": round(achieved / peak, 4), "traffic": read_traffic(spec["key"], args.apply),
+                "peak_source": peak_src, "kernel": kname, "bytes_per_launch": step_bytes,
+                "us_per_launch": round(per_launch_s * 1e6, 2)}
 
     # --- end to end through the host-buffer C-ABI call ---------------------------------
     hb = [bb.cpu().pin_memory() for bb in bs]
@@ -247,31 +306,30 @@ def run_ours(args, rank, world, local_rank):
         nc.pcg_solve_host(S, hb[i % n_rhs], hx, TOL, MAXIT)
     barrier()
     t0 = time.perf_counter()
-    e2e_res = []
     for i in range(args.steps):
-        e2e_res.append(nc.pcg_solve_host(S, hb[i % n_rhs], hx, TOL, MAXIT))
+        nc.pcg_solve_host(S, hb[i % n_rhs], hx, TOL, MAXIT)
     torch.cuda.synchronize()
     e2e_s = allmax(time.perf_counter() - t0)
     e2e = {"value": world * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": n * 8,
            "d2h_bytes_per_step": n * 8 + 48}
 
-    # --- oracle on the host (rank 0, one GPU only) ---------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline_subprocess(args)
+        cpu = cpu_baseline_subprocess(args, rec["iters"])
 
     iters = rec["iters"]
-    launches_per_solve = 1 + (4 + k + (1 if args.apply != "f64" else 0)) + iters * (k + 3) + 3
+    kk = max(k, 1)
+    launches_per_solve = 1 + (4 + kk + (1 if args.apply != "f64" else 0)) + iters * (kk + 3) + 3
     line = {
         "metric": METRIC, "value": round(rec["solves_per_s"], 3), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(rec["ms_per_solve"], 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.apply == "f64" else f"{args.apply}-apply+f64-outer",
         "data": "synthetic (seeded generators, no dataset)",
-        "config": {"workload": f"diffusion3d-7pt lognormal {args.grid}^3 CSR (n={n}, nnz={nnz}), Jacobi-scaled",
-                   "degree_k": args.k, "theta_scale": S_THETA, "tol": TOL, "bounds": "lanczos-20",
-                   "lmin": lo, "lmax": hi, "rhs": f"{n_rhs} seeded U[-1,1], cycled",
-                   "l2": "inputs larger than L2 (A = %.0f MB)" % (nnz * 12 / 1e6), "parallelism": f"replicas x{world}"},
+        "config": {"workload": spec["workload"], "degree_k": k, "theta_scale": spec["s"], "tol": TOL,
+                   "bounds": "lanczos-20" if spec["bounds"] == "lanczos" else "exact closed form",
+                   "lmin": lo, "lmax": hi, "rhs": f"{n_rhs} seeded, cycled", "l2": spec["l2"],
+                   "parallelism": f"replicas x{world}"},
         "p50_ms": round(rec["p50_ms"], 3), "p99_ms": round(rec["p99_ms"], 3), "iters": iters,
         "all_converged": rec["all_converged"], "max_relres": rec["max_relres"],
         "clocks": main["clocks"], "e2e": e2e, "gpu_launches": launches_per_solve * args.steps,
@@ -281,11 +339,30 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_subprocess(args):
+def read_traffic(key, mode):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    (profiles/traffic.txt lines `<workload>:<n> <mode> <bytes>`), else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        with open(path) as f:
+            for line in f:
+                p = line.split()
+                if len(p) >= 3 and not line.startswith("#") and p[0] == key and p[1] == mode:
+                    return int(p[2])
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline_subprocess(args, gpu_iters):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "1", "--warmup", "0",
-           "--k", str(args.k), "--grid", str(args.grid), "--oracle-iters", str(args.oracle_iters)]
+           "--workload", args.workload, "--oracle-iters", str(args.oracle_iters), "--gpu-iters", str(gpu_iters)]
+    if args.k:
+        cmd += ["--k", str(args.k)]
+    if args.grid:
+        cmd += ["--grid", str(args.grid)]
     try:
         r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
         line = [ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1]
@@ -301,54 +378,273 @@ def cpu_baseline_subprocess(args):
 def run_reference(args, rank, world):
     """The FP64 oracle as it stands, timed on the host cores: each step runs
     `oracle_iters` PCG iterations of the full workload and the rate is
-    extrapolated with the oracle's own full-solve iteration count."""
+    extrapolated with a full-solve iteration count (the oracle's own, from
+    tests/golden/c2_oracle.json, for the default workload)."""
     if rank != 0:
         return
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     import numpy as np
     import oracle as O
     import workloads as W
-    A = make_system(args.grid)
-    val, dis = O.jacobi_scale_csr(A.rowptr, A.col, A.val, A.n)
-    mv = O.csr_matvec(A.rowptr, A.col, val, A.n)
+    spec = {"c1": spec_c1, "c2": spec_c2, "c3": spec_c3}.get(args.workload)
+    if spec is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle timing for workload {args.workload}"}))
+        return
+    sp = spec(args)
+    A = sp["A"]
+    k = sp["k"]
+    if sp["kind"] == "csr":
+        if sp["jacobi"]:
+            val, dis = O.jacobi_scale_csr(A.rowptr, A.col, A.val, A.n)
+        else:
+            val, dis = A.val, np.ones(A.n)
+        mv = O.csr_matvec(A.rowptr, A.col, val, A.n)
+        rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+        gersh = float(np.bincount(rows, weights=np.abs(val), minlength=A.n).max())
+    else:
+        val, dis = O.jacobi_scale_bsr3(A.browptr, A.bcol, A.val, A.nb)
+        mv = O.bsr3_matvec(A.browptr, A.bcol, val, A.nb)
+        brows = np.repeat(np.arange(A.nb), np.diff(A.browptr))
+        rs = np.zeros(A.n)
+        np.add.at(rs, (3 * brows[:, None] + np.arange(3)[None, :]).ravel(), np.abs(val).sum(axis=2).ravel())
+        gersh = float(rs.max())
     golden = None
-    if args.grid == GRID and os.path.exists(GOLDEN):
+    if args.workload == "c2" and (args.grid in (None, GRID)) and os.path.exists(GOLDEN):
         with open(GOLDEN) as f:
             golden = json.load(f)
-    if golden is not None and str(args.k) in golden["solves"]:
+    iters_src = "oracle's"
+    if golden is not None and str(k) in golden["solves"]:
         lo, hi = golden["lmin"], golden["lmax"]
-        full_iters = golden["solves"][str(args.k)]["iters"]
+        full_iters = golden["solves"][str(k)]["iters"]
     else:
-        rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
-        g = float(np.bincount(rows, weights=np.abs(val), minlength=A.n).max())
-        lo, hi, _ = O.lanczos_bounds(mv, W.uniform_vector(A.n, seed=SEED_V0), 20, gershgorin=g)
+        if sp["bounds"] == "lanczos":
+            lo, hi, _ = O.lanczos_bounds(mv, W.uniform_vector(A.n, seed=SEED_V0), 20, gershgorin=gersh)
+        else:
+            lo, hi = sp["bounds"]
         full_iters = None
-    prm = O.cheb_params(lo, hi, S_THETA)
-    b = dis * W.uniform_vector(A.n, seed=SEED_B)
+    prm = O.cheb_params(lo, hi, sp["s"])
+    b = dis * sp["rhs"][0]
     m = args.oracle_iters
+    if full_iters is None and args.workload == "c1":
+        # small enough to run the whole oracle solve
+        full_iters = O.pcg(mv, b, lambda r: O.cheb_apply(mv, r, prm, k), m=k, tol=TOL, maxit=MAXIT).iters
+    if full_iters is None:
+        full_iters = args.gpu_iters or 1
+        iters_src = "GPU solver's (equal within +-1 in the parity tests)"
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        res = O.pcg(mv, b, lambda r: O.cheb_apply(mv, r, prm, args.k), m=args.k, tol=TOL, maxit=m)
+        res = O.pcg(mv, b, lambda r: O.cheb_apply(mv, r, prm, k), m=k, tol=TOL, maxit=min(m, full_iters))
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt / max(res.iters, 1))
-        if full_iters is None and i == 0:
-            full = O.pcg(mv, b, lambda r: O.cheb_apply(mv, r, prm, args.k), m=args.k, tol=TOL, maxit=MAXIT)
-            full_iters = full.iters
     t_iter = statistics.median(times)
-    value = 1.0 / (t_iter * full_iters)
-    sample = (f"{m} PCG iterations (k={args.k}, {m * (args.k + 1)} SpMVs) of the full {args.grid}^3 system per step, "
-              f"extrapolated to the oracle's {full_iters}-iteration solve; scipy CSR matvec + numpy, 1 thread")
+    value = 1.0 / (t_iter * max(full_iters, 1))
+    sample = (f"{min(m, full_iters)} PCG iterations (k={k}) of the full system per step, extrapolated to the "
+              f"{iters_src} {full_iters}-iteration solve; scipy sparse matvec + numpy, 1 thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * full_iters * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generators, no dataset)",
-            "config": {"workload": f"diffusion3d-7pt lognormal {args.grid}^3 CSR (n={A.n}, nnz={A.nnz}), Jacobi-scaled",
-                       "degree_k": args.k, "theta_scale": S_THETA, "tol": TOL},
+            "config": {"workload": sp["workload"], "degree_k": k, "theta_scale": sp["s"], "tol": TOL},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- batched ------
+def c4_systems(seed=41):
+    """256 anisotropic 7-point Laplacians: sides U{16..96} per axis, axis
+    weights U[0.01, 1], 1-8 right-hand sides, degree U{8..32}; exact bounds of
+    the Jacobi-scaled operator (closed form)."""
+    import numpy as np
+    import workloads as W
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(256):
+        nx, ny, nz = (int(v) for v in rng.integers(16, 97, 3))
+        wx, wy, wz = rng.uniform(0.01, 1.0, 3)
+        st = W.stencil7_aniso(nx, ny, nz, wx, wy, wz)
+        nrhs = int(rng.integers(1, 9))
+        k = int(rng.integers(8, 33))
+        c0 = st.c0
+        sc = W.Stencil7(nx, ny, nz, 1.0, st.cx / c0, st.cy / c0, st.cz / c0)
+        lo, hi = W.stencil7_bounds(sc)
+        out.append(dict(st=st, nrhs=nrhs, k=k, lo=lo, hi=hi, seed=1000 + i))
+    return out
+
+
+def run_c4(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    import paper_2008_01440_gb300 as nc
+    dev = torch.device("cuda", local_rank)
+    sy = c4_systems()
+    pairs = []
+    for s in sy:
+        g = torch.Generator(device=dev)
+        g.manual_seed(s["seed"])
+        for _ in range(s["nrhs"]):
+            b = torch.rand(s["st"].n, generator=g, dtype=torch.float64, device=dev) * 2.0 - 1.0
+            pairs.append((s, b))
+    units = sum(p[0]["st"].n for p in pairs)
+    eng = nc.pcg_batch_create(len(pairs), units, 32)
+    xs = [torch.empty(p[0]["st"].n, dtype=torch.float64, device=dev) for p in pairs]
+
+    def one_batch():
+        slots = []
+        for s, b in pairs:
+            st = s["st"]
+            slots.append(nc.pcg_batch_add(eng, st.nx, st.ny, st.nz, st.c0, st.cx, st.cy, st.cz, s["lo"], s["hi"],
+                                          s["k"], S_THETA, b))
+        nc.pcg_batch_run(eng, TOL, MAXIT, 0)
+        res = []
+        for sl, x in zip(slots, xs):
+            _, r = nc.pcg_batch_status(eng, sl)
+            nc.pcg_batch_collect(eng, sl, x)
+            res.append(r)
+        for sl in slots:
+            nc.pcg_batch_release(eng, sl)
+        return res
+
+    for _ in range(args.warmup):
+        one_batch()
+    torch.cuda.synchronize()
+    clk = start_clocks(torch, dev)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res = one_batch()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    clocks = clk.stop()
+    t_step = statistics.median(times)
+    iters = [r["iters"] for r in res]
+    ok = all(r["status"] == 0 and r["true_relres"] <= 2 * TOL for r in res)
+    # algorithmic bytes of the whole batch: per slot and iteration, k float32
+    # stencil steps (16 B per unknown), q = A p (16 B), x/r/p/q update with
+    # the float copy of r (52 B), p update (24 B)
+    tot_bytes = sum((16 * p[0]["k"] + 92) * p[0]["st"].n * max(r["iters"], 1) for p, r in zip(pairs, res))
+    peak, src = peak_hbm()
+    achieved = tot_bytes / t_step / 1e9
+    # plain FP64 one system at a time (same right-hand sides), bounded sample
+    t_budget = 90.0
+    t0 = time.perf_counter()
+    done_pairs = 0
+    for (s, b), x in zip(pairs, xs):
+        st = s["st"]
+        A = nc.nc_matrix_stencil7(st.nx, st.ny, st.nz, st.c0, st.cx, st.cy, st.cz)
+        As = nc.nc_matrix_jacobi(A)
+        S = nc.pcg_setup(As, s["lo"], s["hi"], s["k"], S_THETA, x0_is_zero=True)
+        nc.pcg_solve(S, b, x, TOL, MAXIT)
+        S.close()
+        done_pairs += 1
+        if time.perf_counter() - t0 > t_budget:
+            break
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    work = [p[0]["st"].n * max(r["iters"], 1) for p, r in zip(pairs, res)]
+    frac = sum(work[:done_pairs]) / sum(work)
+    plain_batch_rate = len(pairs) / (t_plain / frac)
+    line = {"metric": METRIC, "value": round(len(pairs) / t_step, 3), "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-apply+f64-outer",
+            "data": "synthetic (seeded generators; RHS from torch's CUDA generator, seeded)",
+            "config": {"workload": "batched: 256 anisotropic 7-point Laplacians, sides U{16..96}, weights U[0.01,1], "
+                                   "1-8 RHS, k U{8..32}, one batched launch per step",
+                       "systems": len(sy), "solves_per_step": len(pairs), "unknowns": units, "tol": TOL,
+                       "theta_scale": S_THETA, "bounds": "exact closed form of the scaled operator",
+                       "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+            "iters_range": [min(iters), max(iters)], "all_converged": ok, "clocks": clocks,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src,
+                         "kernel": "whole batched solve (all engine kernels; algorithmic bytes / wall time)"},
+            "plain_f64_one_at_a_time": {"solves_per_s": round(plain_batch_rate, 3),
+                                        "sample": f"{done_pairs} of {len(pairs)} solves in {t_plain:.1f} s, "
+                                                  "extrapolated by unknowns x iterations"},
+            "speedup_vs_plain_f64": round((len(pairs) / t_step) / plain_batch_rate, 2)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- serving ------
+def c5_requests(nreq, dev, torch, seed=51):
+    """Request sizes N^3 with log(N^3) ~ U[ln 16^3, ln 320^3], 1% N = 512;
+    constant 7-point Poisson operator (c0 = 6, c = 1), k = 31 (nlev = 5),
+    theta scale 1.001, RHS U[-1,1]; bounds of the Jacobi-scaled operator
+    1 -+ cos(pi/(N+1)) (closed form)."""
+    import numpy as np
+    from paper_2008_01440_gb300.serving import Request
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nreq):
+        N = 512 if rng.random() < 0.01 else int(round(math.exp(rng.uniform(math.log(16), math.log(320)))))
+        c = math.cos(math.pi / (N + 1))
+        g = torch.Generator(device=dev)
+        g.manual_seed(10_000 + i)
+        b = torch.rand(N ** 3, generator=g, dtype=torch.float64, device=dev) * 2.0 - 1.0
+        out.append(Request(rid=i, arrival=0.0, nx=N, ny=N, nz=N, c=(6.0, 1.0, 1.0, 1.0), lmin=1.0 - c,
+                           lmax=1.0 + c, k=31, s=S_THETA, b=b))
+    return out
+
+
+def run_c5(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2008_01440_gb300 import serving
+    dev = torch.device("cuda", local_rank)
+    reqs = c5_requests(args.requests, dev, torch)
+
+    def clone(r):
+        return serving.Request(rid=r.rid, arrival=r.arrival, nx=r.nx, ny=r.ny, nz=r.nz, c=r.c, lmin=r.lmin,
+                               lmax=r.lmax, k=r.k, s=r.s, b=r.b)
+
+    # calibrate the arrival rate: plain FP64 one-at-a-time utilisation 0.8
+    cal = [clone(r) for r in reqs[:8]]
+    serving.serve_one_at_a_time_fp64(cal[:1], TOL, MAXIT)       # warm-up
+    t_cal = serving.serve_one_at_a_time_fp64(cal, TOL, MAXIT)
+    mean_service = t_cal / len(cal)
+    lam = 0.8 / mean_service
+    rng = np.random.default_rng(52)
+    t = 0.0
+    for r in reqs:
+        t += rng.exponential(1.0 / lam)
+        r.arrival = t
+    budget = int(48e9 // 64)   # 48 GB of engine pools, 64 B per unknown
+    torch.cuda.synchronize()
+    clk = start_clocks(torch, dev)
+    span_cb = serving.serve_continuous(reqs, budget, 64, 31, TOL, MAXIT, iters_per_tick=2)
+    clocks = clk.stop()
+    lat_cb = [r.t_done - r.arrival for r in reqs]
+    ok_cb = all(r.result.get("status") == 0 and r.result.get("true_relres", 1) <= 2 * TOL for r in reqs)
+    iters_cb = [r.result["iters"] for r in reqs]
+    plain = [clone(r) for r in reqs]
+    span_pl = serving.serve_one_at_a_time_fp64(plain, TOL, MAXIT)
+    lat_pl = [r.t_done - r.arrival for r in plain]
+    ok_pl = all(r.result.get("status") == 0 for r in plain)
+    err = max(float(torch.linalg.norm(a.x - b.x) / torch.linalg.norm(b.x)) for a, b in zip(reqs[:16], plain[:16]))
+    sizes = [r.nx for r in reqs]
+    line = {"metric": METRIC, "value": round(len(reqs) / span_cb, 3), "unit": "solves/s", "n_gpus": world,
+            "steps": len(reqs), "warmup": 0, "ms_per_step": round(1e3 * span_cb / len(reqs), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-apply+f64-outer",
+            "data": "synthetic (seeded sizes and Poisson arrivals; RHS from torch's CUDA generator, seeded)",
+            "config": {"workload": "serving: Poisson arrivals, 7-point Poisson N^3, log-uniform 16^3..320^3, "
+                                   "1% 512^3, k=31, s=1.001, continuous batching (2 PCG iterations per tick)",
+                       "requests": len(reqs), "arrival_rate_per_s": round(lam, 3),
+                       "calibration": f"plain FP64 mean service {mean_service * 1e3:.1f} ms on 8 requests, "
+                                      "utilisation 0.8", "budget_GB": 48, "max_slots": 64,
+                       "sizes_min_median_max": [min(sizes), int(np.median(sizes)), max(sizes)],
+                       "n_512": sum(1 for s_ in sizes if s_ == 512), "parallelism": f"replicas x{world}"},
+            "p50_ms": round(1e3 * float(np.percentile(lat_cb, 50)), 2),
+            "p99_ms": round(1e3 * float(np.percentile(lat_cb, 99)), 2),
+            "all_converged": ok_cb, "iters_range": [min(iters_cb), max(iters_cb)], "clocks": clocks,
+            "plain_f64_one_at_a_time": {"solves_per_s": round(len(plain) / span_pl, 3),
+                                        "p50_ms": round(1e3 * float(np.percentile(lat_pl, 50)), 2),
+                                        "p99_ms": round(1e3 * float(np.percentile(lat_pl, 99)), 2),
+                                        "all_converged": ok_pl},
+            "max_rel_diff_vs_plain_f64_first16": err}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def main():
@@ -360,8 +656,13 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, rank, world)
+        elif args.workload == "c4":
+            run_c4(args, rank, world, local_rank)
+        elif args.workload == "c5":
+            run_c5(args, rank, world, local_rank)
         else:
-            run_ours(args, rank, world, local_rank)
+            spec = {"c1": spec_c1, "c2": spec_c2, "c3": spec_c3}[args.workload](args)
+            run_system(args, spec, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist
