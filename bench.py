@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--apply", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--grid", type=int, default=None, help="grid side (c2) or nodes per side (c3)")
     ap.add_argument("--requests", type=int, default=120, help="c5: number of requests")
+    ap.add_argument("--c4-systems", type=int, default=256, help="c4: number of systems")
     ap.add_argument("--no-modes", action="store_true", help="skip the other apply precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--oracle-iters", type=int, default=6, help="PCG iterations per oracle sample")
@@ -452,7 +453,7 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------- batched ------
-def c4_systems(seed=41):
+def c4_systems(count=256, seed=41):
     """256 anisotropic 7-point Laplacians: sides U{16..96} per axis, axis
     weights U[0.01, 1], 1-8 right-hand sides, degree U{8..32}; exact bounds of
     the Jacobi-scaled operator (closed form)."""
@@ -460,7 +461,7 @@ def c4_systems(seed=41):
     import workloads as W
     rng = np.random.default_rng(seed)
     out = []
-    for i in range(256):
+    for i in range(count):
         nx, ny, nz = (int(v) for v in rng.integers(16, 97, 3))
         wx, wy, wz = rng.uniform(0.01, 1.0, 3)
         st = W.stencil7_aniso(nx, ny, nz, wx, wy, wz)
@@ -478,7 +479,7 @@ def run_c4(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     import paper_2008_01440_gb300 as nc
     dev = torch.device("cuda", local_rank)
-    sy = c4_systems()
+    sy = c4_systems(args.c4_systems)
     pairs = []
     for s in sy:
         g = torch.Generator(device=dev)
@@ -487,7 +488,7 @@ def run_c4(args, rank, world, local_rank):
             b = torch.rand(s["st"].n, generator=g, dtype=torch.float64, device=dev) * 2.0 - 1.0
             pairs.append((s, b))
     units = sum(p[0]["st"].n for p in pairs)
-    eng = nc.pcg_batch_create(len(pairs), units, 32)
+    eng = nc.pcg_batch_create(len(pairs), units, 32, host_loop=args.host_loop)
     xs = [torch.empty(p[0]["st"].n, dtype=torch.float64, device=dev) for p in pairs]
 
     def one_batch():

@@ -237,7 +237,9 @@ NC_API nc_status pcg_destroy(nc_solver S);
  *
  * pcg_batch_create: capacity of max_slots slots and max_unknowns pooled
  *   unknowns (6 float64 + 4 float32 vectors each: 64 bytes per unknown,
- *   allocated once -- the HBM budget); kmax = largest degree accepted.
+ *   allocated once -- the HBM budget); kmax = largest degree accepted;
+ *   flags: 0, or NC_BATCH_HOST_LOOP to drive the same kernels from a host
+ *   loop (one synchronisation per iteration; for profilers).
  * pcg_batch_add: admit one system with right-hand side b_dev (n float64,
  *   read during the call).  NC_ERR_ADMISSION when no slot or pool space is
  *   free (retry after releasing finished slots).  The slot starts with the
@@ -250,7 +252,9 @@ NC_API nc_status pcg_destroy(nc_solver S);
  *   (unscaled) system; only for finished slots.
  * pcg_batch_release: free a finished slot and its memory.
  * pcg_batch_free_units: largest contiguous and total free pooled unknowns. */
-NC_API nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, void* stream, nc_batch* out);
+#define NC_BATCH_HOST_LOOP 1
+NC_API nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, int flags, void* stream,
+                                  nc_batch* out);
 NC_API nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx, double cy, double cz,
                                double lambda_min, double lambda_max, int degree_k, double theta_scale,
                                const double* b_dev, void* stream, int* slot);

@@ -83,7 +83,7 @@ _SIGS = {
     "nc_apply_poly_csr_noalloc": (ctypes.c_int, [_i64, _vp, _vp, _vp, _dbl, _dbl, ctypes.c_int, _dbl, _vp, _vp,
                                                  _vp]),
     "nc_apply_poly_noalloc_max_n": (_i64, []),
-    "pcg_batch_create": (ctypes.c_int, [ctypes.c_int, _i64, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "pcg_batch_create": (ctypes.c_int, [ctypes.c_int, _i64, ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
     "pcg_batch_add": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dbl, _dbl, _dbl, _dbl, _dbl,
                                      _dbl, ctypes.c_int, _dbl, _vp, _vp, ctypes.POINTER(ctypes.c_int)]),
     "pcg_batch_run": (ctypes.c_int, [_vp, _dbl, ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int)]),
@@ -351,10 +351,14 @@ class Batch:
             pass
 
 
-def pcg_batch_create(max_slots: int, max_unknowns: int, kmax: int, stream=None) -> Batch:
+NC_BATCH_HOST_LOOP = 1
+
+
+def pcg_batch_create(max_slots: int, max_unknowns: int, kmax: int, stream=None, host_loop: bool = False) -> Batch:
     h = _vp()
-    _check(lib.pcg_batch_create(int(max_slots), int(max_unknowns), int(kmax), _stream(stream), ctypes.byref(h)),
-           "pcg_batch_create")
+    flags = NC_BATCH_HOST_LOOP if host_loop else 0
+    _check(lib.pcg_batch_create(int(max_slots), int(max_unknowns), int(kmax), flags, _stream(stream),
+                                ctypes.byref(h)), "pcg_batch_create")
     return Batch(h.value)
 
 

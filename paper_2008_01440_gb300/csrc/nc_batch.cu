@@ -299,10 +299,10 @@ __global__ void __launch_bounds__(256) bk_true(const BDesc* __restrict__ D, BSta
     }
 }
 
-__global__ void bk_cond(BCtl* ctl, cudaGraphConditionalHandle h) {
+__global__ void bk_cond(BCtl* ctl, cudaGraphConditionalHandle h, int use_cond) {
     ctl->iters_this_call += 1;
     const int go = ctl->active > 0 && ctl->iters_this_call < ctl->iter_limit;
-    cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (use_cond) cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 __global__ void bk_scale(int n, const double* __restrict__ in, double s, double* __restrict__ out) {
@@ -315,6 +315,7 @@ __global__ void bk_scale(int n, const double* __restrict__ in, double s, double*
 using namespace nc;
 
 struct nc_batch_s {
+    int flags = 0;
     int cap_slots = 0;
     int64_t cap_units = 0;        // unknowns the pools hold
     int kmax = 0;
@@ -416,6 +417,18 @@ nc_status grow(void** p, int* cap, int need, size_t elem) {
     return NC_OK;
 }
 
+// One PCG iteration of every slot (the graph body).
+void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, cudaStream_t st) {
+    const dim3 tb(kTX, kTY);
+    bk_opq<<<kBatchGrid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
+    bk_axpy<<<kBatchGrid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
+    for (int j = 1; j <= B->kmax; ++j)
+        bk_cheb<<<kBatchGrid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_coef, B->d_ctl, B->d_partials, j);
+    bk_pupd<<<kBatchGrid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
+    bk_true<<<kBatchGrid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
+    bk_cond<<<1, 1, 0, st>>>(B->d_ctl, h, use_cond);
+}
+
 nc_status build_batch_graph(nc_batch B) {
     if (B->exec) {
         cudaGraphExecDestroy(B->exec);
@@ -437,15 +450,7 @@ nc_status build_batch_graph(nc_batch B) {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         if ((e = cudaStreamBeginCaptureToGraph(B->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
             break;
-        const dim3 tb(kTX, kTY);
-        bk_opq<<<kBatchGrid, tb, 0, B->cap>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
-        bk_axpy<<<kBatchGrid, 256, 0, B->cap>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
-        for (int j = 1; j <= B->kmax; ++j)
-            bk_cheb<<<kBatchGrid, tb, 0, B->cap>>>(B->d_desc, B->d_state, B->d_tiles, B->d_coef, B->d_ctl,
-                                                   B->d_partials, j);
-        bk_pupd<<<kBatchGrid, 256, 0, B->cap>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
-        bk_true<<<kBatchGrid, tb, 0, B->cap>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
-        bk_cond<<<1, 1, 0, B->cap>>>(B->d_ctl, h);
+        enqueue_iteration(B, h, 1, B->cap);
         cudaError_t e1 = cudaGetLastError();
         cudaGraph_t tmp = nullptr;
         e = cudaStreamEndCapture(B->cap, &tmp);
@@ -517,12 +522,13 @@ extern "C" {
 
 const char* nc_batch_last_cuda_error(void) { return cudaGetErrorString(g_batch_err); }
 
-nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, void* stream, nc_batch* out) {
+nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, int flags, void* stream, nc_batch* out) {
     if (!out) return NC_ERR_ARG;
     *out = nullptr;
-    if (max_slots < 1 || max_unknowns < 1 || kmax < 1 || kmax > 4096) return NC_ERR_ARG;
+    if (max_slots < 1 || max_unknowns < 1 || kmax < 1 || kmax > 4096 || (flags & ~NC_BATCH_HOST_LOOP)) return NC_ERR_ARG;
     nc_batch B = new (std::nothrow) nc_batch_s();
     if (!B) return NC_ERR_OOM;
+    B->flags = flags;
     B->cap_slots = max_slots;
     B->cap_units = max_unknowns;
     B->kmax = kmax;
@@ -652,7 +658,18 @@ nc_status pcg_batch_run(nc_batch B, double tol, int maxit, int iter_limit, void*
         c->iters_this_call = 0;
         c->iter_limit = iter_limit > 0 ? iter_limit : 0x7fffffff;
         NB_CU(cudaMemcpyAsync(B->d_ctl, c, sizeof(BCtl), cudaMemcpyHostToDevice, st));
-        NB_CU(cudaGraphLaunch(B->exec, st));
+        if (B->flags & NC_BATCH_HOST_LOOP) {
+            // the same kernels driven from the host, one iteration at a time
+            for (;;) {
+                enqueue_iteration(B, 0, 0, st);
+                NB_CU(cudaGetLastError());
+                NB_CU(cudaMemcpyAsync(c, B->d_ctl, sizeof(BCtl), cudaMemcpyDeviceToHost, st));
+                NB_CU(cudaStreamSynchronize(st));
+                if (!(c->active > 0 && c->iters_this_call < c->iter_limit)) break;
+            }
+        } else {
+            NB_CU(cudaGraphLaunch(B->exec, st));
+        }
         NB_CU(cudaMemcpyAsync(c, B->d_ctl, sizeof(BCtl), cudaMemcpyDeviceToHost, st));
         NB_CU(cudaMemcpyAsync(B->h_state, B->d_state, sizeof(BState) * B->cap_slots, cudaMemcpyDeviceToHost, st));
         NB_CU(cudaStreamSynchronize(st));

@@ -41,8 +41,10 @@ bsr3_step_kernel(const int nb, const int32_t* __restrict__ browptr, const int32_
                  const double* __restrict__ rdot, const Reduce R, const int* __restrict__ done) {
     using AT = typename AccOf<XT>::type;
     if (done != nullptr && *done) return;
-    const int br = blockIdx.x * kBlock + threadIdx.x;
     double dv = 0.0;
+    const int ntiles = (nb + kBlock - 1) / kBlock;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int br = tile * kBlock + threadIdx.x;
     if (br < nb) {
         AT acc[3] = {AT(0), AT(0), AT(0)};
         for (int p = browptr[br]; p < browptr[br + 1]; ++p) {
@@ -56,7 +58,8 @@ bsr3_step_kernel(const int nb, const int32_t* __restrict__ browptr, const int32_
                 acc[t] = fma((AT)ld_val(b + 3 * t + 2), x2, acc[t]);
             }
         }
-        dv = bsr_rows_out<XT, YT, DOT, AT>(br, acc, c, u, w, r, y, rdot);
+        dv += bsr_rows_out<XT, YT, DOT, AT>(br, acc, c, u, w, r, y, rdot);
+    }
     }
     if (DOT != 0) grid_reduce<kBlock>(dv, R);
 }
@@ -72,8 +75,10 @@ bsell3_step_kernel(const int nb, const int32_t* __restrict__ slice_ptr, const in
                    const double* __restrict__ rdot, const Reduce R, const int* __restrict__ done) {
     using AT = typename AccOf<XT>::type;
     if (done != nullptr && *done) return;
-    const int br = blockIdx.x * kBlock + threadIdx.x;
     double dv = 0.0;
+    const int ntiles = (nb + kBlock - 1) / kBlock;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int br = tile * kBlock + threadIdx.x;
     if (br < nb) {
         const int s = br >> 5, lane = br & 31;
         const int beg = slice_ptr[s];
@@ -97,7 +102,8 @@ bsell3_step_kernel(const int nb, const int32_t* __restrict__ slice_ptr, const in
             cp += 32;
             vp += 32 * 9;
         }
-        dv = bsr_rows_out<XT, YT, DOT, AT>(br, acc, c, u, w, r, y, rdot);
+        dv += bsr_rows_out<XT, YT, DOT, AT>(br, acc, c, u, w, r, y, rdot);
+    }
     }
     if (DOT != 0) grid_reduce<kBlock>(dv, R);
 }
@@ -108,7 +114,8 @@ cudaError_t bsr_dispatch(bool sliced, int nb, const int32_t* ptr, const int32_t*
                          double cd, int dot, const double* rdot, const Reduce& R, const int* done,
                          cudaStream_t st) {
     using AT = typename AccOf<XT>::type;
-    const int grid = (nb + kBlock - 1) / kBlock;
+    const int tiles = (nb + kBlock - 1) / kBlock;
+    const int grid = (dot == 0 || tiles < kRedGrid) ? tiles : kRedGrid;
     const StepCoef<AT> c = make_coef<AT>(ca, cb, cc, cd);
     const VT* v = static_cast<const VT*>(val);
     const XT* uu = static_cast<const XT*>(u);

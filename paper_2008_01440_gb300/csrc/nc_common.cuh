@@ -18,7 +18,8 @@ namespace nc {
 constexpr int kBlock = 256;           // threads per CTA of the row kernels
 constexpr int kChunk = 2048;          // nonzeros staged in shared memory per pass
 constexpr int kSMs = 152;             // GB300 streaming multiprocessors
-constexpr int kVecGrid = kSMs * 4;    // CTAs of the grid-stride vector kernels
+constexpr int kVecGrid = kSMs * 8;    // CTAs of the grid-stride vector kernels (2048 threads/SM)
+constexpr int kRedGrid = kSMs * 8;    // CTAs of the persistent reduction variants of the step kernels
 
 // What the last CTA of a reduction does with the finished sum.
 enum Fin : int {

@@ -32,7 +32,10 @@ csr_step_kernel(const int n, const int32_t* __restrict__ rowptr, const int32_t* 
     if (done != nullptr && *done) return;
     __shared__ VT s_val[kChunk];
     __shared__ int32_t s_col[kChunk];
-    const int row0 = blockIdx.x * kBlock;
+    double dv = 0.0;
+    const int ntiles = (n + kBlock - 1) / kBlock;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int row0 = tile * kBlock;
     const int row = row0 + threadIdx.x;
     const int row_end = min(row0 + kBlock, n);
     const int blk_s = rowptr[row0];
@@ -55,8 +58,8 @@ csr_step_kernel(const int n, const int32_t* __restrict__ rowptr, const int32_t* 
             acc = fma((AT)ld_val(&s_val[j - cs]), (AT)__ldg(&u[s_col[j - cs]]), acc);
         __syncthreads();
     }
-    double dv = 0.0;
-    if (row < n) dv = step_row_out<XT, YT, DOT, AT>(row, acc, c, u, w, r, y, rdot);
+    if (row < n) dv += step_row_out<XT, YT, DOT, AT>(row, acc, c, u, w, r, y, rdot);
+    }
     if (DOT != 0) grid_reduce<kBlock>(dv, R);
 }
 
@@ -65,7 +68,8 @@ cudaError_t step_dispatch(int n, const int32_t* rowptr, const int32_t* col, cons
                           const void* u, const void* w, const void* r, void* y, double ca,
                           double cb, double cc, double cd, int dot, const double* rdot,
                           const Reduce& R, const int* done, cudaStream_t st) {
-    const int grid = (n + kBlock - 1) / kBlock;
+    const int tiles = (n + kBlock - 1) / kBlock;
+    const int grid = (dot == 0 || tiles < kRedGrid) ? tiles : kRedGrid;
     const VT* v = static_cast<const VT*>(val);
     const XT* uu = static_cast<const XT*>(u);
     const XT* ww = static_cast<const XT*>(w);

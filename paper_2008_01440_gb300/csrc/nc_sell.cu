@@ -27,76 +27,96 @@ namespace {
 
 constexpr int kSellGroup = 8;
 
+// One row: the slot loop and the epilogue; returns the row's dot term.
+template <typename VT, typename XT, typename YT, int DOT>
+__device__ __forceinline__ double sell_row(const int row, const int32_t* __restrict__ slice_ptr,
+                                           const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                           const XT* __restrict__ u, const XT* __restrict__ w,
+                                           const XT* __restrict__ r, YT* __restrict__ y,
+                                           const StepCoef<typename AccOf<XT>::type>& c,
+                                           const double* __restrict__ rdot) {
+    using AT = typename AccOf<XT>::type;
+    const int s = row >> 5;
+    const int beg = slice_ptr[s];
+    const int len = (slice_ptr[s + 1] - beg) >> 5;   // warp-uniform
+    const VT* vp = val + beg + (row & 31);
+    const int32_t* cp = col + beg + (row & 31);
+    AT acc = AT(0);
+    if constexpr (sizeof(AT) == 8) {
+        // float64: the fma chain itself is long-latency on GB300's narrow
+        // FP64 pipe, so occupancy matters most: a 4-slot unroll keeps the
+        // kernel at 32 registers and 8 CTAs (2048 threads) per SM.
+        int j = 0;
+        for (; j + 4 <= len; j += 4) {
+            const int c0 = ld_stream(cp), c1 = ld_stream(cp + 32), c2 = ld_stream(cp + 64),
+                      c3 = ld_stream(cp + 96);
+            const AT v0 = (AT)ld_stream(vp), v1 = (AT)ld_stream(vp + 32), v2 = (AT)ld_stream(vp + 64),
+                     v3 = (AT)ld_stream(vp + 96);
+            const AT x0 = (AT)__ldg(u + c0), x1 = (AT)__ldg(u + c1), x2 = (AT)__ldg(u + c2),
+                     x3 = (AT)__ldg(u + c3);
+            acc = fma(v0, x0, acc);
+            acc = fma(v1, x1, acc);
+            acc = fma(v2, x2, acc);
+            acc = fma(v3, x3, acc);
+            vp += 128;
+            cp += 128;
+        }
+        for (; j < len; ++j) {
+            const int c0 = ld_stream(cp);
+            acc = fma((AT)ld_stream(vp), (AT)__ldg(u + c0), acc);
+            vp += 32;
+            cp += 32;
+        }
+    } else {
+        // float: memory latency is the limit, so every column and value
+        // load of a group of 8 slots is issued before the gathers, and all
+        // gathers before the fma chain: a grid row (<= 8 slots) costs two
+        // memory latencies in total.  The guards are warp-uniform.
+        constexpr int G = kSellGroup;
+        for (int j0 = 0; j0 < len; j0 += G) {
+            int cc_[G];
+            AT vv[G], xx[G];
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (j0 + t < len) {
+                    cc_[t] = ld_stream(cp + 32 * t);
+                    vv[t] = (AT)ld_stream(vp + 32 * t);
+                }
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (j0 + t < len) xx[t] = (AT)__ldg(u + cc_[t]);
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (j0 + t < len) acc = fma(vv[t], xx[t], acc);
+            vp += 32 * G;
+            cp += 32 * G;
+        }
+    }
+    return step_row_out<XT, YT, DOT, AT>(row, acc, c, u, w, r, y, rdot);
+}
+
 template <typename VT, typename XT, typename YT, int DOT>
 __global__ void __launch_bounds__(kBlock)
 sell_step_kernel(const int n, const int32_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
                  const VT* __restrict__ val, const XT* __restrict__ u, const XT* __restrict__ w,
                  const XT* __restrict__ r, YT* __restrict__ y, const StepCoef<typename AccOf<XT>::type> c,
                  const double* __restrict__ rdot, const Reduce R, const int* __restrict__ done) {
-    using AT = typename AccOf<XT>::type;
     if (done != nullptr && *done) return;
-    const int row = blockIdx.x * kBlock + threadIdx.x;
-    double dv = 0.0;
-    if (row < n) {
-        const int s = row >> 5;
-        const int beg = slice_ptr[s];
-        const int len = (slice_ptr[s + 1] - beg) >> 5;   // warp-uniform
-        const VT* vp = val + beg + (row & 31);
-        const int32_t* cp = col + beg + (row & 31);
-        AT acc = AT(0);
-        if constexpr (sizeof(AT) == 8) {
-            // float64: the fma chain itself is long-latency on GB300's narrow
-            // FP64 pipe, so occupancy matters most: a 4-slot unroll keeps the
-            // kernel at 32 registers and 8 CTAs (2048 threads) per SM.
-            int j = 0;
-            for (; j + 4 <= len; j += 4) {
-                const int c0 = ld_stream(cp), c1 = ld_stream(cp + 32), c2 = ld_stream(cp + 64),
-                          c3 = ld_stream(cp + 96);
-                const AT v0 = (AT)ld_stream(vp), v1 = (AT)ld_stream(vp + 32), v2 = (AT)ld_stream(vp + 64),
-                         v3 = (AT)ld_stream(vp + 96);
-                const AT x0 = (AT)__ldg(u + c0), x1 = (AT)__ldg(u + c1), x2 = (AT)__ldg(u + c2),
-                         x3 = (AT)__ldg(u + c3);
-                acc = fma(v0, x0, acc);
-                acc = fma(v1, x1, acc);
-                acc = fma(v2, x2, acc);
-                acc = fma(v3, x3, acc);
-                vp += 128;
-                cp += 128;
-            }
-            for (; j < len; ++j) {
-                const int c0 = ld_stream(cp);
-                acc = fma((AT)ld_stream(vp), (AT)__ldg(u + c0), acc);
-                vp += 32;
-                cp += 32;
-            }
-        } else {
-            // float: memory latency is the limit, so every column and value
-            // load of a group of 8 slots is issued before the gathers, and all
-            // gathers before the fma chain: a grid row (<= 8 slots) costs two
-            // memory latencies in total.  The guards are warp-uniform.
-            constexpr int G = kSellGroup;
-            for (int j0 = 0; j0 < len; j0 += G) {
-                int cc_[G];
-                AT vv[G], xx[G];
-#pragma unroll
-                for (int t = 0; t < G; ++t)
-                    if (j0 + t < len) {
-                        cc_[t] = ld_stream(cp + 32 * t);
-                        vv[t] = (AT)ld_stream(vp + 32 * t);
-                    }
-#pragma unroll
-                for (int t = 0; t < G; ++t)
-                    if (j0 + t < len) xx[t] = (AT)__ldg(u + cc_[t]);
-#pragma unroll
-                for (int t = 0; t < G; ++t)
-                    if (j0 + t < len) acc = fma(vv[t], xx[t], acc);
-                vp += 32 * G;
-                cp += 32 * G;
-            }
+    if constexpr (DOT == 0) {
+        // one 256-row tile per CTA
+        const int row = blockIdx.x * kBlock + threadIdx.x;
+        if (row < n) sell_row<VT, XT, YT, 0>(row, slice_ptr, col, val, u, w, r, y, c, rdot);
+    } else {
+        // with a dot product: a persistent grid loops over the tiles and
+        // reduces once per CTA
+        double dv = 0.0;
+        const int ntiles = (n + kBlock - 1) / kBlock;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int row = tile * kBlock + threadIdx.x;
+            if (row < n) dv += sell_row<VT, XT, YT, DOT>(row, slice_ptr, col, val, u, w, r, y, c, rdot);
         }
-        dv = step_row_out<XT, YT, DOT, AT>(row, acc, c, u, w, r, y, rdot);
+        grid_reduce<kBlock>(dv, R);
     }
-    if (DOT != 0) grid_reduce<kBlock>(dv, R);
 }
 
 // longest row of each slice
@@ -159,7 +179,8 @@ cudaError_t sell_dispatch(int n, const int32_t* sptr, const int32_t* col, const 
                           const void* w, const void* r, void* y, double ca, double cb, double cc, double cd,
                           int dot, const double* rdot, const Reduce& R, const int* done, cudaStream_t st) {
     using AT = typename AccOf<XT>::type;
-    const int grid = (n + kBlock - 1) / kBlock;
+    const int tiles = (n + kBlock - 1) / kBlock;
+    const int grid = (dot == 0 || tiles < kRedGrid) ? tiles : kRedGrid;
     const StepCoef<AT> c = make_coef<AT>(ca, cb, cc, cd);
     const VT* v = static_cast<const VT*>(val);
     const XT* uu = static_cast<const XT*>(u);

@@ -19,6 +19,12 @@ struct StencilCoef {
 //     + cb w + cc r over planes [k0, k1) of tile (bx, by).  DOT 1: returns
 // this thread's sum of rdot*y, DOT 2: u*y, DOT 3: y*y.  Must be called by all
 // 32 lanes of a warp together (shuffles).
+//
+// The z-march works in batches of P planes: every load a batch needs (the
+// next P centre values, the y- and tile-edge x-neighbours, w and r) is issued
+// before any of the batch's arithmetic, so a batch costs one memory latency
+// rather than one per plane.  u at the planes below and at the current plane
+// stay in registers across batches.
 template <typename XT, typename YT, int DOT>
 __device__ __forceinline__ double stencil_tile(const int nx, const int ny, const int nz, const int bx, const int by,
                                                const int k0, const int k1, const XT* __restrict__ u,
@@ -26,39 +32,59 @@ __device__ __forceinline__ double stencil_tile(const int nx, const int ny, const
                                                YT* __restrict__ y, const StencilCoef<typename AccOf<XT>::type>& c,
                                                const double* __restrict__ rdot, const int lane, const int ty) {
     using AT = typename AccOf<XT>::type;
+    constexpr int P = sizeof(AT) == 8 ? 2 : 4;
     const int i = bx * kTX + lane;
     const int j = by * kTY + ty;
     const bool in = i < nx && j < ny;
     const long long plane = (long long)nx * ny;
     long long idx = ((long long)k0 * ny + j) * nx + i;
     const AT zero = AT(0);
+    const bool has_w = (c.terms & kTermW) != 0, has_r = (c.terms & kTermR) != 0;
     AT u_prev = (in && k0 > 0) ? (AT)__ldg(u + idx - plane) : zero;
     AT u_cur = (in && k0 < nz) ? (AT)__ldg(u + idx) : zero;
     double dv = 0.0;
-    for (int k = k0; k < k1; ++k) {
-        const AT u_next = (in && k + 1 < nz) ? (AT)__ldg(u + idx + plane) : zero;
-        AT xm = __shfl_up_sync(0xffffffffu, u_cur, 1);
-        AT xp = __shfl_down_sync(0xffffffffu, u_cur, 1);
-        if (lane == 0) xm = (in && i > 0) ? (AT)__ldg(u + idx - 1) : zero;
-        if (lane == kTX - 1) xp = (in && i + 1 < nx) ? (AT)__ldg(u + idx + 1) : zero;
-        if (in) {
-            const AT ym = j > 0 ? (AT)__ldg(u + idx - nx) : zero;
-            const AT yp = j + 1 < ny ? (AT)__ldg(u + idx + nx) : zero;
-            AT o = c.e0 * u_cur;
-            o = fma(c.ex, xm + xp, o);
-            o = fma(c.ey, ym + yp, o);
-            o = fma(c.ez, u_prev + u_next, o);
-            if (c.terms & kTermR) o = fma(c.cc, (AT)r[idx], o);
-            if (c.terms & kTermW) o = fma(c.cb, (AT)w[idx], o);
-            const YT yo = (YT)o;
-            y[idx] = yo;
-            if (DOT == 1) dv += rdot[idx] * (double)yo;
-            if (DOT == 2) dv += (double)u_cur * (double)yo;
-            if (DOT == 3) dv += (double)yo * (double)yo;
+    for (int k = k0; k < k1; k += P) {
+        AT un[P], ym[P], yp[P], xe[P], wv[P], rv[P];
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            const long long q = idx + t * plane;
+            const bool live = in && k + t < k1;
+            un[t] = (in && k + 1 + t < nz) ? (AT)__ldg(u + q + plane) : zero;
+            ym[t] = (live && j > 0) ? (AT)__ldg(u + q - nx) : zero;
+            yp[t] = (live && j + 1 < ny) ? (AT)__ldg(u + q + nx) : zero;
+            // the neighbour across the tile edge, for lanes 0 and 31 only
+            xe[t] = zero;
+            if (live && lane == 0 && i > 0) xe[t] = (AT)__ldg(u + q - 1);
+            if (live && lane == kTX - 1 && i + 1 < nx) xe[t] = (AT)__ldg(u + q + 1);
+            wv[t] = (live && has_w) ? (AT)w[q] : zero;
+            rv[t] = (live && has_r) ? (AT)r[q] : zero;
         }
-        u_prev = u_cur;
-        u_cur = u_next;
-        idx += plane;
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            if (k + t >= k1) break;   // uniform across the CTA
+            const AT u_next = un[t];
+            AT xm = __shfl_up_sync(0xffffffffu, u_cur, 1);
+            AT xp = __shfl_down_sync(0xffffffffu, u_cur, 1);
+            if (lane == 0) xm = xe[t];
+            if (lane == kTX - 1) xp = xe[t];
+            if (in) {
+                const long long q = idx + t * plane;
+                AT o = c.e0 * u_cur;
+                o = fma(c.ex, xm + xp, o);
+                o = fma(c.ey, ym[t] + yp[t], o);
+                o = fma(c.ez, u_prev + u_next, o);
+                if (has_r) o = fma(c.cc, rv[t], o);
+                if (has_w) o = fma(c.cb, wv[t], o);
+                const YT yo = (YT)o;
+                y[q] = yo;
+                if (DOT == 1) dv += rdot[q] * (double)yo;
+                if (DOT == 2) dv += (double)u_cur * (double)yo;
+                if (DOT == 3) dv += (double)yo * (double)yo;
+            }
+            u_prev = u_cur;
+            u_cur = u_next;
+        }
+        idx += P * plane;
     }
     return dv;
 }

@@ -142,3 +142,18 @@ def test_batch_zero_rhs_and_maxit(env):
     assert r0["status"] == 0 and r0["iters"] == 0 and np.all(x0 == 0)
     r1, _ = collect(nc, torch, B, s1, st.n)
     assert r1["status"] == nc.NC_ERR_MAXIT and r1["iters"] == 2
+
+
+def test_batch_host_loop_identical(env):
+    """The host-driven loop (for profilers) runs the same kernels: results
+    are bit-for-bit those of the graph."""
+    torch, nc = env
+    sy = systems(4, seed=5)
+    out = []
+    for host in (False, True):
+        B = nc.pcg_batch_create(8, sum(t[0].n for t in sy) + 10, 32, host_loop=host)
+        slots = [add(nc, torch, B, *t) for t in sy]
+        nc.pcg_batch_run(B, 1e-8, 3000)
+        out.append([collect(nc, torch, B, s, t[0].n) for s, t in zip(slots, sy)])
+    for (ra, xa), (rb, xb) in zip(*out):
+        assert ra == rb and np.array_equal(xa, xb)
