@@ -72,6 +72,30 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def replica_barrier(world):
+    """Barrier over the replicas (gloo process group; no-op for one process)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def replica_max(value, world):
+    """Max over the replicas of a host float (the slowest replica's time)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(steps_per_rank, local_seconds, world):
+    """Whole-job rate of N independent replicas: all units over the slowest
+    replica's time (weak scaling: each rank does `steps_per_rank` units)."""
+    return world * steps_per_rank / replica_max(local_seconds, world)
+
+
 # ---------------------------------------------------------------- clocks ----
 class Clocks:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
@@ -212,17 +236,10 @@ def run_system(args, spec, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        replica_barrier(world)
 
     def allmax(v):
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(v, world)
 
     def timed_solves(S, steps, warmup):
         for i in range(warmup):

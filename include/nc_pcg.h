@@ -62,8 +62,10 @@ typedef enum { NC_F64 = 0, NC_F32 = 1, NC_BF16 = 2 } nc_dtype;
  * SELL: slices of 32 rows (block rows for BSR3) stored slot-major, rows
  * padded to the slice's longest row (coalesced thread-per-row access); AUTO
  * picks SELL when the padding is at most 1.5x the nonzeros, else CSR (plain
- * block CSR for BSR3).  Stencil handles ignore the option. */
-typedef enum { NC_FORMAT_AUTO = 0, NC_FORMAT_CSR = 1, NC_FORMAT_SELL = 2 } nc_format;
+ * block CSR for BSR3); TUNE builds SELL (padding up to 4x), times one fused
+ * step in each layout on this matrix during pcg_setup and keeps the faster
+ * (timings in nc_solver_info).  Stencil handles ignore the option. */
+typedef enum { NC_FORMAT_AUTO = 0, NC_FORMAT_CSR = 1, NC_FORMAT_SELL = 2, NC_FORMAT_TUNE = 3 } nc_format;
 
 typedef struct {
     int apply_dtype;   /* nc_dtype: F64 = plain method; F32: float32 matrix and
@@ -92,6 +94,8 @@ typedef struct {
     double shift;         /* the stored operator is A - shift*I (theta' with
                              SELL: the (1 - x/theta') factor of the p_k
                              recursion, Sec. 3), 0 = A itself               */
+    double tune_us_plain; /* TUNE: measured step time, plain layout (us)   */
+    double tune_us_sliced;/* TUNE: measured step time, sliced layout (us)  */
 } nc_solver_info;
 
 typedef struct {

@@ -29,8 +29,8 @@ _DTYPES = {"f64": NC_F64, "f32": NC_F32, "bf16": NC_BF16}
 SOLVE_STATUSES = (NC_OK, NC_ERR_MAXIT, NC_ERR_INDEFINITE, NC_ERR_BREAKDOWN)
 
 
-NC_FORMAT_AUTO, NC_FORMAT_CSR, NC_FORMAT_SELL = 0, 1, 2
-_FORMATS = {"auto": NC_FORMAT_AUTO, "csr": NC_FORMAT_CSR, "sell": NC_FORMAT_SELL}
+NC_FORMAT_AUTO, NC_FORMAT_CSR, NC_FORMAT_SELL, NC_FORMAT_TUNE = 0, 1, 2, 3
+_FORMATS = {"auto": NC_FORMAT_AUTO, "csr": NC_FORMAT_CSR, "sell": NC_FORMAT_SELL, "tune": NC_FORMAT_TUNE}
 
 
 class nc_options(ctypes.Structure):
@@ -42,7 +42,7 @@ class nc_solver_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("degree_k", ctypes.c_int32), ("spmv_format", ctypes.c_int32),
                 ("apply_dtype", ctypes.c_int32), ("pad0", ctypes.c_int32), ("padding", ctypes.c_double),
                 ("theta", ctypes.c_double), ("delta", ctypes.c_double), ("sigma", ctypes.c_double),
-                ("shift", ctypes.c_double)]
+                ("shift", ctypes.c_double), ("tune_us_plain", ctypes.c_double), ("tune_us_sliced", ctypes.c_double)]
 
 
 class nc_result(ctypes.Structure):

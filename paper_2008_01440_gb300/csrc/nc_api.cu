@@ -63,6 +63,7 @@ struct nc_solver_s {
     OpView op64;                          // float64 operator (outer CG, true residual)
     OpView opP;                           // operator inside P_k (apply precision)
     double padding = 1.0;                 // SELL stored entries / nnz
+    double tune_us[2] = {0.0, 0.0};       // measured step time, plain / sliced layout (TUNE)
     double shift = 0.0;                   // op values hold A - shift*I (theta' for SELL, else 0)
     void* lval = nullptr;                 // converted CSR values (F32/BF16), owned
     int32_t* sell_ptr = nullptr;          // SELL-32 arrays, owned
@@ -454,9 +455,41 @@ nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
     return (nc_status)o.status;
 }
 
+// Average time of one representative fused step (DOT-free, all four terms
+// of a Chebyshev step after the first) with operator view `op`, in the
+// solver's apply precision, on the zero-filled rotating buffers.
+nc_status time_step(nc_solver S, const OpView& op, bool shifted, cudaStream_t st, double* us) {
+    const size_t vb = S->mixed ? sizeof(float) : sizeof(double);
+    for (int i = 0; i < 3; ++i) NC_CU(cudaMemsetAsync(S->buf[i], 0, vb * (size_t)S->n, st));
+    const Reduce none = make_reduce(S->partials, S->counter, S->S, nullptr, FIN_NONE);
+    const double ca = shifted ? 0.0 : 0.5;
+    auto launch = [&]() {
+        return op_step(op, S->mixed, !S->mixed, S->buf[0], S->buf[1], S->buf[0], S->buf[2], ca, -0.25, 0.1, -1.0, 0,
+                       nullptr, none, nullptr, st);
+    };
+    for (int i = 0; i < 3; ++i) NC_CU(launch());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NC_CU(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e) { cudaEventDestroy(e0); g_last_cuda = e; return NC_ERR_CUDA; }
+    const int reps = 10;
+    e = cudaEventRecord(e0, st);
+    for (int i = 0; i < reps && e == cudaSuccess; ++i) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e) { g_last_cuda = e; return NC_ERR_CUDA; }
+    *us = 1e3 * (double)ms / reps;
+    return NC_OK;
+}
+
 // Choose and build the layout the step kernels read.  SELL-32 when its
 // padding is at most kSellMaxPadding (or when forced), else the CSR arrays.
 constexpr double kSellMaxPadding = 1.5;
+constexpr double kSellTunePadding = 4.0;   // TUNE times SELL only below this padding
 
 // Block counterpart of the SELL setup: BSELL-32 over block rows when its
 // padding is at most kSellMaxPadding (or forced), else the plain block CSR.
@@ -486,18 +519,21 @@ nc_status setup_operator_bsr3(nc_solver S, cudaStream_t st, size_t eb) {
         S->padding = A->nnz > 0 ? (double)hptr[nslices] / (double)A->nnz : 1.0;
         if (hptr[nslices] >= ((int64_t)1 << 31)) sliced = false;
         if (S->opt.spmv_format == NC_FORMAT_AUTO && S->padding > kSellMaxPadding) sliced = false;
+        if (S->opt.spmv_format == NC_FORMAT_TUNE && S->padding > kSellTunePadding) sliced = false;
+    }
+    OpView bsr64{OP_BSR3, n, A->rowptr, A->col, A->val, NC_F64};
+    OpView bsrP = bsr64;
+    if (S->mixed && (!sliced || S->opt.spmv_format == NC_FORMAT_TUNE)) {
+        NC_TRY(dev_alloc(&S->lval, eb * 9 * (size_t)(A->nnz > 0 ? A->nnz : 1)));
+        cudaError_t e = launch_convert(9 * A->nnz, A->val, S->vdt, S->lval, st);
+        if (e) { g_last_cuda = e; return NC_ERR_CUDA; }
+        bsrP = OpView{OP_BSR3, n, A->rowptr, A->col, S->lval, S->vdt};
     }
     if (!sliced) {
         S->padding = 1.0;
         S->shift = 0.0;
-        S->op64 = OpView{OP_BSR3, n, A->rowptr, A->col, A->val, NC_F64};
-        S->opP = S->op64;
-        if (S->mixed) {
-            NC_TRY(dev_alloc(&S->lval, eb * 9 * (size_t)(A->nnz > 0 ? A->nnz : 1)));
-            cudaError_t e = launch_convert(9 * A->nnz, A->val, S->vdt, S->lval, st);
-            if (e) { g_last_cuda = e; return NC_ERR_CUDA; }
-            S->opP = OpView{OP_BSR3, n, A->rowptr, A->col, S->lval, S->vdt};
-        }
+        S->op64 = bsr64;
+        S->opP = bsrP;
         return NC_OK;
     }
     const int nslices = (nb + 31) / 32;
@@ -543,6 +579,21 @@ nc_status setup_operator_bsr3(nc_solver S, cudaStream_t st, size_t eb) {
         S->opP = OpView{OP_BSELL3, n, S->sell_ptr, S->sell_col, S->sell_valP, S->vdt};
     }
     if ((e = cudaStreamSynchronize(st))) { g_last_cuda = e; return NC_ERR_CUDA; }
+    if (S->opt.spmv_format == NC_FORMAT_TUNE) {
+        NC_TRY(time_step(S, bsrP, false, st, &S->tune_us[0]));
+        NC_TRY(time_step(S, S->opP, S->shift != 0.0, st, &S->tune_us[1]));
+        if (S->tune_us[0] < S->tune_us[1]) {
+            dev_free(S->sell_ptr); dev_free(S->sell_col); dev_free(S->sell_val64); dev_free(S->sell_valP);
+            S->sell_ptr = nullptr; S->sell_col = nullptr; S->sell_val64 = nullptr; S->sell_valP = nullptr;
+            S->padding = 1.0;
+            S->shift = 0.0;
+            S->op64 = bsr64;
+            S->opP = bsrP;
+        } else if (S->lval) {
+            dev_free(S->lval);
+            S->lval = nullptr;
+        }
+    }
     return NC_OK;
 }
 
@@ -582,17 +633,21 @@ nc_status setup_operator(nc_solver S, cudaStream_t st) {
         S->padding = A->nnz > 0 ? (double)total / (double)A->nnz : 1.0;
         if (total >= ((int64_t)1 << 31)) sell = false;
         if (S->opt.spmv_format == NC_FORMAT_AUTO && S->padding > kSellMaxPadding) sell = false;
+        if (S->opt.spmv_format == NC_FORMAT_TUNE && S->padding > kSellTunePadding) sell = false;
+    }
+    // the plain CSR view (always available: the handle's arrays)
+    OpView csr64{OP_CSR, n, A->rowptr, A->col, A->val, NC_F64};
+    OpView csrP = csr64;
+    if (S->mixed && (!sell || S->opt.spmv_format == NC_FORMAT_TUNE)) {
+        NC_TRY(dev_alloc(&S->lval, eb * (size_t)(A->nnz > 0 ? A->nnz : 1)));
+        cudaError_t e = launch_convert(A->nnz, A->val, S->vdt, S->lval, st);
+        if (e) { g_last_cuda = e; return NC_ERR_CUDA; }
+        csrP = OpView{OP_CSR, n, A->rowptr, A->col, S->lval, S->vdt};
     }
     if (!sell) {
         S->padding = 1.0;
-        S->op64 = OpView{OP_CSR, n, A->rowptr, A->col, A->val, NC_F64};
-        S->opP = S->op64;
-        if (S->mixed) {
-            NC_TRY(dev_alloc(&S->lval, eb * (size_t)(A->nnz > 0 ? A->nnz : 1)));
-            cudaError_t e = launch_convert(A->nnz, A->val, S->vdt, S->lval, st);
-            if (e) { g_last_cuda = e; return NC_ERR_CUDA; }
-            S->opP = OpView{OP_CSR, n, A->rowptr, A->col, S->lval, S->vdt};
-        }
+        S->op64 = csr64;
+        S->opP = csrP;
         return NC_OK;
     }
     const int nslices = (n + 31) / 32;
@@ -641,6 +696,22 @@ nc_status setup_operator(nc_solver S, cudaStream_t st) {
     }
     // the host vector hp32 must outlive the copy
     if ((e = cudaStreamSynchronize(st))) { g_last_cuda = e; return NC_ERR_CUDA; }
+    if (S->opt.spmv_format == NC_FORMAT_TUNE) {
+        // measure both layouts on this matrix and keep the faster
+        NC_TRY(time_step(S, csrP, false, st, &S->tune_us[0]));
+        NC_TRY(time_step(S, S->opP, S->shift != 0.0, st, &S->tune_us[1]));
+        if (S->tune_us[0] < S->tune_us[1]) {
+            dev_free(S->sell_ptr); dev_free(S->sell_col); dev_free(S->sell_val64); dev_free(S->sell_valP);
+            S->sell_ptr = nullptr; S->sell_col = nullptr; S->sell_val64 = nullptr; S->sell_valP = nullptr;
+            S->padding = 1.0;
+            S->shift = 0.0;
+            S->op64 = csr64;
+            S->opP = csrP;
+        } else if (S->lval) {
+            dev_free(S->lval);
+            S->lval = nullptr;
+        }
+    }
     return NC_OK;
 }
 
@@ -934,7 +1005,7 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
     if (opt) o = *opt;
     if (o.apply_dtype != NC_F64 && o.apply_dtype != NC_F32 && o.apply_dtype != NC_BF16) return NC_ERR_ARG;
     if (o.rr_period < 0) return NC_ERR_ARG;
-    if (o.spmv_format < NC_FORMAT_AUTO || o.spmv_format > NC_FORMAT_SELL) return NC_ERR_ARG;
+    if (o.spmv_format < NC_FORMAT_AUTO || o.spmv_format > NC_FORMAT_TUNE) return NC_ERR_ARG;
     cudaStream_t st = as_stream(stream);
     nc_solver S = new (std::nothrow) nc_solver_s();
     if (!S) return NC_ERR_OOM;
@@ -1030,6 +1101,8 @@ nc_status pcg_get_info(nc_solver S, nc_solver_info* info) {
     info->delta = S->delta;
     info->sigma = S->sigma;
     info->shift = S->shift;
+    info->tune_us_plain = S->tune_us[0];
+    info->tune_us_sliced = S->tune_us[1];
     return NC_OK;
 }
 

@@ -41,7 +41,7 @@ namespace nc {
 namespace {
 
 constexpr int kVch = 8192;    // vector-chunk length
-constexpr int kZC = 8;        // planes per stencil tile
+constexpr int kZC = 16;       // planes per stencil tile
 constexpr int kBatchGrid = kSMs * 8;
 
 enum Phase : int { PH_FREE = 0, PH_INIT = 1, PH_RUN = 2, PH_FINISH = 3, PH_DONE = 4 };
@@ -222,8 +222,11 @@ __global__ void __launch_bounds__(256) bk_axpy(const BDesc* __restrict__ D, BSta
 }
 
 __global__ void __launch_bounds__(256) bk_cheb(const BDesc* __restrict__ D, BState* S, const BTile* __restrict__ T,
-                                               const BCoef* __restrict__ C, BCtl* ctl, double* partials, int j) {
-    const int nt = ctl->ntiles;
+                                               const BCoef* __restrict__ C, BCtl* ctl, double* partials, int j,
+                                               const int* __restrict__ ntile_step) {
+    // tiles are ordered by their slot's degree, highest first: step j only
+    // visits the prefix of tiles whose slots have k >= j
+    const int nt = ntile_step[j];
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const BTile tl = T[t];
         BState* st = S + tl.pair;
@@ -328,6 +331,7 @@ struct nc_batch_s {
     BTile* d_tiles = nullptr;
     BVch* d_vch = nullptr;
     BCoef* d_coef = nullptr;
+    int* d_ntile_step = nullptr;  // tiles of slots with k >= j, j = 0..kmax
     double* d_partials = nullptr;
     double* pool64 = nullptr;
     float* pool32 = nullptr;
@@ -423,7 +427,8 @@ void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, c
     bk_opq<<<kBatchGrid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
     bk_axpy<<<kBatchGrid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
     for (int j = 1; j <= B->kmax; ++j)
-        bk_cheb<<<kBatchGrid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_coef, B->d_ctl, B->d_partials, j);
+        bk_cheb<<<kBatchGrid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_coef, B->d_ctl, B->d_partials, j,
+                                           B->d_ntile_step);
     bk_pupd<<<kBatchGrid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
     bk_true<<<kBatchGrid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
     bk_cond<<<1, 1, 0, st>>>(B->d_ctl, h, use_cond);
@@ -472,8 +477,12 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
     std::vector<BTile> tiles;
     std::vector<BVch> vch;
     std::vector<BCoef> coef;
-    for (int s = 0; s < B->cap_slots; ++s) {
-        if (!B->used[s]) continue;
+    std::vector<int> order;
+    for (int s = 0; s < B->cap_slots; ++s)
+        if (B->used[s]) order.push_back(s);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->kdeg[a] > B->kdeg[b]; });
+    std::vector<int> nstep(B->kmax + 1, 0);
+    for (int s : order) {
         BDesc& d = B->desc[s];
         d.tile0 = (int)tiles.size();
         const int tx = (d.nx + kTX - 1) / kTX, ty = (d.ny + kTY - 1) / kTY, tz = (d.nz + kZC - 1) / kZC;
@@ -481,6 +490,7 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
             for (int by = 0; by < ty; ++by)
                 for (int bx = 0; bx < tx; ++bx) tiles.push_back(BTile{s, bx, by, bz});
         d.tile1 = (int)tiles.size();
+        for (int j = 0; j <= std::min(d.k, B->kmax); ++j) nstep[j] = d.tile1;   // prefix ends after this slot
         d.vch0 = (int)vch.size();
         for (int i = 0; i < d.n; i += kVch) vch.push_back(BVch{s, i});
         d.vch1 = (int)vch.size();
@@ -507,6 +517,7 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
         NB_CU(cudaMemcpyAsync(B->d_vch, vch.data(), sizeof(BVch) * vch.size(), cudaMemcpyHostToDevice, st));
     if (!coef.empty())
         NB_CU(cudaMemcpyAsync(B->d_coef, coef.data(), sizeof(BCoef) * coef.size(), cudaMemcpyHostToDevice, st));
+    NB_CU(cudaMemcpyAsync(B->d_ntile_step, nstep.data(), sizeof(int) * nstep.size(), cudaMemcpyHostToDevice, st));
     NB_CU(cudaMemcpyAsync(B->d_desc, B->desc.data(), sizeof(BDesc) * B->cap_slots, cudaMemcpyHostToDevice, st));
     B->h_ctl->ntiles = (int)tiles.size();
     B->h_ctl->nvch = (int)vch.size();
@@ -545,6 +556,7 @@ nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, int fl
         if ((s = balloc(reinterpret_cast<void**>(&B->d_desc), sizeof(BDesc) * max_slots))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->d_state), sizeof(BState) * max_slots))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->d_ctl), sizeof(BCtl)))) break;
+        if ((s = balloc(reinterpret_cast<void**>(&B->d_ntile_step), sizeof(int) * (kmax + 1)))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->pool64), sizeof(double) * 6 * (size_t)max_unknowns))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->pool32), sizeof(float) * 4 * (size_t)max_unknowns))) break;
         cudaError_t e;
@@ -747,6 +759,7 @@ nc_status pcg_batch_destroy(nc_batch B) {
     cudaFree(B->d_tiles);
     cudaFree(B->d_vch);
     cudaFree(B->d_coef);
+    cudaFree(B->d_ntile_step);
     cudaFree(B->d_partials);
     cudaFree(B->pool64);
     cudaFree(B->pool32);

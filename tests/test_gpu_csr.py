@@ -348,3 +348,33 @@ def test_residual_replacement(env, dt, period):
     tol_it = 1 if dt == "f64" else max(2, 0.1 * ro2.iters)
     assert abs(res["iters"] - ro2.iters) <= tol_it
     assert res["n_replace"] == (res["iters"] - 1) // period
+
+
+def test_autotune_layout(env):
+    """TUNE measures both layouts on the matrix and keeps the faster; the
+    result of the apply is the same either way."""
+    torch, nc = env
+    A = W.diffusion_3d_7pt_lognormal(48, seed=2)
+    M = nc.nc_matrix_jacobi(csr_to_gpu(torch, nc, A))
+    lo, hi = 0.01, 2.0
+    S = nc.pcg_setup(M, lo, hi, 10, 1.001, spmv_format="tune")
+    info = nc.pcg_get_info(S)
+    assert info["tune_us_plain"] > 0 and info["tune_us_sliced"] > 0
+    faster = "sell" if info["tune_us_sliced"] <= info["tune_us_plain"] else "csr"
+    assert info["spmv_format"] == faster
+    S2 = nc.pcg_setup(M, lo, hi, 10, 1.001, spmv_format="csr" if faster == "sell" else "sell")
+    v = to_dev(torch, W.uniform_vector(A.n, seed=1))
+    z1 = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    z2 = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    nc.pcg_apply_poly(S, v, z1)
+    nc.pcg_apply_poly(S2, v, z2)
+    assert rel_err(z1.cpu().numpy(), z2.cpu().numpy()) <= 1e-13
+    # with a dense row the sliced layout is skipped (padding > 4x): no timing of it
+    n = 3000
+    rows = [np.array([i]) for i in range(n)]
+    rows[5] = np.arange(n)
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    B = W.CSR(n, rowptr, np.concatenate(rows).astype(np.int32), np.ones(rowptr[-1]))
+    S3 = nc.pcg_setup(csr_to_gpu(torch, nc, B), 0.1, 2.0, 4, 1.0, spmv_format="tune")
+    assert nc.pcg_get_info(S3)["spmv_format"] == "csr"
