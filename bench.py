@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--oracle-iters", type=int, default=6, help="PCG iterations per oracle sample")
     ap.add_argument("--gpu-iters", type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--solve", default="auto", choices=["auto", "graph", "persistent"],
+                    help="solve driver: one CUDA graph, or one kernel on one thread-block cluster per solve "
+                         "(auto: the workload's choice; persistent for the small c1 system)")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the PCG loop from the host instead of the device-side graph "
                          "(same kernels; lets a profiler list every launch)")
@@ -191,6 +194,7 @@ def spec_c1(args):
     return dict(kind="csr", A=A, n=A.n, nnz=A.nnz, jacobi=False, bounds=(lo, hi), k=args.k or 8, s=1.0, rhs=rhs,
                 rr_mixed=0, bytes=lambda mode: csr_step_bytes(A.n, A.nnz, SV[mode], 8 if mode == "f64" else 4),
                 workload="laplacian2d-5pt 64x64 CSR (n=4096, nnz=20224), exact bounds 4sin^2(pi i/130) sums, b=A x*",
+                persistent=True,
                 key=f"c1:{A.n}", l2="L2-resident system (0.4 MB); latency-bound by construction")
 
 
@@ -273,13 +277,15 @@ def run_system(args, spec, rank, world, local_rank):
         per_launch_s = e0.elapsed_time(e1) / 1e3 / (reps * max(k, 1))
         return per_launch_s, spec["bytes"](mode)
 
+    persistent = (args.solve == "persistent" or (args.solve == "auto" and spec.get("persistent", False))) \
+        and not args.host_loop
     modes = [args.apply] + ([] if args.no_modes else [m for m in ("f64", "f32", "bf16") if m != args.apply])
     out_modes = {}
     main = None
     for mode in modes:
         rr = spec["rr_mixed"] if mode != "f64" else 0
         S = nc.pcg_setup(M, lo, hi, k, spec["s"], apply_dtype=mode, x0_is_zero=True, rr_period=rr,
-                         use_graph=not args.host_loop)
+                         use_graph=not args.host_loop, persistent=persistent)
         barrier()
         clk = start_clocks(torch, dev) if mode == args.apply else None
         torch.cuda.synchronize()
@@ -295,7 +301,9 @@ def run_system(args, spec, rank, world, local_rank):
                "all_converged": all(r["status"] == 0 for r in results),
                "max_relres": max(r["relres"] for r in results),
                "max_true_relres": max(r["true_relres"] for r in results), "rr_period": rr,
-               "layout": nc.pcg_get_info(S)["spmv_format"]}
+               "layout": nc.pcg_get_info(S)["spmv_format"],
+               "solve": "persistent" if nc.pcg_get_info(S)["persistent"] else
+                        ("host-loop" if args.host_loop else "graph")}
         t_launch, nbytes = time_step_kernel(S, mode)
         rec["step_us"] = round(t_launch * 1e6, 2)
         rec["step_GBps"] = round(nbytes / t_launch / 1e9, 1)
@@ -316,6 +324,22 @@ def run_system(args, spec, rank, world, local_rank):
                 "frac": round(achieved / peak, 4), "traffic": read_traffic(spec["key"], args.apply),
                 "peak_source": peak_src, "kernel": kname, "bytes_per_launch": step_bytes,
                 "us_per_launch": round(per_launch_s * 1e6, 2)}
+    if rec["solve"] == "persistent":
+        # one launch runs the whole solve: its algorithmic bytes are the
+        # (k+1) products and the vector updates of every iteration; its
+        # duration is bounded above by the event-timed solve (which adds the
+        # copy-in, true-residual and copy-out kernels)
+        it = rec["iters"]
+        vec = 8 * n * 12   # p,q,x,r,z loads/stores of the update, dot and direction phases
+        pbytes = it * ((k + 1) * step_bytes + vec)
+        dur = rec["p50_ms"] / 1e3
+        roofline.update({"achieved": round(pbytes / dur / 1e9, 1), "frac": round(pbytes / dur / 1e9 / peak, 4),
+                         "traffic": None, "bytes_per_launch": pbytes, "us_per_launch": round(dur * 1e6, 2),
+                         "kernel": "cluster_pcg_kernel (whole solve on one 16-CTA cluster, system in "
+                                   "distributed shared memory; duration = median solve latency)",
+                         "bound": "latency",
+                         "note": "shared-memory-resident system: cluster barriers and DSMEM latency, "
+                                 "not HBM bandwidth, set the time"})
 
     # --- end to end through the host-buffer C-ABI call ---------------------------------
     hb = [bb.cpu().pin_memory() for bb in bs]
@@ -338,6 +362,8 @@ def run_system(args, spec, rank, world, local_rank):
     iters = rec["iters"]
     kk = max(k, 1)
     launches_per_solve = 1 + (4 + kk + (1 if args.apply != "f64" else 0)) + iters * (kk + 3) + 3
+    if rec["solve"] == "persistent":
+        launches_per_solve = 5   # copy-in, the solve kernel, true residual (product + dot), copy-out
     line = {
         "metric": METRIC, "value": round(rec["solves_per_s"], 3), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(rec["ms_per_solve"], 3),

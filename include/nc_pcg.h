@@ -79,7 +79,14 @@ typedef struct {
                           initial product b - A x0).                            */
     int use_graph;     /* 1 (default): one CUDA graph per solve with the
                           stopping test evaluated on the device; 0: host loop
-                          reading the residual every iteration.                 */
+                          reading the residual every iteration; 2: the whole
+                          solve in one kernel on one thread-block cluster of up
+                          to 16 CTAs, operator and vectors held in the
+                          cluster's shared memory (small systems, where
+                          launches and L2 latency dominate).  Taken when the
+                          solver is float64, SELL, without residual
+                          replacement, and its slices fit (about 20k rows of a
+                          7-point operator); else the graph.                    */
     int spmv_format;   /* nc_format of the solver's product kernels (AUTO).    */
 } nc_options;
 
@@ -88,7 +95,7 @@ typedef struct {
     int32_t degree_k;
     int32_t spmv_format;  /* NC_FORMAT_CSR or NC_FORMAT_SELL (after AUTO)      */
     int32_t apply_dtype;
-    int32_t pad0;
+    int32_t persistent;   /* 1: solves run as one kernel on one cluster     */
     double padding;       /* stored entries / nonzeros of the chosen layout    */
     double theta, delta, sigma;   /* theta' = s(a+b)/2, delta, sigma (Sec. 3/4) */
     double shift;         /* the stored operator is A - shift*I (theta' with

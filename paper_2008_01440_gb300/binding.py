@@ -40,7 +40,7 @@ class nc_options(ctypes.Structure):
 
 class nc_solver_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("degree_k", ctypes.c_int32), ("spmv_format", ctypes.c_int32),
-                ("apply_dtype", ctypes.c_int32), ("pad0", ctypes.c_int32), ("padding", ctypes.c_double),
+                ("apply_dtype", ctypes.c_int32), ("persistent", ctypes.c_int32), ("padding", ctypes.c_double),
                 ("theta", ctypes.c_double), ("delta", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("shift", ctypes.c_double), ("tune_us_plain", ctypes.c_double), ("tune_us_sliced", ctypes.c_double)]
 
@@ -237,14 +237,15 @@ def nc_bounds_lanczos(A: Matrix, steps: int, v0, stream=None):
     return lo.value, hi.value, rmin.value, rmax.value
 
 
-def make_options(apply_dtype="f64", rr_period=0, x0_is_zero=False, use_graph=True, spmv_format="auto") -> nc_options:
+def make_options(apply_dtype="f64", rr_period=0, x0_is_zero=False, use_graph=True, spmv_format="auto",
+                 persistent=False) -> nc_options:
     o = nc_options()
     lib.nc_options_default(ctypes.byref(o))
     o.spmv_format = _FORMATS[spmv_format] if isinstance(spmv_format, str) else int(spmv_format)
     o.apply_dtype = _DTYPES[apply_dtype] if isinstance(apply_dtype, str) else int(apply_dtype)
     o.rr_period = int(rr_period)
     o.x0_is_zero = int(bool(x0_is_zero))
-    o.use_graph = int(bool(use_graph))
+    o.use_graph = 2 if persistent else int(bool(use_graph))
     return o
 
 
@@ -261,7 +262,7 @@ def pcg_get_info(S: Solver) -> dict:
     info = nc_solver_info()
     _check(lib.pcg_get_info(S.handle, ctypes.byref(info)), "pcg_get_info")
     d = {f: getattr(info, f) for f, _ in info._fields_}
-    d.pop("pad0")
+    d["persistent"] = bool(d["persistent"])
     d["spmv_format"] = {NC_FORMAT_CSR: "csr", NC_FORMAT_SELL: "sell"}.get(d["spmv_format"], d["spmv_format"])
     return d
 

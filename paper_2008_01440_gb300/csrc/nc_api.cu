@@ -80,6 +80,11 @@ struct nc_solver_s {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool graph_failed = false;
+    // one-cluster solve (use_graph == 2)
+    bool persistent = false;
+    ClusterPlan plan{};
+    double* pcoef = nullptr;          // 4*(k+1) step coefficients, shifted-operator form
+    std::vector<int32_t> h_sell_ptr;  // host copy of the scalar SELL slice offsets
 };
 
 namespace {
@@ -416,22 +421,26 @@ nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
     *S->h_io = init;
     NC_CU(cudaMemcpyAsync(S->S, S->h_io, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
     NC_CU(launch_copy_in(n, b_dev, x_dev, S->A->dis, S->A->dis_scalar, S->opt.x0_is_zero, S->b, S->x, st));
-    bool graph = S->opt.use_graph && !S->graph_failed;
-    if (graph && S->exec == nullptr) {
-        if (build_graph(S) != NC_OK) {
+    if (S->persistent) {
+        NC_CU(launch_cluster_pcg(S->plan, n, S->k, S->opt.x0_is_zero, maxit, tol * tol, S->shift, S->op64.ptr,
+                                 S->op64.col, static_cast<const double*>(S->op64.val), S->pcoef, S->b, S->x, S->S,
+                                 st));
+    } else {
+        bool graph = S->opt.use_graph && !S->graph_failed;
+        if (graph && S->exec == nullptr && build_graph(S) != NC_OK) {
             S->graph_failed = true;
             graph = false;
         }
-    }
-    if (graph) {
-        NC_CU(cudaGraphLaunch(S->exec, st));
-    } else {
-        NC_CU(enqueue_prologue(S, st));
-        for (;;) {
-            NC_CU(cudaMemcpyAsync(S->h_io, S->S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
-            NC_CU(cudaStreamSynchronize(st));
-            if (S->h_io->done) break;
-            NC_CU(enqueue_body(S, 0, 0, st));
+        if (graph) {
+            NC_CU(cudaGraphLaunch(S->exec, st));
+        } else {
+            NC_CU(enqueue_prologue(S, st));
+            for (;;) {
+                NC_CU(cudaMemcpyAsync(S->h_io, S->S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+                NC_CU(cudaStreamSynchronize(st));
+                if (S->h_io->done) break;
+                NC_CU(enqueue_body(S, 0, 0, st));
+            }
         }
     }
     // true residual of the (scaled) system at exit
@@ -685,6 +694,7 @@ nc_status setup_operator(nc_solver S, cudaStream_t st) {
     }
     S->op64 = OpView{OP_SELL, n, S->sell_ptr, S->sell_col, S->sell_val64, NC_F64};
     S->opP = S->op64;
+    S->h_sell_ptr = hp32;
     if (S->mixed) {
         NC_TRY(dev_alloc(&S->sell_valP, eb * (size_t)total));
         if ((e = launch_sell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, S->vdt, S->shift, S->sell_col,
@@ -1039,6 +1049,26 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
         }
         if ((e = cudaMallocHost(&S->h_io, sizeof(PcgScalars)))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
         if ((e = cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
+        if (o.use_graph == 2 && S->op64.kind == OP_SELL && !S->mixed && o.rr_period == 0 &&
+            plan_cluster_pcg(n, S->h_sell_ptr.data(), &S->plan)) {
+            // one-cluster solve: per-step coefficients of the shifted operator
+            std::vector<double> cf(4 * (size_t)(S->k + 1), 0.0);
+            if (S->k == 0) cf[0] = 1.0 / S->theta;
+            for (int j = 1; j <= S->k; ++j) {
+                double ca = S->ca[j];
+                if (S->shift != 0.0) ca = (j == 1) ? S->ca1_shifted : 0.0;
+                cf[4 * j] = ca;
+                cf[4 * j + 1] = S->cb[j];
+                cf[4 * j + 2] = S->cc[j];
+                cf[4 * j + 3] = S->cd[j];
+            }
+            if ((s = dev_alloc_n(&S->pcoef, (int64_t)cf.size()))) break;
+            if ((e = cudaMemcpyAsync(S->pcoef, cf.data(), sizeof(double) * cf.size(), cudaMemcpyHostToDevice, st)) ||
+                (e = cudaStreamSynchronize(st))) {
+                g_last_cuda = e; s = NC_ERR_CUDA; break;
+            }
+            S->persistent = true;
+        }
         if ((e = cudaStreamSynchronize(st))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
     } while (0);
     if (s != NC_OK) {
@@ -1096,6 +1126,7 @@ nc_status pcg_get_info(nc_solver S, nc_solver_info* info) {
     info->degree_k = S->k;
     info->spmv_format = (S->op64.kind == OP_SELL || S->op64.kind == OP_BSELL3) ? NC_FORMAT_SELL : NC_FORMAT_CSR;
     info->apply_dtype = S->vdt;
+    info->persistent = S->persistent ? 1 : 0;
     info->padding = S->padding;
     info->theta = S->theta;
     info->delta = S->delta;
@@ -1114,6 +1145,7 @@ nc_status pcg_destroy(nc_solver S) {
     for (int i = 0; i < 3; ++i) dev_free(S->buf[i]);
     dev_free(S->r32); dev_free(S->lval); dev_free(S->partials); dev_free(S->counter); dev_free(S->S);
     dev_free(S->sell_ptr); dev_free(S->sell_col); dev_free(S->sell_val64); dev_free(S->sell_valP);
+    dev_free(S->pcoef);
     if (S->h_io) cudaFreeHost(S->h_io);
     delete S;
     return NC_OK;

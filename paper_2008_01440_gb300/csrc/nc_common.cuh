@@ -226,6 +226,20 @@ cudaError_t launch_convert(int64_t count, const double* in, int out_dt, void* ou
 
 int vec_grid(int64_t n);
 
+// Whole PCG solve in one kernel on one thread-block cluster, the system held
+// in the cluster's shared memory (nc_cluster.cu).  C CTAs of R rows each;
+// `slots` SELL entries and `smem` bytes of shared memory per CTA.
+struct ClusterPlan {
+    int C, R, slots;
+    size_t smem;
+};
+// Plan for a float64 SELL-32 operator of n rows with host slice offsets
+// hsptr[0..ceil(n/32)]; false when it does not fit one cluster.
+bool plan_cluster_pcg(int n, const int32_t* hsptr, ClusterPlan* plan);
+cudaError_t launch_cluster_pcg(const ClusterPlan& p, int n, int k, int x0_zero, int maxit, double tol2, double shift,
+                               const int32_t* sptr, const int32_t* col, const double* val, const double* coef,
+                               const double* b, double* x, PcgScalars* S, cudaStream_t st);
+
 // x += alpha p; r -= alpha q; r32 = (float) r (if r32); (r, r) -> FIN_RR
 cudaError_t launch_axpy2_rr(int n, double* x, double* r, const double* p, const double* q,
                             float* r32, const Reduce& R, cudaStream_t st);
