@@ -43,6 +43,7 @@ sys.path.insert(0, ROOT)
 METRIC = "solves/s and p50/p99 latency at rel. resid 1e-8; P_k(A)v HBM GB/s vs peak"
 GRID, SEED_A, SEED_V0, SEED_B, S_THETA, TOL, MAXIT = 128, 7, 3, 5, 1.001, 1e-8, 5000
 GOLDEN = os.path.join(ROOT, "tests", "golden", "c2_oracle.json")
+GOLDEN_C3 = os.path.join(ROOT, "tests", "golden", "c3_oracle.json")
 
 
 def parse():
@@ -423,7 +424,8 @@ def run_reference(args, rank, world):
     """The FP64 oracle as it stands, timed on the host cores: each step runs
     `oracle_iters` PCG iterations of the full workload and the rate is
     extrapolated with a full-solve iteration count (the oracle's own, from
-    tests/golden/c2_oracle.json, for the default workload)."""
+    tests/golden/c2_oracle.json and c3_oracle.json, for the c2 and c3
+    workloads at their default sizes)."""
     if rank != 0:
         return
     import numpy as np
@@ -452,8 +454,10 @@ def run_reference(args, rank, world):
         np.add.at(rs, (3 * brows[:, None] + np.arange(3)[None, :]).ravel(), np.abs(val).sum(axis=2).ravel())
         gersh = float(rs.max())
     golden = None
-    if args.workload == "c2" and (args.grid in (None, GRID)) and os.path.exists(GOLDEN):
-        with open(GOLDEN) as f:
+    gpath = {"c2": GOLDEN, "c3": GOLDEN_C3}.get(args.workload)
+    default_grid = {"c2": GRID, "c3": 100}.get(args.workload)
+    if gpath and args.grid in (None, default_grid) and os.path.exists(gpath):
+        with open(gpath) as f:
             golden = json.load(f)
     iters_src = "oracle's"
     if golden is not None and str(k) in golden["solves"]:
