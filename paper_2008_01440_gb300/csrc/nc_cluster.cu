@@ -62,42 +62,50 @@ __device__ __forceinline__ double ld_cluster(uint32_t a) {
     return v;
 }
 
-// CTA sum in a fixed order; valid in thread 0.
-__device__ __forceinline__ double cta_sum(double v, double* wsum) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < kCT / 32; ++w) s += wsum[w];
-    return s;
-}
+// Cluster sum s of v (every thread gets it) and, computed once per CTA by
+// thread 0, a derived scalar q: `div` 1 gives num / s, 2 gives s / num.
+// On GB300 a warp-wide float64 instruction costs about as much as a few
+// dozen float32 ones, so the CTA stage is the shared-memory halving tree of
+// block_sum (12 warp-wide adds for 256 threads) and only warp 0 finishes.
+// The CTA's partial goes to one of two alternating slots: a CTA writes slot
+// s again only two sums later, after a barrier that every reader of the
+// previous use of s has passed.  The butterfly gives the same bits in every
+// lane and every CTA (each level adds the same two values, in either order).
+struct ClusterSum {
+    double s, q;
+};
 
-// Cluster sum, valid in every thread.  The two partial slots alternate: a
-// CTA writes slot s again only two sums later, after a barrier that every
-// reader of the previous use of s has passed.  The butterfly gives the same
-// bits in every lane (each level adds the same two values in either order).
-__device__ __forceinline__ double cluster_sum(double v, double* wsum, double* red, int& slot) {
-    const double s = cta_sum(v, wsum);
+__device__ __forceinline__ ClusterSum cluster_sum(double v, double num, int div, double* sh, double* red,
+                                                  double* bc, int& slot) {
+    const double c = block_sum<kCT>(v, sh, (int)threadIdx.x);   // valid in warp 0
     double* mine = red + (slot & 1);
     ++slot;
-    if (threadIdx.x == 0) *mine = s;
+    if (threadIdx.x == 0) *mine = c;
     cluster_sync();
-    const int lane = threadIdx.x & 31;
-    double t = 0.0;
-    if (lane < (int)gridDim.x) t = ld_cluster(map_rank((uint32_t)__cvta_generic_to_shared(mine), (uint32_t)lane));
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double t = 0.0;
+        if (lane < (int)gridDim.x) t = ld_cluster(map_rank((uint32_t)__cvta_generic_to_shared(mine), (uint32_t)lane));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    return t;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) {
+            bc[0] = t;
+            bc[1] = div == 1 ? num / t : (div == 2 ? t / num : 0.0);
+        }
+    }
+    __syncthreads();
+    return ClusterSum{bc[0], bc[1]};
 }
 
-// (A' u)_i for local row i; `uoff` is the byte offset of u's slot
+// acc + (A' u)_i for local row i; `uoff` is the byte offset of u's slot.
+// On GB300 a float64 FMA is the scarce resource (about two per clock per
+// SM): the loop adds nothing beyond the row's own FMAs.  (Measured on the
+// 64 x 64 Laplacian: splitting the chain over two accumulators, or issuing
+// all gathers of a row before its FMAs, made the solve 8-15% slower.)
 __device__ __forceinline__ double row_product(int i, const int32_t* lptr, const double* mval, const uint32_t* maddr,
-                                              uint32_t uoff) {
+                                              uint32_t uoff, double acc) {
     const int s = i >> 5;
     const int end = lptr[s + 1];
-    double acc = 0.0;
 #pragma unroll 4
     for (int e = lptr[s] + (i & 31); e < end; e += 32) acc = fma(mval[e], ld_cluster(maddr[e] + uoff), acc);
     return acc;
@@ -108,9 +116,10 @@ __global__ void __launch_bounds__(kCT) cluster_pcg_kernel(const ClusterArgs a) {
     const int R = a.rows;
     double* vec = reinterpret_cast<double*>(smem);                      // kNumVec * R
     double* mval = vec + (size_t)kNumVec * R;                           // slots
-    double* red = mval + a.slots;                                       // 2
-    double* wsum = red + 2;                                             // kCT / 32
-    uint32_t* maddr = reinterpret_cast<uint32_t*>(wsum + kCT / 32);     // slots
+    double* red = mval + a.slots;                                       // 2 partial slots
+    double* bc = red + 2;                                               // 2 broadcast scalars
+    double* sh = bc + 2;                                                // kCT, CTA sums
+    uint32_t* maddr = reinterpret_cast<uint32_t*>(sh + kCT);            // slots
     int32_t* lptr = reinterpret_cast<int32_t*>(maddr + a.slots);        // R / 32 + 1
     const int C = (int)gridDim.x;   // the grid is one cluster
     const int rank = (int)blockIdx.x;
@@ -150,21 +159,22 @@ __global__ void __launch_bounds__(kCT) cluster_pcg_kernel(const ClusterArgs a) {
     for (int i = threadIdx.x; i < nloc; i += kCT) {
         const double bi = a.b[row0 + i];
         double ri = bi;
-        if (!a.x0_zero) ri = bi - fma(a.shift, Xv[i], row_product(i, lptr, mval, maddr, V_X * vstride));
+        if (!a.x0_zero) ri = bi - fma(a.shift, Xv[i], row_product(i, lptr, mval, maddr, V_X * vstride, 0.0));
         Rv[i] = ri;
         pb = fma(bi, bi, pb);
         pr = fma(ri, ri, pr);
     }
-    const double bb = cluster_sum(pb, wsum, red, slot);
-    double rr = cluster_sum(pr, wsum, red, slot);
+    const double bb = cluster_sum(pb, 0.0, 0, sh, red, bc, slot).s;
+    double rr = cluster_sum(pr, 0.0, 0, sh, red, bc, slot).s;
     int status = NC_ERR_MAXIT, iter = 0, n_dot = 0, n_prec = 0;
     bool done = false;
     if (!isfinite(rr)) { status = NC_ERR_BREAKDOWN; done = true; }
     else if (bb == 0.0 || rr <= a.tol2 * bb) { status = NC_OK; done = true; }
     else if (a.maxit <= 0) { status = NC_ERR_MAXIT; done = true; }
 
-    // z = P_k r: x_j in slot T0 + j % 3, the last into Z; returns (r, z)
-    auto apply_poly = [&]() -> double {
+    // z = P_k r: x_j in slot T0 + j % 3, the last into Z; returns (r, z) and
+    // the derived scalar of `div` (see cluster_sum)
+    auto apply_poly = [&](double num, int div) -> ClusterSum {
         double pz = 0.0;
         if (k == 0) {
             const double c0 = a.coef[0];
@@ -179,25 +189,29 @@ __global__ void __launch_bounds__(kCT) cluster_pcg_kernel(const ClusterArgs a) {
             const int ws = V_T0 + (j + 1) % 3;   // x_{j-2}; read only when cb != 0 (j >= 3)
             const int ys = (j == k) ? V_Z : V_T0 + j % 3;
             const double ca = a.coef[4 * j], cb = a.coef[4 * j + 1], cc = a.coef[4 * j + 2], cd = a.coef[4 * j + 3];
+            // which optional terms the step has, decided once (a float64
+            // compare per row would occupy the float64 pipe)
+            const bool ha = ca != 0.0, hb = cb != 0.0, hc = cc != 0.0;
             const double* U = vec + (size_t)us * R;
             const double* Wv = vec + (size_t)ws * R;
             double* Y = vec + (size_t)ys * R;
+            const uint32_t uoff = (uint32_t)us * vstride;
             for (int i = threadIdx.x; i < nloc; i += kCT) {
-                double o = cd * row_product(i, lptr, mval, maddr, (uint32_t)us * vstride);
-                if (cc != 0.0) o = fma(cc, Rv[i], o);
-                if (cb != 0.0) o = fma(cb, Wv[i], o);
-                if (ca != 0.0) o = fma(ca, U[i], o);
+                double o = cd * row_product(i, lptr, mval, maddr, uoff, 0.0);
+                if (hc) o = fma(cc, Rv[i], o);
+                if (hb) o = fma(cb, Wv[i], o);
+                if (ha) o = fma(ca, U[i], o);
                 Y[i] = o;
                 if (j == k) pz = fma(Rv[i], o, pz);
             }
             if (j < k) cluster_sync();   // x_j visible before step j+1 gathers it
         }
-        return cluster_sum(pz, wsum, red, slot);
+        return cluster_sum(pz, num, div, sh, red, bc, slot);
     };
 
     double rz = 0.0;
     if (!done) {
-        rz = apply_poly();
+        rz = apply_poly(0.0, 0).s;
         n_dot += 1;
         n_prec += 1;
         if (!(rz > 0.0)) { status = isfinite(rz) ? NC_ERR_INDEFINITE : NC_ERR_BREAKDOWN; done = true; }
@@ -205,17 +219,18 @@ __global__ void __launch_bounds__(kCT) cluster_pcg_kernel(const ClusterArgs a) {
         cluster_sync();
     }
     while (!done) {
-        // q = A p = A' p + shift p, (p, q)
+        // q = A p = A' p + shift p, (p, q), alpha = rz / (p, q)
         double pq = 0.0;
         for (int i = threadIdx.x; i < nloc; i += kCT) {
-            const double qi = fma(a.shift, Pv[i], row_product(i, lptr, mval, maddr, V_P * vstride));
+            const double qi = fma(a.shift, Pv[i], row_product(i, lptr, mval, maddr, V_P * vstride, 0.0));
             Qv[i] = qi;
             pq = fma(Pv[i], qi, pq);
         }
-        pq = cluster_sum(pq, wsum, red, slot);
+        const ClusterSum sq = cluster_sum(pq, rz, 1, sh, red, bc, slot);
+        pq = sq.s;
         n_dot += 1;
         if (!(pq > 0.0) || !isfinite(pq)) { status = isfinite(pq) ? NC_ERR_INDEFINITE : NC_ERR_BREAKDOWN; break; }
-        const double alpha = rz / pq;
+        const double alpha = sq.q;
         double prr = 0.0;
         for (int i = threadIdx.x; i < nloc; i += kCT) {
             Xv[i] = fma(alpha, Pv[i], Xv[i]);
@@ -223,20 +238,22 @@ __global__ void __launch_bounds__(kCT) cluster_pcg_kernel(const ClusterArgs a) {
             Rv[i] = ri;
             prr = fma(ri, ri, prr);
         }
-        rr = cluster_sum(prr, wsum, red, slot);   // also publishes r for step 1
+        rr = cluster_sum(prr, 0.0, 0, sh, red, bc, slot).s;   // also publishes r for step 1
         n_dot += 1;
         iter += 1;
         if (!isfinite(rr)) { status = NC_ERR_BREAKDOWN; break; }
         if (rr <= a.tol2 * bb) { status = NC_OK; break; }
         if (iter >= a.maxit) { status = NC_ERR_MAXIT; break; }
-        const double rz_new = apply_poly();
+        // new (r, z) and beta = (r, z)_new / (r, z)_old
+        const ClusterSum sz = apply_poly(rz, 2);
+        const double rz_new = sz.s;
         n_dot += 1;
         n_prec += 1;
         if (!(rz_new > 0.0) || !isfinite(rz_new)) {
             status = isfinite(rz_new) ? NC_ERR_INDEFINITE : NC_ERR_BREAKDOWN;
             break;
         }
-        const double beta = rz_new / rz;
+        const double beta = sz.q;
         rz = rz_new;
         for (int i = threadIdx.x; i < nloc; i += kCT) Pv[i] = fma(beta, Pv[i], Zv[i]);
         cluster_sync();   // p visible before the next product gathers it
@@ -257,7 +274,7 @@ __global__ void __launch_bounds__(kCT) cluster_pcg_kernel(const ClusterArgs a) {
 }
 
 size_t cluster_smem(int R, int slots) {
-    return (size_t)kNumVec * R * 8 + (size_t)slots * 8 + (2 + kCT / 32) * 8 + (size_t)slots * 4 +
+    return (size_t)kNumVec * R * 8 + (size_t)slots * 8 + (4 + kCT) * 8 + (size_t)slots * 4 +
            (size_t)(R / 32 + 1) * 4;
 }
 
