@@ -4,8 +4,9 @@
 //
 // All slots advance together: one PCG iteration for every slot is a fixed
 // sequence of persistent grid-stride kernels over two work lists held in
-// device memory -- stencil tiles (32 x 8 x ZC points of one slot) and vector
-// chunks (kVch entries of one slot):
+// device memory -- stencil tiles (kFT consecutive points of one slot's
+// flattened xy-plane x ZC planes) and vector chunks (kVch entries of one
+// slot):
 //   opq      q = A p and (p, q) -> alpha              (float64, tiles)
 //   axpy     x += alpha p, r -= alpha q, ||r||^2, stop? (float64, chunks);
 //            slots being admitted instead start r = b, x = 0, ||b||^2
@@ -69,7 +70,7 @@ struct BCoef {
 };
 
 struct BTile {
-    int pair, bx, by, bz;
+    int pair, f0, pad, bz;   // f0: first point of the tile in the flattened xy-plane
 };
 
 struct BVch {
@@ -167,6 +168,7 @@ __device__ void reduce_slot(double v, double* partials, int slotidx, int first, 
 
 __global__ void __launch_bounds__(256) bk_opq(const BDesc* __restrict__ D, BState* S, const BTile* __restrict__ T,
                                               BCtl* ctl, double* partials) {
+    const int tid = threadIdx.x + kTX * threadIdx.y;   // launched as kTX x kTY
     const int nt = ctl->ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const BTile tl = T[t];
@@ -182,8 +184,8 @@ __global__ void __launch_bounds__(256) bk_opq(const BDesc* __restrict__ D, BStat
         c.cc = 0.0;
         c.terms = 0;
         const int k0 = tl.bz * kZC, k1 = min(k0 + kZC, d.nz);
-        const double dv = stencil_tile<double, double, 2>(d.nx, d.ny, d.nz, tl.bx, tl.by, k0, k1, d.p, nullptr,
-                                                          nullptr, d.q, c, nullptr, threadIdx.x, threadIdx.y);
+        const double dv = stencil_flat<double, double, 2>(d.nx, d.ny, d.nz, tl.f0, k0, k1, d.p, nullptr, nullptr,
+                                                          d.q, c, nullptr, tid);
         reduce_slot(dv, partials, t, d.tile0, d.tile1 - d.tile0, st, ctl, BF_ALPHA);
     }
 }
@@ -224,6 +226,7 @@ __global__ void __launch_bounds__(256) bk_axpy(const BDesc* __restrict__ D, BSta
 __global__ void __launch_bounds__(256) bk_cheb(const BDesc* __restrict__ D, BState* S, const BTile* __restrict__ T,
                                                const BCoef* __restrict__ C, BCtl* ctl, double* partials, int j,
                                                const int* __restrict__ ntile_step) {
+    const int tid = threadIdx.x + kTX * threadIdx.y;   // launched as kTX x kTY
     // tiles are ordered by their slot's degree, highest first: step j only
     // visits the prefix of tiles whose slots have k >= j
     const int nt = ntile_step[j];
@@ -248,12 +251,11 @@ __global__ void __launch_bounds__(256) bk_cheb(const BDesc* __restrict__ D, BSta
         const float* w = (j >= 3) ? tb[(j - 2) % 3] : nullptr;
         const int k0 = tl.bz * kZC, k1 = min(k0 + kZC, d.nz);
         if (j == d.k) {
-            const double dv = stencil_tile<float, double, 1>(d.nx, d.ny, d.nz, tl.bx, tl.by, k0, k1, u, w, d.r32, d.z,
-                                                             c, d.r, threadIdx.x, threadIdx.y);
+            const double dv = stencil_flat<float, double, 1>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r32, d.z, c,
+                                                             d.r, tid);
             reduce_slot(dv, partials, t, d.tile0, d.tile1 - d.tile0, st, ctl, BF_RZ);
         } else {
-            stencil_tile<float, float, 0>(d.nx, d.ny, d.nz, tl.bx, tl.by, k0, k1, u, w, d.r32, tb[j % 3], c, nullptr,
-                                          threadIdx.x, threadIdx.y);
+            stencil_flat<float, float, 0>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r32, tb[j % 3], c, nullptr, tid);
         }
     }
 }
@@ -281,6 +283,7 @@ __global__ void __launch_bounds__(256) bk_pupd(const BDesc* __restrict__ D, BSta
 
 __global__ void __launch_bounds__(256) bk_true(const BDesc* __restrict__ D, BState* S, const BTile* __restrict__ T,
                                                BCtl* ctl, double* partials) {
+    const int tid = threadIdx.x + kTX * threadIdx.y;   // launched as kTX x kTY
     const int nt = ctl->ntiles;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const BTile tl = T[t];
@@ -296,8 +299,8 @@ __global__ void __launch_bounds__(256) bk_true(const BDesc* __restrict__ D, BSta
         c.cc = 1.0;
         c.terms = kTermR;
         const int k0 = tl.bz * kZC, k1 = min(k0 + kZC, d.nz);
-        const double dv = stencil_tile<double, double, 3>(d.nx, d.ny, d.nz, tl.bx, tl.by, k0, k1, d.x, nullptr, d.b,
-                                                          d.q, c, nullptr, threadIdx.x, threadIdx.y);
+        const double dv = stencil_flat<double, double, 3>(d.nx, d.ny, d.nz, tl.f0, k0, k1, d.x, nullptr, d.b, d.q,
+                                                          c, nullptr, tid);
         reduce_slot(dv, partials, t, d.tile0, d.tile1 - d.tile0, st, ctl, BF_TRUE);
     }
 }
@@ -485,10 +488,9 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
     for (int s : order) {
         BDesc& d = B->desc[s];
         d.tile0 = (int)tiles.size();
-        const int tx = (d.nx + kTX - 1) / kTX, ty = (d.ny + kTY - 1) / kTY, tz = (d.nz + kZC - 1) / kZC;
+        const int nxy = d.nx * d.ny, tz = (d.nz + kZC - 1) / kZC;
         for (int bz = 0; bz < tz; ++bz)
-            for (int by = 0; by < ty; ++by)
-                for (int bx = 0; bx < tx; ++bx) tiles.push_back(BTile{s, bx, by, bz});
+            for (int f0 = 0; f0 < nxy; f0 += kFT) tiles.push_back(BTile{s, f0, 0, bz});
         d.tile1 = (int)tiles.size();
         for (int j = 0; j <= std::min(d.k, B->kmax); ++j) nstep[j] = d.tile1;   // prefix ends after this slot
         d.vch0 = (int)vch.size();

@@ -89,4 +89,84 @@ __device__ __forceinline__ double stencil_tile(const int nx, const int ny, const
     return dv;
 }
 
+// The same step over a flattened tile: the kFT consecutive points
+// [f0, f0 + kFT) of the row-major xy-plane (thread tid owns f0 + tid), planes
+// [k0, k1).  Every lane is busy whatever nx is (a 32-wide box tile leaves
+// 32 ceil(nx/32) - nx lanes idle); x-neighbours come from the adjacent lane
+// within a row and are loaded where the row or the warp ends.  Must be
+// called by all lanes of each warp together.
+constexpr int kFT = 256;
+
+template <typename XT, typename YT, int DOT>
+__device__ __forceinline__ double stencil_flat(const int nx, const int ny, const int nz, const int f0, const int k0,
+                                               const int k1, const XT* __restrict__ u, const XT* __restrict__ w,
+                                               const XT* __restrict__ r, YT* __restrict__ y,
+                                               const StencilCoef<typename AccOf<XT>::type>& c,
+                                               const double* __restrict__ rdot, const int tid) {
+    using AT = typename AccOf<XT>::type;
+    constexpr int P = sizeof(AT) == 8 ? 2 : 4;
+    const int lane = tid & 31;
+    const int nxy = nx * ny;
+    const int f = f0 + tid;
+    const bool in = f < nxy;
+    const int yy = in ? f / nx : 0;
+    const int xx = f - yy * nx;
+    const bool has_xm = in && xx > 0, has_xp = in && xx + 1 < nx;
+    const bool has_ym = in && yy > 0, has_yp = in && yy + 1 < ny;
+    // lane 0's left and lane 31's right neighbour live in another warp
+    const bool ld_xm = has_xm && lane == 0, ld_xp = has_xp && lane == 31;
+    const long long plane = nxy;
+    long long idx = (long long)k0 * plane + f;
+    const AT zero = AT(0);
+    const bool has_w = (c.terms & kTermW) != 0, has_r = (c.terms & kTermR) != 0;
+    AT u_prev = (in && k0 > 0) ? (AT)__ldg(u + idx - plane) : zero;
+    AT u_cur = (in && k0 < nz) ? (AT)__ldg(u + idx) : zero;
+    double dv = 0.0;
+    for (int k = k0; k < k1; k += P) {
+        AT un[P], ym[P], yp[P], xe[P], wv[P], rv[P];
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            const long long q = idx + t * plane;
+            const bool live = in && k + t < k1;
+            un[t] = (in && k + 1 + t < nz) ? (AT)__ldg(u + q + plane) : zero;
+            ym[t] = (live && has_ym) ? (AT)__ldg(u + q - nx) : zero;
+            yp[t] = (live && has_yp) ? (AT)__ldg(u + q + nx) : zero;
+            xe[t] = zero;
+            if (live && ld_xm) xe[t] = (AT)__ldg(u + q - 1);
+            if (live && ld_xp) xe[t] = (AT)__ldg(u + q + 1);
+            wv[t] = (live && has_w) ? (AT)w[q] : zero;
+            rv[t] = (live && has_r) ? (AT)r[q] : zero;
+        }
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            if (k + t >= k1) break;   // uniform across the CTA
+            const AT u_next = un[t];
+            AT xm = __shfl_up_sync(0xffffffffu, u_cur, 1);
+            AT xp = __shfl_down_sync(0xffffffffu, u_cur, 1);
+            if (lane == 0) xm = xe[t];
+            if (lane == 31) xp = xe[t];
+            if (!has_xm) xm = zero;
+            if (!has_xp) xp = zero;
+            if (in) {
+                const long long q = idx + t * plane;
+                AT o = c.e0 * u_cur;
+                o = fma(c.ex, xm + xp, o);
+                o = fma(c.ey, ym[t] + yp[t], o);
+                o = fma(c.ez, u_prev + u_next, o);
+                if (has_r) o = fma(c.cc, rv[t], o);
+                if (has_w) o = fma(c.cb, wv[t], o);
+                const YT yo = (YT)o;
+                y[q] = yo;
+                if (DOT == 1) dv += rdot[q] * (double)yo;
+                if (DOT == 2) dv += (double)u_cur * (double)yo;
+                if (DOT == 3) dv += (double)yo * (double)yo;
+            }
+            u_prev = u_cur;
+            u_cur = u_next;
+        }
+        idx += P * plane;
+    }
+    return dv;
+}
+
 }  // namespace nc
