@@ -251,17 +251,21 @@ NC_API nc_status pcg_destroy(nc_solver S);
  *   allocated once -- the HBM budget); kmax = largest degree accepted;
  *   flags: 0, or NC_BATCH_HOST_LOOP to drive the same kernels from a host
  *   loop (one synchronisation per iteration; for profilers).
+ * All calls on one engine are ordered on its `stream` (they enqueue work
+ * there and only pcg_batch_run synchronises it); a caller that switches
+ * streams orders them itself.
  * pcg_batch_add: admit one system with right-hand side b_dev (n float64,
- *   read during the call).  NC_ERR_ADMISSION when no slot or pool space is
- *   free (retry after releasing finished slots).  The slot starts with the
- *   next pcg_batch_run.
+ *   read by a kernel enqueued on `stream`).  NC_ERR_ADMISSION when no slot or
+ *   pool space is free (retry after releasing finished slots).  The slot
+ *   starts with the next pcg_batch_run.
  * pcg_batch_run: advance every admitted slot by up to iter_limit PCG
  *   iterations (<= 0: until all slots have stopped) in one graph launch;
  *   synchronises the stream; *active_left = slots not yet finished.
  * pcg_batch_status: done flag and result of a slot (as of the last run).
  * pcg_batch_collect: x_dev (n float64) = the slot's solution of the original
  *   (unscaled) system; only for finished slots.
- * pcg_batch_release: free a finished slot and its memory.
+ * pcg_batch_release: free a finished slot and its memory (collects already
+ *   enqueued on `stream` still read it first).
  * pcg_batch_free_units: largest contiguous and total free pooled unknowns. */
 #define NC_BATCH_HOST_LOOP 1
 NC_API nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, int flags, void* stream,

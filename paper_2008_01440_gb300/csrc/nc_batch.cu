@@ -349,6 +349,7 @@ struct nc_batch_s {
     std::map<int64_t, int64_t> free_list;   // offset -> length
     bool dirty = true;
     BState* h_state = nullptr;    // pinned
+    std::vector<int> state_upload;   // slots whose host state goes to the device at the next run
     BCtl* h_ctl = nullptr;        // pinned
 };
 
@@ -520,6 +521,10 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
     if (!coef.empty())
         NB_CU(cudaMemcpyAsync(B->d_coef, coef.data(), sizeof(BCoef) * coef.size(), cudaMemcpyHostToDevice, st));
     NB_CU(cudaMemcpyAsync(B->d_ntile_step, nstep.data(), sizeof(int) * nstep.size(), cudaMemcpyHostToDevice, st));
+    // states of slots admitted or released since the last run (pinned source)
+    for (int slot : B->state_upload)
+        NB_CU(cudaMemcpyAsync(B->d_state + slot, &B->h_state[slot], sizeof(BState), cudaMemcpyHostToDevice, st));
+    B->state_upload.clear();
     NB_CU(cudaMemcpyAsync(B->d_desc, B->desc.data(), sizeof(BDesc) * B->cap_slots, cudaMemcpyHostToDevice, st));
     B->h_ctl->ntiles = (int)tiles.size();
     B->h_ctl->nvch = (int)vch.size();
@@ -651,8 +656,7 @@ nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx
     init.phase = PH_INIT;
     init.status = NC_ERR_MAXIT;
     B->h_state[s] = init;
-    NB_CU(cudaMemcpyAsync(B->d_state + s, &B->h_state[s], sizeof(BState), cudaMemcpyHostToDevice, st));
-    NB_CU(cudaStreamSynchronize(st));
+    B->state_upload.push_back(s);   // uploaded (stream-ordered) by the next pcg_batch_run
     B->h_ctl->active += 1;
     *slot = s;
     return NC_OK;
@@ -724,18 +728,16 @@ nc_status pcg_batch_release(nc_batch B, int slot, void* stream) {
     if (!B || slot < 0 || slot >= B->cap_slots || !B->used[slot]) return NC_ERR_ARG;
     const int ph = B->h_state[slot].phase;
     if (ph != PH_DONE) return NC_ERR_ARG;   // only finished slots can be released
-    // make sure pending collects on `stream` finished before the memory is reused
-    NB_CU(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    // no synchronisation: collects already enqueued on the engine's stream
+    // run before any later kernel that reuses this memory
     pool_free(B, B->off[slot], B->desc[slot].n);
     B->used[slot] = 0;
     B->off[slot] = -1;
     B->desc[slot] = BDesc{};
     B->coefs[slot].clear();
     B->h_state[slot] = BState{};
+    B->state_upload.push_back(slot);
     B->dirty = true;
-    NB_CU(cudaMemcpyAsync(B->d_state + slot, &B->h_state[slot], sizeof(BState), cudaMemcpyHostToDevice,
-                          static_cast<cudaStream_t>(stream)));
-    NB_CU(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
     return NC_OK;
 }
 
