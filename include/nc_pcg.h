@@ -67,6 +67,18 @@ typedef enum { NC_F64 = 0, NC_F32 = 1, NC_BF16 = 2 } nc_dtype;
  * (timings in nc_solver_info).  Stencil handles ignore the option. */
 typedef enum { NC_FORMAT_AUTO = 0, NC_FORMAT_CSR = 1, NC_FORMAT_SELL = 2, NC_FORMAT_TUNE = 3 } nc_format;
 
+/* How the preconditioner is evaluated.  CHEBYSHEV: the three-term recurrence
+ * of Algorithm 2 (Sec. 3, Eq. rhocheb), any degree k, one fused product step
+ * per degree.  NEWTON: the recursion of Algorithm 1 (Sec. 2, Eqs. recursive
+ * and zetaNewt), P_0 = zeta_0 I, P_{j+1} = zeta_{j+1} (2 P_j - P_j A P_j),
+ * only for k = 2^nlev - 1 (NC_ERR_ARG otherwise) and a float64 apply
+ * (NC_ERR_UNSUPPORTED otherwise); the same k products, evaluated depth
+ * first, with 2 (nlev - 1) extra float64 work vectors.  By Theorem 3.1 both
+ * give the same polynomial; the modified theta' (Sec. 4) enters both through
+ * the interval [theta' - delta, theta' + delta].  The one-cluster solve
+ * (use_graph = 2) runs the Chebyshev form only. */
+typedef enum { NC_POLY_CHEBYSHEV = 0, NC_POLY_NEWTON = 1 } nc_poly_form;
+
 typedef struct {
     int apply_dtype;   /* nc_dtype: F64 = plain method; F32: float32 matrix and
                           vectors inside P_k; BF16: bfloat16 matrix values,
@@ -88,6 +100,7 @@ typedef struct {
                           replacement, and its slices fit (about 20k rows of a
                           7-point operator); else the graph.                    */
     int spmv_format;   /* nc_format of the solver's product kernels (AUTO).    */
+    int poly_form;     /* nc_poly_form: how z = P(A) r is evaluated.           */
 } nc_options;
 
 typedef struct {
@@ -117,7 +130,7 @@ typedef struct {
 } nc_result;
 
 /* Fill `opt` with the defaults: F64, no residual replacement, x0 from x,
- * graph on, AUTO layout. */
+ * graph on, AUTO layout, Chebyshev form. */
 NC_API void nc_options_default(nc_options* opt);
 NC_API const char* nc_strerror(nc_status s);
 NC_API const char* nc_version(void);

@@ -35,7 +35,8 @@ _FORMATS = {"auto": NC_FORMAT_AUTO, "csr": NC_FORMAT_CSR, "sell": NC_FORMAT_SELL
 
 class nc_options(ctypes.Structure):
     _fields_ = [("apply_dtype", ctypes.c_int), ("rr_period", ctypes.c_int),
-                ("x0_is_zero", ctypes.c_int), ("use_graph", ctypes.c_int), ("spmv_format", ctypes.c_int)]
+                ("x0_is_zero", ctypes.c_int), ("use_graph", ctypes.c_int), ("spmv_format", ctypes.c_int),
+                ("poly_form", ctypes.c_int)]
 
 
 class nc_solver_info(ctypes.Structure):
@@ -237,8 +238,11 @@ def nc_bounds_lanczos(A: Matrix, steps: int, v0, stream=None):
     return lo.value, hi.value, rmin.value, rmax.value
 
 
+_POLY = {"chebyshev": 0, "newton": 1}
+
+
 def make_options(apply_dtype="f64", rr_period=0, x0_is_zero=False, use_graph=True, spmv_format="auto",
-                 persistent=False) -> nc_options:
+                 persistent=False, poly="chebyshev") -> nc_options:
     o = nc_options()
     lib.nc_options_default(ctypes.byref(o))
     o.spmv_format = _FORMATS[spmv_format] if isinstance(spmv_format, str) else int(spmv_format)
@@ -246,6 +250,7 @@ def make_options(apply_dtype="f64", rr_period=0, x0_is_zero=False, use_graph=Tru
     o.rr_period = int(rr_period)
     o.x0_is_zero = int(bool(x0_is_zero))
     o.use_graph = 2 if persistent else int(bool(use_graph))
+    o.poly_form = _POLY[poly] if isinstance(poly, str) else int(poly)
     return o
 
 

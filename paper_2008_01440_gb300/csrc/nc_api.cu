@@ -58,6 +58,11 @@ struct nc_solver_s {
     double theta = 0.0, delta = 0.0, sigma = 0.0;
     std::vector<double> ca, cb, cc, cd;   // per Chebyshev step 1..k (index 0 unused)
     double ca1_shifted = 0.0;             // step-1 coefficient of u = r for the shifted operator
+    // Newton form (Algorithm 1): k = 2^nlev - 1, zeta_0..zeta_nlev, and two
+    // float64 work vectors per level >= 2 (t1 = P_{j-1} v and p = A t1)
+    int nlev = -1;
+    std::vector<double> zeta;
+    std::vector<double*> nbuf;
     bool mixed = false;
     int vdt = NC_F64;
     OpView op64;                          // float64 operator (outer CG, true residual)
@@ -289,11 +294,56 @@ void setup_coefficients(nc_solver S) {
 
 // z = P_k(A) r.  r64: float64 residual; the mixed path reads S->r32 (which
 // must already hold (float) r64).  fin: reduction of (r, z) or FIN_NONE.
+// out = g P_j v (+ w_coef w when w is non-null) by the recursion of
+// Algorithm 1, P_0 = zeta_0 I, P_{j+1} v = zeta_{j+1} (2 P_j v - P_j A P_j v),
+// depth first: 2^j - 1 products.  A level-1 application is one fused step,
+// g zeta_1 zeta_0 (2 v - zeta_0 A v); a level j >= 2 computes t1 = P_{j-1} v
+// and p = A t1 into its own two vectors, then P_{j-1} p into `out`, and
+// combines out = g zeta_j (2 t1 - out) -- for j = 2 inside the last fused
+// step (its x_{k-2} slot carries t1).  With rdot, the last kernel also forms
+// (rdot, out) for the PCG scalars.
+cudaError_t enqueue_newton(nc_solver S, int j, const double* v, double* out, double g, const double* w,
+                           double w_coef, const double* rdot, const Reduce& R, const int* done, cudaStream_t st) {
+    const int n = (int)S->n;
+    const Reduce none = make_reduce(S->partials, S->counter, S->S, nullptr, FIN_NONE);
+    const std::vector<double>& z = S->zeta;
+    const int dot = rdot != nullptr ? 1 : 0;
+    if (j == 0) {   // only as the whole preconditioner (k = 0): out = zeta_0 v
+        return launch_scale_dot(n, v, g * z[0], out, R, done, st);
+    }
+    if (j == 1) {
+        // g zeta_1 zeta_0 (2 v - zeta_0 A v) (+ w_coef w); A v = A' v + shift v
+        const double cd = -g * z[1] * z[0] * z[0];
+        const double ca = 2.0 * g * z[1] * z[0] + cd * S->shift;
+        return op_step(S->op64, false, true, v, w, nullptr, out, ca, w != nullptr ? w_coef : 0.0, 0.0, cd, dot,
+                       rdot, dot ? R : none, done, st);
+    }
+    double* t1 = S->nbuf[2 * (j - 2)];
+    double* pv = S->nbuf[2 * (j - 2) + 1];
+    cudaError_t e = enqueue_newton(S, j - 1, v, t1, 1.0, nullptr, 0.0, nullptr, none, done, st);
+    if (e) return e;
+    e = op64_apply(S, t1, nullptr, pv, 0.0, 1.0, 0, none, done, st);   // p = A t1
+    if (e) return e;
+    if (j == 2 && w == nullptr) {
+        // out = g zeta_2 (2 t1 - P_1 p): the fused level-1 step with t1 in its w slot
+        return enqueue_newton(S, 1, pv, out, -g * z[2], t1, 2.0 * g * z[2], rdot, R, done, st);
+    }
+    e = enqueue_newton(S, j - 1, pv, out, 1.0, nullptr, 0.0, nullptr, none, done, st);
+    if (e) return e;
+    // out = g zeta_j (2 t1 - out) (+ w_coef w, folded by one more pass)
+    e = launch_axpby_dot(n, 2.0 * g * z[j], t1, -g * z[j], out, out, w != nullptr ? nullptr : rdot,
+                         w != nullptr ? none : R, done, st);
+    if (e || w == nullptr) return e;
+    return launch_axpby_dot(n, 1.0, out, w_coef, w, out, rdot, rdot ? R : none, done, st);
+}
+
 cudaError_t enqueue_poly(nc_solver S, const double* r64, double* z, int fin, const int* done,
                          cudaStream_t st) {
     const int n = (int)S->n;
     const Reduce R = make_reduce(S->partials, S->counter, S->S, nullptr, fin);
     if (S->k == 0) return launch_scale_dot(n, r64, 1.0 / S->theta, z, R, done, st);
+    if (S->nlev >= 1)
+        return enqueue_newton(S, S->nlev, r64, z, 1.0, nullptr, 0.0, fin != FIN_NONE ? r64 : nullptr, R, done, st);
     const void* rx = S->mixed ? static_cast<const void*>(S->r32) : static_cast<const void*>(r64);
     for (int j = 1; j <= S->k; ++j) {
         const void* u = (j == 1) ? rx : S->buf[(j - 1) % 3];
@@ -737,6 +787,7 @@ void nc_options_default(nc_options* opt) {
     opt->x0_is_zero = 0;
     opt->use_graph = 1;
     opt->spmv_format = NC_FORMAT_AUTO;
+    opt->poly_form = NC_POLY_CHEBYSHEV;
 }
 
 const char* nc_strerror(nc_status s) {
@@ -1016,6 +1067,16 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
     if (o.apply_dtype != NC_F64 && o.apply_dtype != NC_F32 && o.apply_dtype != NC_BF16) return NC_ERR_ARG;
     if (o.rr_period < 0) return NC_ERR_ARG;
     if (o.spmv_format < NC_FORMAT_AUTO || o.spmv_format > NC_FORMAT_TUNE) return NC_ERR_ARG;
+    int nlev = -1;
+    if (o.poly_form == NC_POLY_NEWTON) {
+        // Algorithm 1 builds P of degree 2^nlev - 1 only; float64 only
+        for (int L = 0; L <= 12; ++L)
+            if ((1 << L) - 1 == degree_k) nlev = L;
+        if (nlev < 0) return NC_ERR_ARG;
+        if (o.apply_dtype != NC_F64) return NC_ERR_UNSUPPORTED;
+    } else if (o.poly_form != NC_POLY_CHEBYSHEV) {
+        return NC_ERR_ARG;
+    }
     cudaStream_t st = as_stream(stream);
     nc_solver S = new (std::nothrow) nc_solver_s();
     if (!S) return NC_ERR_OOM;
@@ -1029,6 +1090,19 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
     S->mixed = o.apply_dtype != NC_F64;
     S->vdt = o.apply_dtype;
     setup_coefficients(S);
+    if (nlev >= 0) {
+        // zeta_0..zeta_nlev (Eq. zetaNewt) on the interval of the scaled
+        // Chebyshev polynomial, [theta' - delta, theta' + delta] (Sec. 4)
+        S->nlev = nlev;
+        S->zeta.assign(nlev + 1, 0.0);
+        const double a0 = S->theta - S->delta, b0 = S->theta + S->delta;
+        S->zeta[0] = 2.0 / (a0 + b0);
+        if (nlev >= 1) {
+            const double a = a0 * S->zeta[0];
+            S->zeta[1] = 2.0 / (1.0 + 2.0 * a - a * a);
+        }
+        for (int i = 2; i <= nlev; ++i) S->zeta[i] = 2.0 / (1.0 + 2.0 * S->zeta[i - 1] - S->zeta[i - 1] * S->zeta[i - 1]);
+    }
     const int64_t n = S->n;
     nc_status s = NC_OK;
     do {
@@ -1041,6 +1115,12 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
         for (int i = 0; i < 3 && s == NC_OK; ++i) s = dev_alloc(&S->buf[i], vb * (size_t)(n > 0 ? n : 1));
         if (s) break;
         if (S->mixed && (s = dev_alloc_n(&S->r32, n))) break;
+        if (S->nlev >= 2) {
+            S->nbuf.assign(2 * (S->nlev - 1), nullptr);
+            for (auto& bp : S->nbuf)
+                if ((s = dev_alloc_n(&bp, n > 0 ? n : 1))) break;
+            if (s) break;
+        }
         if ((s = setup_operator(S, st)) != NC_OK) break;
         cudaError_t e;
         if ((e = cudaMemsetAsync(S->counter, 0, sizeof(unsigned int), st)) ||
@@ -1049,7 +1129,7 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
         }
         if ((e = cudaMallocHost(&S->h_io, sizeof(PcgScalars)))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
         if ((e = cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
-        if (o.use_graph == 2 && S->op64.kind == OP_SELL && !S->mixed && o.rr_period == 0 &&
+        if (o.use_graph == 2 && S->op64.kind == OP_SELL && !S->mixed && o.rr_period == 0 && S->nlev < 0 &&
             plan_cluster_pcg(n, S->h_sell_ptr.data(), &S->plan)) {
             // one-cluster solve: per-step coefficients of the shifted operator
             std::vector<double> cf(4 * (size_t)(S->k + 1), 0.0);
@@ -1146,6 +1226,7 @@ nc_status pcg_destroy(nc_solver S) {
     dev_free(S->r32); dev_free(S->lval); dev_free(S->partials); dev_free(S->counter); dev_free(S->S);
     dev_free(S->sell_ptr); dev_free(S->sell_col); dev_free(S->sell_val64); dev_free(S->sell_valP);
     dev_free(S->pcoef);
+    for (double* bp : S->nbuf) dev_free(bp);
     if (S->h_io) cudaFreeHost(S->h_io);
     delete S;
     return NC_OK;

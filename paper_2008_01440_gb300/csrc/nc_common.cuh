@@ -263,6 +263,10 @@ cudaError_t launch_copy_out(int n, const double* xs, const double* dis, double d
 // y = y + a x and (y, y) -> R
 cudaError_t launch_axpy_dot(int n, double a, const double* x, double* y, const Reduce& R,
                             cudaStream_t st);
+// out = a x + b y (out may alias y); with rdot non-null, (rdot, out) -> R;
+// skipped when *done
+cudaError_t launch_axpby_dot(int n, double a, const double* x, double b, const double* y, double* out,
+                             const double* rdot, const Reduce& R, const int* done, cudaStream_t st);
 // r32 = (float) r unless *skip
 cudaError_t launch_refresh_r32(int n, const double* r, float* r32, const int* skip, cudaStream_t st);
 // y = x / d

@@ -98,6 +98,21 @@ axpy_dot_kernel(int n, double a, const double* __restrict__ x, double* __restric
     grid_reduce<kBlock>(acc, R);
 }
 
+// out = a x + b y (out may alias y); with rdot, (rdot, out) -> R.  The level
+// combine of the Newton recursion, zeta_j (2 P_j u - P_j A P_j u).
+__global__ void __launch_bounds__(kBlock)
+axpby_dot_kernel(int n, double a, const double* __restrict__ x, double b, const double* y, double* out,
+                 const double* __restrict__ rdot, const Reduce R, const int* __restrict__ done) {
+    if (done != nullptr && *done) return;
+    double acc = 0.0;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+        const double o = fma(a, x[i], b * y[i]);
+        out[i] = o;
+        if (rdot != nullptr) acc = fma(rdot[i], o, acc);
+    }
+    if (rdot != nullptr && R.fin != FIN_NONE) grid_reduce<kBlock>(acc, R);
+}
+
 __global__ void refresh_r32_kernel(int n, const double* __restrict__ r, float* __restrict__ r32,
                                    const int* __restrict__ skip) {
     if (*skip) return;
@@ -159,6 +174,12 @@ cudaError_t launch_copy_out(int n, const double* xs, const double* dis, double d
 cudaError_t launch_axpy_dot(int n, double a, const double* x, double* y, const Reduce& R,
                             cudaStream_t st) {
     axpy_dot_kernel<<<vec_grid(n), kBlock, 0, st>>>(n, a, x, y, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpby_dot(int n, double a, const double* x, double b, const double* y, double* out,
+                             const double* rdot, const Reduce& R, const int* done, cudaStream_t st) {
+    axpby_dot_kernel<<<vec_grid(n), kBlock, 0, st>>>(n, a, x, b, y, out, rdot, R, done);
     return cudaGetLastError();
 }
 

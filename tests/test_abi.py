@@ -9,6 +9,8 @@ import pytest
 
 from conftest import ROOT
 
+HEADER = os.path.join(ROOT, "include", "nc_pcg.h")
+
 
 def declared_symbols():
     names = set()
@@ -62,3 +64,30 @@ def test_binding_imports_and_matches_header(libpath):
 def test_built_only_for_sm103a():
     from paper_2008_01440_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _header_struct_fields(name):
+    """Field names, in order, of `typedef struct { ... } name;` in the header."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    names = []
+    for decl in m.group(1).split(";"):
+        parts = [p.strip() for p in decl.strip().split(",") if p.strip()]
+        if parts:   # "double theta, delta, sigma": the type prefixes the first name only
+            names.append(re.findall(r"(\w+)$", parts[0])[0])
+            names.extend(parts[1:])
+    return names
+
+
+def test_binding_structs_match_header(libpath):
+    """The ctypes mirrors of the option, info and result structs list the
+    header's fields in the header's order (an ABI mismatch would shift every
+    field after it)."""
+    from paper_2008_01440_gb300 import binding
+    for name in ("nc_options", "nc_solver_info", "nc_result"):
+        cls = getattr(binding, name)
+        assert [f for f, _ in cls._fields_] == _header_struct_fields(name), name
+    o = binding.make_options(poly="newton", persistent=True, apply_dtype="f32")
+    assert (o.poly_form, o.use_graph, o.apply_dtype) == (1, 2, 1)
