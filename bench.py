@@ -52,10 +52,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "fd3d"])
     ap.add_argument("--k", type=int, default=None, help="polynomial degree (default: the workload's)")
     ap.add_argument("--apply", default="f64", choices=["f64", "f32", "bf16"])
-    ap.add_argument("--grid", type=int, default=None, help="grid side (c2) or nodes per side (c3)")
+    ap.add_argument("--grid", type=int, default=None,
+                    help="grid side (c2), nodes per side (c3) or subdivisions nx (fd3d)")
     ap.add_argument("--requests", type=int, default=120, help="c5: number of requests")
     ap.add_argument("--c4-systems", type=int, default=256, help="c4: number of systems")
     ap.add_argument("--no-modes", action="store_true", help="skip the other apply precisions")
@@ -695,6 +696,130 @@ def run_c5(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ paper workload ----
+# The paper's FD-3D(nx) results (Sec. 5.3, Table 8): iterations and CPU time
+# T_p on p processes of Marconi100 (2 x 16-core POWER9 per node, CPU only).
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 float64 rate (no tensor path)
+PAPER_FD3D = {512: {"procs": 512, "nlev": {5: (45, 13.8), 2: (325, 13.3), 0: (1300, 16.8)}},
+              1024: {"procs": 1024, "nlev": {5: (88, 97.2), 2: (637, 101.6), 0: (2553, 131.5)}}}
+
+
+def run_fd3d(args, rank, world, local_rank):
+    """FD-3D(nx), the paper's own large problems (Sec. 5.3): the 7-point
+    Poisson operator on the (nx-1)^3 interior points of the unit cube,
+    matrix-free; x* = ones, b = A x*, x0 = 0; Jacobi scaling (c0 = 6, a
+    scalar); exact bounds of the scaled operator 1 -+ cos(pi/nx); s = 1.001;
+    tol 1e-8; nlev = 5, 2, 0 (k = 31, 3, 0), the degree-31 polynomial in both
+    the Chebyshev and the Newton form."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local_rank)
+    import paper_2008_01440_gb300 as nc
+    import workloads as W
+    dev = torch.device("cuda", local_rank)
+    nx = args.grid or 512
+    m = nx - 1
+    n = m ** 3
+    A = nc.nc_matrix_stencil7(m, m, m, 6.0, 1.0, 1.0, 1.0)
+    As = nc.nc_matrix_jacobi(A)
+    lo, hi = W.stencil7_bounds(W.Stencil7(m, m, m, 1.0, 1.0 / 6, 1.0 / 6, 1.0 / 6))
+    ones = torch.ones(n, dtype=torch.float64, device=dev)
+    b = torch.empty(n, dtype=torch.float64, device=dev)
+    nc.nc_matvec(A, ones, b)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    steps, warmup = max(1, min(args.steps, 3)), max(0, min(args.warmup, 1))
+    runs = {}
+    clk = None
+    for nlev, form, mode in ((5, "chebyshev", "f64"), (5, "newton", "f64"), (2, "chebyshev", "f64"),
+                             (0, "chebyshev", "f64"), (5, "chebyshev", "f32")):
+        k = 2 ** nlev - 1
+        S = nc.pcg_setup(As, lo, hi, k, S_THETA, x0_is_zero=True, poly=form, apply_dtype=mode,
+                         rr_period=50 if mode != "f64" else 0)
+        for _ in range(warmup):
+            nc.pcg_solve(S, b, x, TOL, MAXIT)
+        replica_barrier(world)
+        main_cfg = nlev == 5 and form == "chebyshev" and mode == "f64"
+        if main_cfg:
+            clk = start_clocks(torch, dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            res = nc.pcg_solve(S, b, x, TOL, MAXIT)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = replica_max(e0.elapsed_time(e1) / 1e3 / steps, world)
+        if main_cfg:
+            clocks = clk.stop()
+            # the fused stencil step alone: CUDA events around P_31 applications
+            z = torch.empty(n, dtype=torch.float64, device=dev)
+            nc.pcg_apply_poly(S, b, z)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(3):
+                nc.pcg_apply_poly(S, b, z)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            t_step = a0.elapsed_time(a1) / 1e3 / (3 * k)
+            del z
+        err = float(torch.linalg.norm(x - ones) / torch.linalg.norm(ones))
+        runs[f"nlev{nlev}_{form}" + ("" if mode == "f64" else f"_{mode}apply_rr50")] = {
+            "k": k, "iters": res["iters"], "seconds_per_solve": round(sec, 4),
+                                      "relres": res["relres"], "true_relres": res["true_relres"],
+                                      "err_vs_exact_solution": err, "converged": res["status"] == 0}
+        S.close()
+    main_run = runs["nlev5_chebyshev"]
+    paper = PAPER_FD3D.get(nx)
+    peak, src = peak_hbm()
+    step_bytes = 4 * n * 8   # u_{k-1}, x_{k-2}, r read, x_k written; no matrix
+    # the float64 matrix-free step is bound by GB300's float64 rate, not HBM:
+    # 14 flops per point (e0 u, three neighbour pairs, the r and x_{k-2}
+    # terms) against the nominal 1.25 TFLOP/s float64 peak
+    step_flops = 14 * n
+    roofline = {"bound": "alu", "achieved": round(step_flops / t_step / 1e12, 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(step_flops / t_step / 1e12 / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "nominal float64 rate (1.25 TFLOP/s; an FMA-chain probe measured 1.20)",
+                "kernel": "stencil7_step_kernel (matrix-free 7-point step, float64)",
+                "flops_per_launch": step_flops, "bytes_per_launch": step_bytes,
+                "hbm": {"achieved_GBps": round(step_bytes / t_step / 1e9, 1), "peak": peak,
+                        "frac": round(step_bytes / t_step / 1e9 / peak, 4)},
+                "us_per_launch": round(t_step * 1e6, 2)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import time as _t
+        import oracle as O
+        mv = O.stencil7_matvec(m, m, m, 1.0, 1.0 / 6, 1.0 / 6, 1.0 / 6)
+        v = np.ones(n)
+        t0 = _t.perf_counter()
+        mv(v)
+        t_mv = _t.perf_counter() - t0
+        est = main_run["iters"] * (main_run["k"] + 1) * t_mv
+        cpu = {"value": round(1.0 / est, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"one oracle 7-point product on the full {m}^3 grid ({t_mv:.2f} s), extrapolated to "
+                         f"{main_run['iters']} x {main_run['k'] + 1} products (vector updates not counted)"}
+    line = {"metric": METRIC, "value": round(1.0 / main_run["seconds_per_solve"], 4), "unit": "solves/s",
+            "n_gpus": world, "steps": steps, "warmup": warmup,
+            "ms_per_step": round(1e3 * main_run["seconds_per_solve"], 2), "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": (round((1.0 / main_run["seconds_per_solve"]) / (1.0 / paper["nlev"][5][1]), 2)
+                            if paper else None),
+            "dtype": "f64", "data": "synthetic (the paper's FD-3D Poisson problem, x* = ones)",
+            "config": {"workload": f"FD-3D({nx}) Poisson, 7-point matrix-free on {m}^3 (n={n}), Jacobi, exact "
+                                   "bounds, s=1.001, tol 1e-8, nlev=5 (k=31)", "l2": "inputs larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "runs": runs, "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu,
+            "t_nlev0_over_t_nlev5": round(runs["nlev0_chebyshev"]["seconds_per_solve"] /
+                                          main_run["seconds_per_solve"], 2),
+            "paper": ({"procs": paper["procs"], "hardware": "Marconi100, 2x16-core POWER9 per node, CPU only",
+                       "iters_nlev5_2_0": [paper["nlev"][L][0] for L in (5, 2, 0)],
+                       "seconds_nlev5_2_0": [paper["nlev"][L][1] for L in (5, 2, 0)]} if paper else None),
+            "gpu_launches": steps * (1 + (4 + main_run["k"]) + main_run["iters"] * (main_run["k"] + 3) + 3)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local_rank = dist_env()
@@ -708,6 +833,8 @@ def main():
             run_c4(args, rank, world, local_rank)
         elif args.workload == "c5":
             run_c5(args, rank, world, local_rank)
+        elif args.workload == "fd3d":
+            run_fd3d(args, rank, world, local_rank)
         else:
             spec = {"c1": spec_c1, "c2": spec_c2, "c3": spec_c3}[args.workload](args)
             run_system(args, spec, rank, world, local_rank)
