@@ -241,6 +241,23 @@ NC_API nc_status pcg_solve(nc_solver S, const double* b_dev, double* x_dev, doub
 NC_API nc_status pcg_solve_host(nc_solver S, const double* b_host, double* x_host, double tol,
                          int maxit, void* stream, nc_result* res);
 
+/* Solve A X = B for m right-hand sides at once, 1 <= m <= 8: m independent
+ * PCG recurrences (each with its own alpha, beta, stopping test and Table 4
+ * counts) whose products with A share the matrix -- every fused Chebyshev
+ * step and every q = A p reads A once for all m columns (a sparse matrix
+ * times a dense block).  A column that stops is frozen while the others go
+ * on.  B_dev, X_dev: n x m float64 on the device, column-major (column c at
+ * offset c*n); X_dev holds the initial guesses unless opt.x0_is_zero.  res:
+ * host array of m results (required).  Returns NC_OK when every column
+ * converged, else the first column's non-OK status.  Needs the sliced
+ * (SELL) layout and the Chebyshev form without residual replacement
+ * (NC_ERR_UNSUPPORTED otherwise); allocates 9 m n-vectors of workspace on
+ * first use for a given m (kept until pcg_destroy).  Synchronises `stream`.
+ * Not in the paper: a throughput form of its solver for many right-hand
+ * sides. */
+NC_API nc_status pcg_solve_multi(nc_solver S, int m, const double* B_dev, double* X_dev, double tol, int maxit,
+                                 void* stream, nc_result* res);
+
 /* Layout and parameters the solver chose. */
 NC_API nc_status pcg_get_info(nc_solver S, nc_solver_info* info);
 

@@ -59,4 +59,5 @@ from .binding import (  # noqa: F401
     pcg_setup,
     pcg_solve,
     pcg_solve_host,
+    pcg_solve_multi,
 )

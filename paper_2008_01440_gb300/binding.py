@@ -79,6 +79,8 @@ _SIGS = {
     "pcg_apply_poly": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "pcg_solve": (ctypes.c_int, [_vp, _vp, _vp, _dbl, ctypes.c_int, _vp, ctypes.POINTER(nc_result)]),
     "pcg_solve_host": (ctypes.c_int, [_vp, _vp, _vp, _dbl, ctypes.c_int, _vp, ctypes.POINTER(nc_result)]),
+    "pcg_solve_multi": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _dbl, ctypes.c_int, _vp,
+                                       ctypes.POINTER(nc_result)]),
     "pcg_destroy": (ctypes.c_int, [_vp]),
     "pcg_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(nc_solver_info)]),
     "nc_apply_poly_csr_noalloc": (ctypes.c_int, [_i64, _vp, _vp, _vp, _dbl, _dbl, ctypes.c_int, _dbl, _vp, _vp,
@@ -286,6 +288,21 @@ def pcg_solve(S: Solver, b, x, tol: float, maxit: int, stream=None) -> dict:
     if st not in SOLVE_STATUSES:
         _check(st, "pcg_solve")
     return res.as_dict()
+
+
+def pcg_solve_multi(S: Solver, B, X, tol: float, maxit: int, stream=None) -> list:
+    """B, X: CUDA float64 tensors of shape (m, n) (row c = right-hand side /
+    solution c, i.e. the n x m block column-major), 1 <= m <= 8."""
+    import torch
+    if B.dim() != 2 or B.shape != X.shape or B.shape[1] != S.n:
+        raise ValueError(f"B, X: expected equal shapes (m, {S.n})")
+    m = int(B.shape[0])
+    res = (nc_result * m)()
+    st = lib.pcg_solve_multi(S.handle, m, _ptr(B, torch.float64, m * S.n, "B"), _ptr(X, torch.float64, m * S.n, "X"),
+                             float(tol), int(maxit), _stream(stream), res)
+    if st not in SOLVE_STATUSES:
+        _check(st, "pcg_solve_multi")
+    return [r.as_dict() for r in res]
 
 
 def pcg_solve_host(S: Solver, b, x, tol: float, maxit: int, stream=None) -> dict:

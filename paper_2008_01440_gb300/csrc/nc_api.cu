@@ -63,6 +63,17 @@ struct nc_solver_s {
     int nlev = -1;
     std::vector<double> zeta;
     std::vector<double*> nbuf;
+    // multi-right-hand-side workspace (pcg_solve_multi), allocated on first
+    // use for up to mcap columns: column c of each block at offset c * n
+    int mcap = 0;
+    double *mb = nullptr, *mx = nullptr, *mr = nullptr, *mz = nullptr, *mp = nullptr, *mq = nullptr;
+    void* mbuf[3] = {nullptr, nullptr, nullptr};
+    float* mr32 = nullptr;
+    PcgScalars* mS = nullptr;          // device, one per column
+    PcgScalars* mh = nullptr;          // pinned host copy
+    cudaGraphExec_t mexec = nullptr;   // graph of the last column count
+    int mexec_m = 0;
+    bool mgraph_failed = false;
     bool mixed = false;
     int vdt = NC_F64;
     OpView op64;                          // float64 operator (outer CG, true residual)
@@ -512,6 +523,165 @@ nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
     rr.n_replace = o.n_replace;
     if (res) *res = rr;
     return (nc_status)o.status;
+}
+
+// ---- several right-hand sides sharing the matrix ----------------------------
+// m PCG recurrences (Algorithm 1's outer loop, one per column) whose products
+// with A are one block kernel per step (launch_sell_mstep: the matrix read
+// once for all columns); dot products, updates and the stopping test run
+// per column in the single-vector kernels, each on its own scalar block, so
+// a column that stops is frozen while the others go on.
+
+cudaError_t menqueue_poly(nc_solver S, int m, int fin, cudaStream_t st) {
+    const int n = (int)S->n;
+    const size_t cn = (size_t)n;
+    if (S->k == 0) {
+        for (int c = 0; c < m; ++c) {
+            cudaError_t e = launch_scale_dot(n, S->mr + c * cn, 1.0 / S->theta, S->mz + c * cn,
+                                             make_reduce(S->partials, S->counter, S->mS + c, nullptr, fin),
+                                             &S->mS[c].done, st);
+            if (e) return e;
+        }
+        return cudaSuccess;
+    }
+    const void* rx = S->mixed ? static_cast<const void*>(S->mr32) : static_cast<const void*>(S->mr);
+    for (int j = 1; j <= S->k; ++j) {
+        const void* u = (j == 1) ? rx : S->mbuf[(j - 1) % 3];
+        const void* w = (j >= 3) ? S->mbuf[(j - 2) % 3] : nullptr;
+        const bool last = (j == S->k);
+        void* y = last ? static_cast<void*>(S->mz) : S->mbuf[j % 3];
+        double ca = S->ca[j];
+        if (S->shift != 0.0) ca = (j == 1) ? S->ca1_shifted : 0.0;
+        cudaError_t e = launch_sell_mstep(n, m, n, S->opP.ptr, S->opP.col, S->opP.val, S->opP.vdt, S->mixed,
+                                          last || !S->mixed, u, w, rx, y, ca, S->cb[j], S->cc[j], S->cd[j], S->mS,
+                                          st);
+        if (e) return e;
+    }
+    if (fin == FIN_NONE) return cudaSuccess;
+    for (int c = 0; c < m; ++c) {
+        cudaError_t e = launch_dot(n, S->mr + c * cn, S->mz + c * cn,
+                                   make_reduce(S->partials, S->counter, S->mS + c, nullptr, fin), &S->mS[c].done, st);
+        if (e) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t menqueue_prologue(nc_solver S, int m, cudaStream_t st) {
+    const int n = (int)S->n;
+    const size_t cn = (size_t)n;
+    cudaError_t e;
+    for (int c = 0; c < m; ++c) {
+        double* b = S->mb + c * cn;
+        double* x = S->mx + c * cn;
+        double* r = S->mr + c * cn;
+        PcgScalars* Sc = S->mS + c;
+        const Reduce none = make_reduce(S->partials, S->counter, Sc, nullptr, FIN_NONE);
+        if ((e = launch_dot(n, b, b, make_reduce(S->partials, S->counter, Sc, nullptr, FIN_BB), nullptr, st))) return e;
+        e = S->opt.x0_is_zero ? launch_copy(n, b, r, nullptr, st) : op64_apply(S, x, b, r, 1.0, -1.0, 0, none, nullptr, st);
+        if (e) return e;
+        if ((e = launch_dot(n, r, r, make_reduce(S->partials, S->counter, Sc, nullptr, FIN_RR0), nullptr, st))) return e;
+        if (S->mixed && (e = launch_convert(n, r, NC_F32, S->mr32 + c * cn, st))) return e;
+    }
+    if ((e = menqueue_poly(S, m, FIN_RZ0, st))) return e;
+    for (int c = 0; c < m; ++c)
+        if ((e = launch_copy(n, S->mz + c * cn, S->mp + c * cn, &S->mS[c].done, st))) return e;
+    return cudaSuccess;
+}
+
+cudaError_t menqueue_body(nc_solver S, int m, cudaGraphConditionalHandle h, int use_cond, int* active,
+                          cudaStream_t st) {
+    const int n = (int)S->n;
+    const size_t cn = (size_t)n;
+    cudaError_t e;
+    // q = A p for all columns (A' p + shift p with the shifted operator)
+    if ((e = launch_sell_mstep(n, m, n, S->op64.ptr, S->op64.col, S->op64.val, NC_F64, false, true, S->mp, nullptr,
+                               nullptr, S->mq, S->shift, 0.0, 0.0, 1.0, S->mS, st)))
+        return e;
+    for (int c = 0; c < m; ++c) {
+        PcgScalars* Sc = S->mS + c;
+        if ((e = launch_dot(n, S->mp + c * cn, S->mq + c * cn,
+                            make_reduce(S->partials, S->counter, Sc, nullptr, FIN_ALPHA), &Sc->done, st)))
+            return e;
+        if ((e = launch_axpy2_rr(n, S->mx + c * cn, S->mr + c * cn, S->mp + c * cn, S->mq + c * cn,
+                                 S->mixed ? S->mr32 + c * cn : nullptr,
+                                 make_reduce(S->partials, S->counter, Sc, nullptr, FIN_RR), st)))
+            return e;
+    }
+    if ((e = menqueue_poly(S, m, FIN_BETA, st))) return e;
+    for (int c = 0; c < m; ++c)
+        if ((e = launch_p_update(n, S->mp + c * cn, S->mz + c * cn, S->mS + c, h, 0, st))) return e;
+    return launch_any_active(S->mS, m, h, use_cond, active, st);
+}
+
+nc_status mbuild_graph(nc_solver S, int m) {
+    if (S->mexec) {
+        cudaGraphExecDestroy(S->mexec);
+        S->mexec = nullptr;
+    }
+    cudaGraph_t g = nullptr, gp = nullptr;
+    cudaGraphNode_t np = nullptr, nw = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    nc_status st = NC_ERR_CUDA;
+    cudaError_t e;
+    do {
+        if ((e = cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal))) break;
+        cudaError_t e1 = menqueue_prologue(S, m, S->cap);
+        e = cudaStreamEndCapture(S->cap, &gp);
+        if (e1) { e = e1; break; }
+        if (e) break;
+        if ((e = cudaGraphCreate(&g, 0))) break;
+        if ((e = cudaGraphAddChildGraphNode(&np, g, nullptr, 0, gp))) break;
+        if ((e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault))) break;
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if ((e = cudaGraphAddNode(&nw, g, &np, nullptr, 1, &cp))) break;
+        cudaGraph_t gb = cp.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(S->cap, gb, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+            break;
+        e1 = menqueue_body(S, m, h, 1, nullptr, S->cap);
+        cudaGraph_t gb_out = nullptr;
+        e = cudaStreamEndCapture(S->cap, &gb_out);
+        if (e1) { e = e1; break; }
+        if (e) break;
+        if ((e = cudaGraphInstantiate(&S->mexec, g, 0))) break;
+        S->mexec_m = m;
+        st = NC_OK;
+    } while (0);
+    if (st != NC_OK) {
+        g_last_cuda = e;
+        cudaGetLastError();
+        S->mexec = nullptr;
+    }
+    if (gp) cudaGraphDestroy(gp);
+    if (g) cudaGraphDestroy(g);
+    return st;
+}
+
+nc_status mreserve(nc_solver S, int m) {
+    if (m <= S->mcap) return NC_OK;
+    if (S->mexec) {
+        cudaGraphExecDestroy(S->mexec);
+        S->mexec = nullptr;
+    }
+    dev_free(S->mb); dev_free(S->mx); dev_free(S->mr); dev_free(S->mz); dev_free(S->mp); dev_free(S->mq);
+    for (auto& bp : S->mbuf) { dev_free(bp); bp = nullptr; }
+    dev_free(S->mr32); dev_free(S->mS);
+    if (S->mh) cudaFreeHost(S->mh);
+    S->mb = S->mx = S->mr = S->mz = S->mp = S->mq = nullptr;
+    S->mr32 = nullptr; S->mS = nullptr; S->mh = nullptr; S->mcap = 0;
+    const int64_t len = (int64_t)m * S->n;
+    const size_t vb = S->mixed ? sizeof(float) : sizeof(double);
+    NC_TRY(dev_alloc_n(&S->mb, len)); NC_TRY(dev_alloc_n(&S->mx, len)); NC_TRY(dev_alloc_n(&S->mr, len));
+    NC_TRY(dev_alloc_n(&S->mz, len)); NC_TRY(dev_alloc_n(&S->mp, len)); NC_TRY(dev_alloc_n(&S->mq, len));
+    for (auto& bp : S->mbuf) NC_TRY(dev_alloc(&bp, vb * (size_t)len));
+    if (S->mixed) NC_TRY(dev_alloc_n(&S->mr32, len));
+    NC_TRY(dev_alloc_n(&S->mS, m));
+    cudaError_t e = cudaMallocHost(&S->mh, sizeof(PcgScalars) * m);
+    if (e) { g_last_cuda = e; return NC_ERR_CUDA; }
+    S->mcap = m;
+    return NC_OK;
 }
 
 // Average time of one representative fused step (DOT-free, all four terms
@@ -1179,6 +1349,76 @@ nc_status pcg_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
     return run_solve(S, b_dev, x_dev, tol, maxit, as_stream(stream), res);
 }
 
+nc_status pcg_solve_multi(nc_solver S, int m, const double* B_dev, double* X_dev, double tol, int maxit,
+                          void* stream, nc_result* res) {
+    if (!S || !(tol >= 0.0) || maxit < 0 || m < 1 || m > max_rhs() || !res) return NC_ERR_ARG;
+    if (S->n == 0) {
+        for (int c = 0; c < m; ++c) res[c] = nc_result{0, NC_OK, 0.0, 0.0, 0, 0, 0};
+        return NC_OK;
+    }
+    if (!B_dev || !X_dev || B_dev == X_dev) return NC_ERR_ARG;
+    if (S->op64.kind != OP_SELL || S->opP.kind != OP_SELL || S->opt.rr_period > 0 || S->nlev >= 0)
+        return NC_ERR_UNSUPPORTED;
+    NC_TRY(mreserve(S, m));
+    cudaStream_t st = as_stream(stream);
+    const int n = (int)S->n;
+    const size_t cn = (size_t)n;
+    for (int c = 0; c < m; ++c) {
+        PcgScalars init;
+        std::memset(&init, 0, sizeof(init));
+        init.tol2 = tol * tol;
+        init.maxit = maxit;
+        init.status = NC_ERR_MAXIT;
+        init.rr_skip = 1;
+        S->mh[c] = init;
+    }
+    NC_CU(cudaMemcpyAsync(S->mS, S->mh, sizeof(PcgScalars) * m, cudaMemcpyHostToDevice, st));
+    for (int c = 0; c < m; ++c)
+        NC_CU(launch_copy_in(n, B_dev + c * cn, X_dev + c * cn, S->A->dis, S->A->dis_scalar, S->opt.x0_is_zero,
+                             S->mb + c * cn, S->mx + c * cn, st));
+    bool graph = S->opt.use_graph && !S->mgraph_failed;
+    if (graph && (S->mexec == nullptr || S->mexec_m != m) && mbuild_graph(S, m) != NC_OK) {
+        S->mgraph_failed = true;
+        graph = false;
+    }
+    if (graph) {
+        NC_CU(cudaGraphLaunch(S->mexec, st));
+    } else {
+        int* active = reinterpret_cast<int*>(&S->mS[0].pad1);   // scratch word of column 0's block
+        int h_active = 1;
+        NC_CU(menqueue_prologue(S, m, st));
+        for (;;) {
+            NC_CU(menqueue_body(S, m, 0, 0, active, st));
+            NC_CU(cudaMemcpyAsync(&h_active, active, sizeof(int), cudaMemcpyDeviceToHost, st));
+            NC_CU(cudaStreamSynchronize(st));
+            if (!h_active) break;
+        }
+    }
+    const Reduce none = make_reduce(S->partials, S->counter, S->mS, nullptr, FIN_NONE);
+    for (int c = 0; c < m; ++c) {
+        NC_CU(op64_apply(S, S->mx + c * cn, S->mb + c * cn, S->mq + c * cn, 1.0, -1.0, 0, none, nullptr, st));
+        NC_CU(launch_dot(n, S->mq + c * cn, S->mq + c * cn,
+                         make_reduce(S->partials, S->counter, S->mS + c, nullptr, FIN_TRUE), nullptr, st));
+        NC_CU(launch_copy_out(n, S->mx + c * cn, S->A->dis, S->A->dis_scalar, S->mS + c, X_dev + c * cn, st));
+    }
+    NC_CU(cudaMemcpyAsync(S->mh, S->mS, sizeof(PcgScalars) * m, cudaMemcpyDeviceToHost, st));
+    NC_CU(cudaStreamSynchronize(st));
+    nc_status first = NC_OK;
+    for (int c = 0; c < m; ++c) {
+        const PcgScalars& o = S->mh[c];
+        const double bn = std::sqrt(o.bb);
+        res[c].iters = o.iter;
+        res[c].status = o.status;
+        res[c].relres = bn > 0 ? std::sqrt(o.rr) / bn : 0.0;
+        res[c].true_relres = bn > 0 ? std::sqrt(o.rr_true) / bn : 0.0;
+        res[c].n_dot = o.n_dot;
+        res[c].n_spmv = (int64_t)o.iter + (int64_t)S->k * o.n_prec;
+        res[c].n_replace = 0;
+        if (first == NC_OK && o.status != NC_OK) first = (nc_status)o.status;
+    }
+    return first;
+}
+
 nc_status pcg_solve_host(nc_solver S, const double* b_host, double* x_host, double tol, int maxit,
                          void* stream, nc_result* res) {
     if (!S || !(tol >= 0.0) || maxit < 0) return NC_ERR_ARG;
@@ -1227,6 +1467,11 @@ nc_status pcg_destroy(nc_solver S) {
     dev_free(S->sell_ptr); dev_free(S->sell_col); dev_free(S->sell_val64); dev_free(S->sell_valP);
     dev_free(S->pcoef);
     for (double* bp : S->nbuf) dev_free(bp);
+    if (S->mexec) cudaGraphExecDestroy(S->mexec);
+    dev_free(S->mb); dev_free(S->mx); dev_free(S->mr); dev_free(S->mz); dev_free(S->mp); dev_free(S->mq);
+    for (void* bp : S->mbuf) dev_free(bp);
+    dev_free(S->mr32); dev_free(S->mS);
+    if (S->mh) cudaFreeHost(S->mh);
     if (S->h_io) cudaFreeHost(S->h_io);
     delete S;
     return NC_OK;

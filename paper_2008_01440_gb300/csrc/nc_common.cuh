@@ -263,6 +263,18 @@ cudaError_t launch_copy_out(int n, const double* xs, const double* dis, double d
 // y = y + a x and (y, y) -> R
 cudaError_t launch_axpy_dot(int n, double a, const double* x, double* y, const Reduce& R,
                             cudaStream_t st);
+// Block step for m <= max_rhs() right-hand sides stored one after the other
+// (column c of u, w, r, y at offset c * ld): Y = ca U + cb W + cc R + cd A U,
+// the SELL matrix read once for all columns; returns at once when every
+// column's scalars (Sm[0..m)) say done.
+int max_rhs();
+cudaError_t launch_sell_mstep(int n, int m, int ld, const int32_t* slice_ptr, const int32_t* col, const void* val,
+                              int vdt, bool x_f32, bool y_f64, const void* u, const void* w, const void* r,
+                              void* y, double ca, double cb, double cc, double cd, const PcgScalars* Sm,
+                              cudaStream_t st);
+// loop condition of a multi-right-hand-side graph: some column not done
+cudaError_t launch_any_active(const PcgScalars* Sm, int m, cudaGraphConditionalHandle h, int use_cond, int* active,
+                              cudaStream_t st);
 // out = a x + b y (out may alias y); with rdot non-null, (rdot, out) -> R;
 // skipped when *done
 cudaError_t launch_axpby_dot(int n, double a, const double* x, double b, const double* y, double* out,

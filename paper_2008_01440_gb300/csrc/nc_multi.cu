@@ -1,0 +1,135 @@
+// Multi-right-hand-side fused step: the Chebyshev step of Algorithm 2 (and
+// q = A p) for m independent PCG recurrences that share the matrix:
+//     Y[:, c] = ca U[:, c] + cb W[:, c] + cc R[:, c] + cd (A U[:, c]),  c < m,
+// the coefficients being the same for every column (same polynomial).  The
+// m columns are stored one after the other (column c at offset c * ld), so
+// the per-column vector kernels of the outer loop run unchanged on them.
+//
+// One thread per row of the SELL-32 layout: each slot's column index and
+// value are loaded once and applied to all m columns -- the matrix, the
+// dominant stream of a step, is read once per step instead of m times (a
+// sparse times dense-block product).  The gathers of U stay per column.
+#include "nc_step.cuh"
+
+namespace nc {
+namespace {
+
+constexpr int kMaxRhs = 8;
+constexpr int kMG = 4;   // slots per load group
+
+__device__ __forceinline__ bool all_done(const PcgScalars* Sm, int m) {
+    for (int c = 0; c < m; ++c)
+        if (!Sm[c].done) return false;
+    return true;
+}
+
+template <typename VT, typename XT, typename YT>
+__global__ void __launch_bounds__(kBlock)
+sell_mstep_kernel(const int n, const int m, const int ld, const int32_t* __restrict__ slice_ptr,
+                  const int32_t* __restrict__ col, const VT* __restrict__ val, const XT* __restrict__ u,
+                  const XT* __restrict__ w, const XT* __restrict__ r, YT* __restrict__ y,
+                  const StepCoef<typename AccOf<XT>::type> cf, const PcgScalars* __restrict__ Sm) {
+    using AT = typename AccOf<XT>::type;
+    if (Sm != nullptr && all_done(Sm, m)) return;
+    const int row = blockIdx.x * kBlock + threadIdx.x;
+    if (row >= n) return;
+    const int s = row >> 5;
+    const int beg = slice_ptr[s];
+    const int len = (slice_ptr[s + 1] - beg) >> 5;   // warp-uniform
+    const VT* vp = val + beg + (row & 31);
+    const int32_t* cp = col + beg + (row & 31);
+    AT acc[kMaxRhs];
+#pragma unroll
+    for (int c = 0; c < kMaxRhs; ++c) acc[c] = AT(0);
+    for (int j0 = 0; j0 < len; j0 += kMG) {
+        int cj[kMG];
+        AT vj[kMG];
+#pragma unroll
+        for (int t = 0; t < kMG; ++t)
+            if (j0 + t < len) {
+                cj[t] = ld_stream(cp + 32 * t);
+                vj[t] = (AT)ld_stream(vp + 32 * t);
+            }
+#pragma unroll
+        for (int c = 0; c < kMaxRhs; ++c) {
+            if (c >= m) break;   // uniform
+            const XT* uc = u + (size_t)c * ld;
+            AT xv[kMG];
+#pragma unroll
+            for (int t = 0; t < kMG; ++t)
+                if (j0 + t < len) xv[t] = (AT)__ldg(uc + cj[t]);
+#pragma unroll
+            for (int t = 0; t < kMG; ++t)
+                if (j0 + t < len) acc[c] = fma(vj[t], xv[t], acc[c]);
+        }
+        vp += 32 * kMG;
+        cp += 32 * kMG;
+    }
+#pragma unroll
+    for (int c = 0; c < kMaxRhs; ++c) {
+        if (c >= m) break;
+        const size_t o = (size_t)c * ld;
+        AT v = cf.cd * acc[c];
+        if (cf.terms & kTermR) v = fma(cf.cc, (AT)r[o + row], v);
+        if (cf.terms & kTermW) v = fma(cf.cb, (AT)w[o + row], v);
+        if (cf.terms & kTermU) v = fma(cf.ca, (AT)u[o + row], v);
+        y[o + row] = (YT)v;
+    }
+}
+
+// Graph loop condition of a multi-right-hand-side solve: any column still running.
+__global__ void any_active_kernel(const PcgScalars* __restrict__ Sm, int m, cudaGraphConditionalHandle h,
+                                  int use_cond, int* __restrict__ active) {
+    int a = 0;
+    for (int c = 0; c < m; ++c) a |= Sm[c].done ? 0 : 1;
+    if (active) *active = a;
+    if (use_cond) cudaGraphSetConditional(h, a ? 1u : 0u);
+}
+
+template <typename VT, typename XT, typename YT>
+cudaError_t mstep_launch(int n, int m, int ld, const int32_t* sptr, const int32_t* col, const void* val,
+                         const void* u, const void* w, const void* r, void* y, double ca, double cb, double cc,
+                         double cd, const PcgScalars* Sm, cudaStream_t st) {
+    using AT = typename AccOf<XT>::type;
+    const StepCoef<AT> c = make_coef<AT>(ca, cb, cc, cd);
+    sell_mstep_kernel<VT, XT, YT><<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(
+        n, m, ld, sptr, col, static_cast<const VT*>(val), static_cast<const XT*>(u), static_cast<const XT*>(w),
+        static_cast<const XT*>(r), static_cast<YT*>(y), c, Sm);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int max_rhs() { return kMaxRhs; }
+
+cudaError_t launch_sell_mstep(int n, int m, int ld, const int32_t* slice_ptr, const int32_t* col, const void* val,
+                              int vdt, bool x_f32, bool y_f64, const void* u, const void* w, const void* r,
+                              void* y, double ca, double cb, double cc, double cd, const PcgScalars* Sm,
+                              cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (m < 1 || m > kMaxRhs) return cudaErrorInvalidValue;
+    if (!x_f32) {
+        if (vdt != NC_F64) return cudaErrorInvalidValue;
+        return mstep_launch<double, double, double>(n, m, ld, slice_ptr, col, val, u, w, r, y, ca, cb, cc, cd, Sm,
+                                                    st);
+    }
+    if (vdt == NC_F32)
+        return y_f64 ? mstep_launch<float, float, double>(n, m, ld, slice_ptr, col, val, u, w, r, y, ca, cb, cc, cd,
+                                                          Sm, st)
+                     : mstep_launch<float, float, float>(n, m, ld, slice_ptr, col, val, u, w, r, y, ca, cb, cc, cd,
+                                                         Sm, st);
+    if (vdt == NC_BF16)
+        return y_f64 ? mstep_launch<__nv_bfloat16, float, double>(n, m, ld, slice_ptr, col, val, u, w, r, y, ca, cb,
+                                                                  cc, cd, Sm, st)
+                     : mstep_launch<__nv_bfloat16, float, float>(n, m, ld, slice_ptr, col, val, u, w, r, y, ca, cb,
+                                                                 cc, cd, Sm, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_any_active(const PcgScalars* Sm, int m, cudaGraphConditionalHandle h, int use_cond, int* active,
+                              cudaStream_t st) {
+    any_active_kernel<<<1, 1, 0, st>>>(Sm, m, h, use_cond, active);
+    return cudaGetLastError();
+}
+
+}  // namespace nc
