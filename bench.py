@@ -315,6 +315,35 @@ def run_system(args, spec, rank, world, local_rank):
         else:
             S.close()
 
+    # several right-hand sides per solve: the matrix read once per step for all
+    multi = None
+    if not args.no_modes and spec["kind"] == "csr" and world == 1:
+        multi = {}
+        m_rhs = 8
+        B = torch.stack([torch.from_numpy(W.uniform_vector(n, seed=SEED_B + 100 + c)).to(dev) for c in range(m_rhs)])
+        X = torch.zeros_like(B)
+        for mode in ("f64", "f32"):
+            Sm = nc.pcg_setup(M, lo, hi, k, spec["s"], apply_dtype=mode, x0_is_zero=True)
+            if nc.pcg_get_info(Sm)["spmv_format"] != "sell":
+                Sm.close()
+                break
+            nc.pcg_solve_multi(Sm, B, X, TOL, MAXIT)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            e0.record(stream)
+            for _ in range(reps):
+                rm = nc.pcg_solve_multi(Sm, B, X, TOL, MAXIT)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3 / reps
+            multi[mode] = {"rhs_per_solve": m_rhs, "solves_per_s": round(m_rhs / t, 3), "ms_per_block": round(t * 1e3, 2),
+                           "iters_range": [min(r["iters"] for r in rm), max(r["iters"] for r in rm)],
+                           "all_converged": all(r["status"] == 0 for r in rm),
+                           "speedup_vs_one_rhs": round((m_rhs / t) / out_modes[mode]["solves_per_s"], 2)}
+            Sm.close()
+        del B, X
+
     S = main["S"]
     rec = main["rec"]
     per_launch_s, step_bytes = time_step_kernel(S, args.apply)
@@ -379,7 +408,7 @@ def run_system(args, spec, rank, world, local_rank):
         "p50_ms": round(rec["p50_ms"], 3), "p99_ms": round(rec["p99_ms"], 3), "iters": iters,
         "all_converged": rec["all_converged"], "max_relres": rec["max_relres"],
         "clocks": main["clocks"], "e2e": e2e, "gpu_launches": launches_per_solve * args.steps,
-        "roofline": roofline, "cpu_baseline": cpu, "modes": out_modes,
+        "roofline": roofline, "cpu_baseline": cpu, "modes": out_modes, "multi_rhs": multi,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -15,7 +15,6 @@ namespace nc {
 namespace {
 
 constexpr int kMaxRhs = 8;
-constexpr int kMG = 4;   // slots per load group
 
 __device__ __forceinline__ bool all_done(const PcgScalars* Sm, int m) {
     for (int c = 0; c < m; ++c)
@@ -23,14 +22,20 @@ __device__ __forceinline__ bool all_done(const PcgScalars* Sm, int m) {
     return true;
 }
 
-template <typename VT, typename XT, typename YT>
+// The column count is a template parameter: with a runtime count the guard
+// between columns keeps the compiler from issuing the next column's gathers
+// before this column's FMAs, one memory latency per column (measured: the
+// 8-column float step of the 128^3 system at 30 % of DRAM bandwidth, stalled
+// on loads).  G slots per group, so that about 16 gathers are in flight.
+template <typename VT, typename XT, typename YT, int M>
 __global__ void __launch_bounds__(kBlock)
-sell_mstep_kernel(const int n, const int m, const int ld, const int32_t* __restrict__ slice_ptr,
+sell_mstep_kernel(const int n, const int ld, const int32_t* __restrict__ slice_ptr,
                   const int32_t* __restrict__ col, const VT* __restrict__ val, const XT* __restrict__ u,
                   const XT* __restrict__ w, const XT* __restrict__ r, YT* __restrict__ y,
                   const StepCoef<typename AccOf<XT>::type> cf, const PcgScalars* __restrict__ Sm) {
     using AT = typename AccOf<XT>::type;
-    if (Sm != nullptr && all_done(Sm, m)) return;
+    constexpr int G = M >= 8 ? 2 : (M >= 4 ? 4 : 8);
+    if (Sm != nullptr && all_done(Sm, M)) return;
     const int row = blockIdx.x * kBlock + threadIdx.x;
     if (row >= n) return;
     const int s = row >> 5;
@@ -38,36 +43,36 @@ sell_mstep_kernel(const int n, const int m, const int ld, const int32_t* __restr
     const int len = (slice_ptr[s + 1] - beg) >> 5;   // warp-uniform
     const VT* vp = val + beg + (row & 31);
     const int32_t* cp = col + beg + (row & 31);
-    AT acc[kMaxRhs];
+    AT acc[M];
 #pragma unroll
-    for (int c = 0; c < kMaxRhs; ++c) acc[c] = AT(0);
-    for (int j0 = 0; j0 < len; j0 += kMG) {
-        int cj[kMG];
-        AT vj[kMG];
+    for (int c = 0; c < M; ++c) acc[c] = AT(0);
+    for (int j0 = 0; j0 < len; j0 += G) {
+        int cj[G];
+        AT vj[G];
 #pragma unroll
-        for (int t = 0; t < kMG; ++t)
+        for (int t = 0; t < G; ++t) {
+            cj[t] = row;   // padding of a short group: a valid address, weight 0
+            vj[t] = AT(0);
             if (j0 + t < len) {
                 cj[t] = ld_stream(cp + 32 * t);
                 vj[t] = (AT)ld_stream(vp + 32 * t);
             }
-#pragma unroll
-        for (int c = 0; c < kMaxRhs; ++c) {
-            if (c >= m) break;   // uniform
-            const XT* uc = u + (size_t)c * ld;
-            AT xv[kMG];
-#pragma unroll
-            for (int t = 0; t < kMG; ++t)
-                if (j0 + t < len) xv[t] = (AT)__ldg(uc + cj[t]);
-#pragma unroll
-            for (int t = 0; t < kMG; ++t)
-                if (j0 + t < len) acc[c] = fma(vj[t], xv[t], acc[c]);
         }
-        vp += 32 * kMG;
-        cp += 32 * kMG;
+        AT xv[M][G];
+#pragma unroll
+        for (int c = 0; c < M; ++c)
+#pragma unroll
+            for (int t = 0; t < G; ++t) xv[c][t] = (AT)__ldg(u + (size_t)c * ld + cj[t]);
+#pragma unroll
+        for (int c = 0; c < M; ++c)
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (j0 + t < len) acc[c] = fma(vj[t], xv[c][t], acc[c]);
+        vp += 32 * G;
+        cp += 32 * G;
     }
 #pragma unroll
-    for (int c = 0; c < kMaxRhs; ++c) {
-        if (c >= m) break;
+    for (int c = 0; c < M; ++c) {
         const size_t o = (size_t)c * ld;
         AT v = cf.cd * acc[c];
         if (cf.terms & kTermR) v = fma(cf.cc, (AT)r[o + row], v);
@@ -86,16 +91,29 @@ __global__ void any_active_kernel(const PcgScalars* __restrict__ Sm, int m, cuda
     if (use_cond) cudaGraphSetConditional(h, a ? 1u : 0u);
 }
 
+template <typename VT, typename XT, typename YT, int M>
+cudaError_t mstep_launch_m(int n, int ld, const int32_t* sptr, const int32_t* col, const void* val, const void* u,
+                           const void* w, const void* r, void* y, double ca, double cb, double cc, double cd,
+                           const PcgScalars* Sm, cudaStream_t st) {
+    using AT = typename AccOf<XT>::type;
+    const StepCoef<AT> c = make_coef<AT>(ca, cb, cc, cd);
+    sell_mstep_kernel<VT, XT, YT, M><<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(
+        n, ld, sptr, col, static_cast<const VT*>(val), static_cast<const XT*>(u), static_cast<const XT*>(w),
+        static_cast<const XT*>(r), static_cast<YT*>(y), c, Sm);
+    return cudaGetLastError();
+}
+
 template <typename VT, typename XT, typename YT>
 cudaError_t mstep_launch(int n, int m, int ld, const int32_t* sptr, const int32_t* col, const void* val,
                          const void* u, const void* w, const void* r, void* y, double ca, double cb, double cc,
                          double cd, const PcgScalars* Sm, cudaStream_t st) {
-    using AT = typename AccOf<XT>::type;
-    const StepCoef<AT> c = make_coef<AT>(ca, cb, cc, cd);
-    sell_mstep_kernel<VT, XT, YT><<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(
-        n, m, ld, sptr, col, static_cast<const VT*>(val), static_cast<const XT*>(u), static_cast<const XT*>(w),
-        static_cast<const XT*>(r), static_cast<YT*>(y), c, Sm);
-    return cudaGetLastError();
+#define NC_MSTEP(MM) \
+    case MM: return mstep_launch_m<VT, XT, YT, MM>(n, ld, sptr, col, val, u, w, r, y, ca, cb, cc, cd, Sm, st);
+    switch (m) {
+        NC_MSTEP(1) NC_MSTEP(2) NC_MSTEP(3) NC_MSTEP(4) NC_MSTEP(5) NC_MSTEP(6) NC_MSTEP(7) NC_MSTEP(8)
+    default: return cudaErrorInvalidValue;
+    }
+#undef NC_MSTEP
 }
 
 }  // namespace
