@@ -198,6 +198,16 @@ NC_API nc_status nc_matvec(nc_matrix A, const double* x_dev, double* y_dev, void
 NC_API nc_status nc_bounds_lanczos(nc_matrix A, int steps, const double* v0_dev, void* stream,
                             double* lmin, double* lmax, double* ritz_min, double* ritz_max);
 
+/* lambda_max estimate by the power method, as the paper obtains beta_0 from
+ * a few power iterations (Sec. 5.1): v = v0/||v0||, then `iters` times
+ * w = A v, lambda = (v, w), v = w/||w||; *lmax = the last Rayleigh quotient
+ * (at or below lambda_max: a caller adds a safety margin, e.g. 1.01, since
+ * an underestimate makes P_k(A) indefinite).  v0_dev: n float64 start
+ * vector (not modified).  NC_ERR_ARG for iters < 1 or v0 = 0;
+ * NC_ERR_BREAKDOWN if A v vanishes or the values are not finite.
+ * Synchronises `stream` once per iteration. */
+NC_API nc_status nc_bounds_power(nc_matrix A, int iters, const double* v0_dev, void* stream, double* lmax);
+
 /* Gershgorin upper bound max_i sum_j |a_ij| of the handle's operator. */
 NC_API nc_status nc_gershgorin(nc_matrix A, void* stream, double* bound);
 

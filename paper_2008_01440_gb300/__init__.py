@@ -35,6 +35,7 @@ from .binding import (  # noqa: F401
     nc_apply_poly_csr_noalloc,
     nc_apply_poly_noalloc_max_n,
     nc_bounds_lanczos,
+    nc_bounds_power,
     nc_gershgorin,
     nc_matrix_bsr3,
     nc_matrix_csr,

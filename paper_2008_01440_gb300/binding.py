@@ -72,6 +72,7 @@ _SIGS = {
                                           ctypes.POINTER(_vp)]),
     "nc_matvec": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "nc_bounds_lanczos": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _pd, _pd, _pd, _pd]),
+    "nc_bounds_power": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _pd]),
     "nc_gershgorin": (ctypes.c_int, [_vp, _vp, _pd]),
     "nc_matrix_destroy": (ctypes.c_int, [_vp]),
     "pcg_setup": (ctypes.c_int, [_vp, _dbl, _dbl, ctypes.c_int, _dbl, ctypes.POINTER(nc_options), _vp,
@@ -238,6 +239,15 @@ def nc_bounds_lanczos(A: Matrix, steps: int, v0, stream=None):
                                  ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(rmin), ctypes.byref(rmax)),
            "nc_bounds_lanczos")
     return lo.value, hi.value, rmin.value, rmax.value
+
+
+def nc_bounds_power(A: Matrix, iters: int, v0, stream=None) -> float:
+    """lambda_max estimate: the Rayleigh quotient after `iters` power iterations."""
+    import torch
+    lam = ctypes.c_double()
+    _check(lib.nc_bounds_power(A.handle, int(iters), _ptr(v0, torch.float64, A.n, "v0"), _stream(stream),
+                               ctypes.byref(lam)), "nc_bounds_power")
+    return lam.value
 
 
 _POLY = {"chebyshev": 0, "newton": 1}

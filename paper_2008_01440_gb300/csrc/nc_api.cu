@@ -1132,6 +1132,50 @@ nc_status nc_gershgorin(nc_matrix A, void* stream, double* bound) {
     return NC_OK;
 }
 
+nc_status nc_bounds_power(nc_matrix A, int iters, const double* v0_dev, void* stream, double* lmax) {
+    if (!A || !v0_dev || !lmax || iters < 1 || iters > 100000 || A->n < 1) return NC_ERR_ARG;
+    cudaStream_t st = as_stream(stream);
+    const int n = (int)A->n;
+    double *v = nullptr, *w = nullptr, *part = nullptr, *sc = nullptr;
+    unsigned int* cnt = nullptr;
+    nc_status s = NC_OK;
+    double lam = 0.0;
+    do {
+        if ((s = dev_alloc_n(&v, n)) || (s = dev_alloc_n(&w, n)) || (s = dev_alloc_n(&part, partials_for(A))) ||
+            (s = dev_alloc_n(&sc, 1)) || (s = dev_alloc_n(&cnt, 1)))
+            break;
+        cudaError_t e = cudaSuccess;
+        auto fetch = [&](double* out) -> cudaError_t {
+            cudaError_t ee = cudaMemcpyAsync(out, sc, sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (ee) return ee;
+            return cudaStreamSynchronize(st);
+        };
+        const Reduce Rs = make_reduce(part, cnt, nullptr, sc, FIN_STORE);
+        double h = 0.0;
+        if ((e = cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st)) ||
+            (e = launch_dot(n, v0_dev, v0_dev, Rs, nullptr, st)) || (e = fetch(&h))) {
+            g_last_cuda = e; s = NC_ERR_CUDA; break;
+        }
+        if (!(h > 0.0) || !std::isfinite(h)) { s = NC_ERR_ARG; break; }
+        if ((e = launch_div(n, v0_dev, std::sqrt(h), v, st))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
+        for (int it = 0; it < iters; ++it) {
+            double ww = 0.0;
+            // w = A v with lambda = (v, w); then v = w / ||w||
+            if ((e = op_step_f64(A, v, nullptr, nullptr, w, 0.0, 0.0, 0.0, 1.0, 2, nullptr, Rs, nullptr, st)) ||
+                (e = fetch(&lam)) || (e = launch_dot(n, w, w, Rs, nullptr, st)) || (e = fetch(&ww))) {
+                g_last_cuda = e; s = NC_ERR_CUDA; break;
+            }
+            if (!(ww > 0.0) || !std::isfinite(ww)) { s = NC_ERR_BREAKDOWN; break; }
+            if ((e = launch_div(n, w, std::sqrt(ww), v, st))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
+        }
+    } while (0);
+    dev_free(v); dev_free(w); dev_free(part); dev_free(sc); dev_free(cnt);
+    if (s != NC_OK) return s;
+    if (!std::isfinite(lam)) return NC_ERR_BREAKDOWN;
+    *lmax = lam;
+    return NC_OK;
+}
+
 nc_status nc_bounds_lanczos(nc_matrix A, int steps, const double* v0_dev, void* stream, double* lmin,
                             double* lmax, double* ritz_min, double* ritz_max) {
     if (!A || !v0_dev || !lmin || !lmax || steps < 1 || steps > 256 || A->n < 1) return NC_ERR_ARG;

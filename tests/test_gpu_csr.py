@@ -378,3 +378,28 @@ def test_autotune_layout(env):
     B = W.CSR(n, rowptr, np.concatenate(rows).astype(np.int32), np.ones(rowptr[-1]))
     S3 = nc.pcg_setup(csr_to_gpu(torch, nc, B), 0.1, 2.0, 4, 1.0, spmv_format="tune")
     assert nc.pcg_get_info(S3)["spmv_format"] == "csr"
+
+
+def test_power_method_bound_matches_oracle(env):
+    """Sec. 5.1's beta_0 estimate: the GPU power method against the oracle's
+    (same start vector and iteration count), below the exact lambda_max of the
+    2D Laplacian and approaching it."""
+    torch, nc = env
+    A, lo, hi = lap64()
+    M = csr_to_gpu(torch, nc, A)
+    v0 = W.uniform_vector(A.n, seed=4)
+    mv = O.csr_matvec(A.rowptr, A.col, A.val, A.n)
+    for iters in (1, 5, 40):
+        lam = nc.nc_bounds_power(M, iters, to_dev(torch, v0))
+        ref = O.power_method(mv, v0, iters)
+        assert abs(lam - ref) <= 1e-12 * ref
+        assert lam <= hi * (1 + 1e-12)
+    assert nc.nc_bounds_power(M, 400, to_dev(torch, v0)) >= 0.99 * hi
+    # scaled diffusion operator: below the Lanczos upper end
+    Ad = W.diffusion_3d_7pt_lognormal(20, seed=2)
+    Md = nc.nc_matrix_jacobi(csr_to_gpu(torch, nc, Ad))
+    _, hi_l, _, rmax = nc.nc_bounds_lanczos(Md, 20, to_dev(torch, W.uniform_vector(Ad.n, seed=3)))
+    lam = nc.nc_bounds_power(Md, 30, to_dev(torch, W.uniform_vector(Ad.n, seed=3)))
+    assert lam <= hi_l and lam >= 0.8 * rmax
+    with pytest.raises(nc.NcError):
+        nc.nc_bounds_power(M, 0, to_dev(torch, v0))
