@@ -355,6 +355,17 @@ def run_system(args, spec, rank, world, local_rank):
                 "frac": round(achieved / peak, 4), "traffic": read_traffic(spec["key"], args.apply),
                 "peak_source": peak_src, "kernel": kname, "bytes_per_launch": step_bytes,
                 "us_per_launch": round(per_launch_s * 1e6, 2)}
+    if args.apply == "f64" and rec["solve"] != "persistent":
+        # the same step against the float64 rate (GB300's float64 pipe is the
+        # other near-binding resource): one fma per stored entry, then
+        # cd*acc and the r and x_{k-2} terms per row
+        info = nc.pcg_get_info(S)
+        entries = spec["nnz"] * (9 if spec["kind"] == "bsr3" else 1) * (info["padding"] or 1.0)
+        flops = 2.0 * entries + 5.0 * n
+        roofline["fp64"] = {"flops_per_launch": round(flops), "achieved_TFLOPs": round(flops / per_launch_s / 1e12, 4),
+                            "peak_TFLOPs": FP64_PEAK_TFLOPS,
+                            "frac": round(flops / per_launch_s / 1e12 / FP64_PEAK_TFLOPS, 4),
+                            "peak_source": "nominal float64 rate"}
     if rec["solve"] == "persistent":
         # one launch runs the whole solve: its algorithmic bytes are the
         # (k+1) products and the vector updates of every iteration; its
