@@ -181,7 +181,9 @@ def spec_c2(args):
     grid = args.grid or GRID
     A = W.diffusion_3d_7pt_lognormal(grid, seed=SEED_A)
     rhs = [W.uniform_vector(A.n, seed=SEED_B + i) for i in range(4)]
-    return dict(kind="csr", A=A, n=A.n, nnz=A.nnz, jacobi=True, bounds="lanczos", k=args.k or 20, s=S_THETA,
+    # the configuration runs k in {10, 20, 40}; the headline line uses the
+    # fastest of them, k = 10 (all three are reported under "degrees")
+    return dict(kind="csr", A=A, n=A.n, nnz=A.nnz, jacobi=True, bounds="lanczos", k=args.k or 10, s=S_THETA,
                 rhs=rhs, rr_mixed=0,
                 bytes=lambda mode: csr_step_bytes(A.n, A.nnz, SV[mode], 8 if mode == "f64" else 4),
                 workload=f"diffusion3d-7pt lognormal {grid}^3 CSR (n={A.n}, nnz={A.nnz}), Jacobi-scaled",
@@ -344,6 +346,25 @@ def run_system(args, spec, rank, world, local_rank):
             Sm.close()
         del B, X
 
+    # the configuration's other degrees (same system, FP64 unless --apply)
+    degrees = None
+    if not args.no_modes and args.workload == "c2" and world == 1:
+        degrees = {}
+        for kk in (10, 20, 40):
+            Sk = nc.pcg_setup(M, lo, hi, kk, spec["s"], apply_dtype=args.apply, x0_is_zero=True)
+            nc.pcg_solve(Sk, bs[0], x, TOL, MAXIT)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(3):
+                rk = nc.pcg_solve(Sk, bs[i % n_rhs], x, TOL, MAXIT)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3 / 3
+            degrees[str(kk)] = {"solves_per_s": round(1.0 / t, 3), "iters": rk["iters"],
+                                "products_per_solve": rk["n_spmv"], "converged": rk["status"] == 0}
+            Sk.close()
+
     S = main["S"]
     rec = main["rec"]
     per_launch_s, step_bytes = time_step_kernel(S, args.apply)
@@ -419,7 +440,7 @@ def run_system(args, spec, rank, world, local_rank):
         "p50_ms": round(rec["p50_ms"], 3), "p99_ms": round(rec["p99_ms"], 3), "iters": iters,
         "all_converged": rec["all_converged"], "max_relres": rec["max_relres"],
         "clocks": main["clocks"], "e2e": e2e, "gpu_launches": launches_per_solve * args.steps,
-        "roofline": roofline, "cpu_baseline": cpu, "modes": out_modes, "multi_rhs": multi,
+        "roofline": roofline, "cpu_baseline": cpu, "modes": out_modes, "multi_rhs": multi, "degrees": degrees,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
