@@ -5,8 +5,12 @@
  * Preconditioners for the Conjugate Gradient method".  The library solves
  * A x = b (A symmetric positive definite, Sec. 1) by PCG whose preconditioner
  * is z = P_k(A) r, the degree-k Chebyshev polynomial of Sec. 3 applied with
- * k matrix-vector products by the three-term recurrence of Algorithm 2, with
- * the modified parameter theta' = s*theta of Sec. 4.
+ * k matrix-vector products by the three-term recurrence of Algorithm 2 (or,
+ * for k = 2^nlev - 1, by the Newton recursion of Algorithm 1, Sec. 2: the
+ * same polynomial by Theorem 3.1), with the modified parameter
+ * theta' = s*theta of Sec. 4.  Entry points: matrices and bounds, one solver
+ * per matrix (single or several right-hand sides), the batched engine for
+ * many matrix-free systems, and an allocation-free apply.
  *
  * Conventions for every entry point
  *  - Pointers named *_dev are CUDA device pointers (for instance the storage
