@@ -621,12 +621,38 @@ def run_c4(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = start_clocks(torch, dev)
     times = []
+    _, l0 = nc.pcg_batch_stats(eng)
     for _ in range(args.steps):
         t0 = time.perf_counter()
         res = one_batch()
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     clocks = clk.stop()
+    _, l1 = nc.pcg_batch_stats(eng)
+    launches = l1 - l0
+    # end to end: right-hand sides from pinned host memory, solutions back to it
+    hb = [b.cpu().pin_memory() for _, b in pairs]
+    hx = [torch.empty(b.numel(), dtype=torch.float64).pin_memory() for b in hb]
+    db = [torch.empty_like(b) for _, b in pairs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h, d in zip(hb, db):
+        d.copy_(h, non_blocking=True)
+    slots_e = []
+    for (s_, _), d in zip(pairs, db):
+        st_ = s_["st"]
+        slots_e.append(nc.pcg_batch_add(eng, st_.nx, st_.ny, st_.nz, st_.c0, st_.cx, st_.cy, st_.cz, s_["lo"],
+                                        s_["hi"], s_["k"], S_THETA, d))
+    nc.pcg_batch_run(eng, TOL, MAXIT, 0)
+    for sl, x, h in zip(slots_e, xs, hx):
+        nc.pcg_batch_collect(eng, sl, x)
+        h.copy_(x, non_blocking=True)
+    for sl in slots_e:
+        nc.pcg_batch_release(eng, sl)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    e2e_bytes = 8 * sum(b.numel() for b in hb)
+    del hb, hx, db
     t_step = statistics.median(times)
     iters = [r["iters"] for r in res]
     ok = all(r["status"] == 0 and r["true_relres"] <= 2 * TOL for r in res)
@@ -671,7 +697,10 @@ def run_c4(args, rank, world, local_rank):
             "plain_f64_one_at_a_time": {"solves_per_s": round(plain_batch_rate, 3),
                                         "sample": f"{done_pairs} of {len(pairs)} solves in {t_plain:.1f} s, "
                                                   "extrapolated by unknowns x iterations"},
-            "speedup_vs_plain_f64": round((len(pairs) / t_step) / plain_batch_rate, 2)}
+            "speedup_vs_plain_f64": round((len(pairs) / t_step) / plain_batch_rate, 2),
+            "e2e": {"value": round(len(pairs) / t_e2e, 3), "unit": "solves/s", "h2d_bytes_per_step": e2e_bytes,
+                    "d2h_bytes_per_step": e2e_bytes},
+            "gpu_launches": launches}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -786,11 +815,15 @@ def run_c5(args, rank, world, local_rank):
     budget = int(48e9 // 64)   # 48 GB of engine pools, 64 B per unknown
     torch.cuda.synchronize()
     clk = start_clocks(torch, dev)
-    span_cb = serving.serve_continuous(reqs, budget, 64, 31, TOL, MAXIT, iters_per_tick=2)
+    eng_stats = {}
+    span_cb = serving.serve_continuous(reqs, budget, 64, 31, TOL, MAXIT, iters_per_tick=2, stats=eng_stats)
     clocks = clk.stop()
     lat_cb = [r.t_done - r.arrival for r in reqs]
     ok_cb = all(r.result.get("status") == 0 and r.result.get("true_relres", 1) <= 2 * TOL for r in reqs)
     iters_cb = [r.result["iters"] for r in reqs]
+    # algorithmic bytes as for the batched workload: per request and iteration,
+    # k float32 stencil steps (16 B per unknown) and the float64 outer loop (92 B)
+    c5_bytes = sum((16 * r.k + 92) * r.n * max(r.result["iters"], 1) for r in reqs)
     plain = [clone(r) for r in reqs]
     span_pl = serving.serve_one_at_a_time_fp64(plain, TOL, MAXIT)
     lat_pl = [r.t_done - r.arrival for r in plain]
@@ -815,7 +848,13 @@ def run_c5(args, rank, world, local_rank):
                                         "p50_ms": round(1e3 * float(np.percentile(lat_pl, 50)), 2),
                                         "p99_ms": round(1e3 * float(np.percentile(lat_pl, 99)), 2),
                                         "all_converged": ok_pl},
-            "max_rel_diff_vs_plain_f64_first16": err}
+            "max_rel_diff_vs_plain_f64_first16": err,
+            "gpu_launches": eng_stats.get("launches"),
+            "roofline": {"bound": "hbm", "achieved": round(c5_bytes / span_cb / 1e9, 1), "peak": peak_hbm()[0],
+                         "unit": "GB/s", "frac": round(c5_bytes / span_cb / 1e9 / peak_hbm()[0], 4), "traffic": None,
+                         "peak_source": peak_hbm()[1],
+                         "kernel": "whole serving run (all engine kernels; algorithmic bytes / wall time, "
+                                   "arrival-limited: the GPU waits for requests)"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -322,6 +322,9 @@ NC_API nc_status pcg_batch_status(nc_batch B, int slot, int* done, nc_result* re
 NC_API nc_status pcg_batch_collect(nc_batch B, int slot, double* x_dev, void* stream);
 NC_API nc_status pcg_batch_release(nc_batch B, int slot, void* stream);
 NC_API nc_status pcg_batch_free_units(nc_batch B, int64_t* largest, int64_t* total);
+/* Engine iterations run and kernels launched (engine iterations x (kmax + 5),
+ * plus one per admission and per collect) since pcg_batch_create.  Host only. */
+NC_API nc_status pcg_batch_stats(nc_batch B, int64_t* iterations, int64_t* launches);
 NC_API nc_status pcg_batch_destroy(nc_batch B);
 NC_API const char* nc_batch_last_cuda_error(void);
 

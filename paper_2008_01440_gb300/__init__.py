@@ -54,6 +54,7 @@ from .binding import (  # noqa: F401
     pcg_batch_free_units,
     pcg_batch_release,
     pcg_batch_run,
+    pcg_batch_stats,
     pcg_batch_status,
     pcg_destroy,
     pcg_get_info,

@@ -95,6 +95,7 @@ _SIGS = {
     "pcg_batch_collect": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "pcg_batch_release": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "pcg_batch_free_units": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "pcg_batch_stats": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "pcg_batch_destroy": (ctypes.c_int, [_vp]),
     "nc_batch_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -433,6 +434,13 @@ def pcg_batch_collect(B: Batch, slot: int, x, stream=None):
 
 def pcg_batch_release(B: Batch, slot: int, stream=None):
     _check(lib.pcg_batch_release(B.handle, int(slot), _stream(stream)), "pcg_batch_release")
+
+
+def pcg_batch_stats(B: Batch):
+    """(engine iterations run, kernels launched) since creation."""
+    it, ln = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.pcg_batch_stats(B.handle, ctypes.byref(it), ctypes.byref(ln)), "pcg_batch_stats")
+    return it.value, ln.value
 
 
 def pcg_batch_free_units(B: Batch):

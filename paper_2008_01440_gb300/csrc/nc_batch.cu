@@ -351,6 +351,8 @@ struct nc_batch_s {
     BState* h_state = nullptr;    // pinned
     std::vector<int> state_upload;   // slots whose host state goes to the device at the next run
     BCtl* h_ctl = nullptr;        // pinned
+    int64_t stat_iters = 0;       // engine iterations run since creation
+    int64_t stat_launches = 0;    // kernels launched since creation
 };
 
 namespace {
@@ -658,6 +660,7 @@ nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx
     B->h_state[s] = init;
     B->state_upload.push_back(s);   // uploaded (stream-ordered) by the next pcg_batch_run
     B->h_ctl->active += 1;
+    B->stat_launches += 1;          // bk_scale
     *slot = s;
     return NC_OK;
 }
@@ -691,6 +694,9 @@ nc_status pcg_batch_run(nc_batch B, double tol, int maxit, int iter_limit, void*
         NB_CU(cudaMemcpyAsync(c, B->d_ctl, sizeof(BCtl), cudaMemcpyDeviceToHost, st));
         NB_CU(cudaMemcpyAsync(B->h_state, B->d_state, sizeof(BState) * B->cap_slots, cudaMemcpyDeviceToHost, st));
         NB_CU(cudaStreamSynchronize(st));
+        // one iteration: opq, axpy, kmax Chebyshev steps, pupd, true, cond
+        B->stat_iters += c->iters_this_call;
+        B->stat_launches += (int64_t)c->iters_this_call * (B->kmax + 5);
     }
     if (active_left) *active_left = B->h_ctl->active;
     return NC_OK;
@@ -721,6 +727,14 @@ nc_status pcg_batch_collect(nc_batch B, int slot, double* x_dev, void* stream) {
     const double scale = B->h_state[slot].bb == 0.0 ? 0.0 : B->dis[slot];
     bk_scale<<<std::min<int64_t>(4096, ((int64_t)d.n + 255) / 256), 256, 0, st>>>(d.n, d.x, scale, x_dev);
     NB_CU(cudaGetLastError());
+    B->stat_launches += 1;
+    return NC_OK;
+}
+
+nc_status pcg_batch_stats(nc_batch B, int64_t* iterations, int64_t* launches) {
+    if (!B) return NC_ERR_ARG;
+    if (iterations) *iterations = B->stat_iters;
+    if (launches) *launches = B->stat_launches;
     return NC_OK;
 }
 

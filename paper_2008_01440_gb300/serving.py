@@ -53,9 +53,11 @@ def _wait_until(t0: float, t: float):
 
 
 def serve_continuous(reqs, budget_unknowns: int, max_slots: int, kmax: int, tol: float = 1e-8,
-                     maxit: int = 5000, iters_per_tick: int = 2, stream=None):
+                     maxit: int = 5000, iters_per_tick: int = 2, stream=None, stats=None):
     """Serve `reqs` (sorted by arrival) with continuous batching; returns the
-    wall-clock span of the run.  Fills each request's x, result, t_done."""
+    wall-clock span of the run.  Fills each request's x, result, t_done (the
+    time its solution is in x).  `stats` (a dict, optional) receives the
+    engine's iteration and kernel-launch counts."""
     import torch
     eng = nc.pcg_batch_create(max_slots, budget_unknowns, kmax, stream)
     for r in reqs:
@@ -94,12 +96,21 @@ def serve_continuous(reqs, budget_unknowns: int, max_slots: int, kmax: int, tol:
                 r.result = res
                 finished.append(slot)
         if finished:
+            # the collects are enqueued: a solution counts as delivered when its copy is done
+            if stream is None:
+                torch.cuda.current_stream().synchronize()
+            elif hasattr(stream, "synchronize"):
+                stream.synchronize()
+            else:
+                torch.cuda.synchronize()
             tnow = time.perf_counter() - t0
             for slot in finished:
                 nc.pcg_batch_release(eng, slot, stream)
                 live.pop(slot).t_done = tnow
                 done += 1
     span = time.perf_counter() - t0
+    if stats is not None:
+        stats["iterations"], stats["launches"] = nc.pcg_batch_stats(eng)
     eng.close()
     return span
 
