@@ -42,6 +42,7 @@ from .operators import (  # noqa: F401
     stencil7_matvec,
     jacobi_scale_csr,
     jacobi_scale_bsr3,
+    block_jacobi_factor_bsr3,
     jacobi_scale_stencil7,
 )
 from .lanczos import lanczos_bounds, power_method  # noqa: F401

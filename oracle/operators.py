@@ -76,6 +76,29 @@ def jacobi_scale_bsr3(browptr, bcol, val, nb):
     return val * rs[:, :, None] * cs[:, None, :], dis
 
 
+def block_jacobi_factor_bsr3(browptr, bcol, val, nb):
+    """Two-level preconditioner of the paper's conclusions (Sec. 6): a first
+    level in factored form P_0 = W W^T, here block Jacobi with
+    W = blockdiag(L_i^{-T}), A_ii = L_i L_i^T the Cholesky factor of each 3x3
+    diagonal block, and the Newton-Chebyshev polynomial applied to W^T A W.
+
+    Returns (scaled values of W^T A W in the same block pattern, W blocks
+    (nb, 3, 3), L blocks (nb, 3, 3)); the scaled system is
+    (W^T A W) y = W^T b with x = W y.  numpy's Cholesky and triangular
+    inverse per block; raises if a diagonal block is not positive definite.
+    """
+    brows = np.repeat(np.arange(nb), np.diff(browptr))
+    on_diag = brows == bcol
+    if np.count_nonzero(on_diag) != nb:
+        raise ValueError("every block row needs its diagonal block")
+    D = np.empty((nb, 3, 3))
+    D[brows[on_diag]] = val[on_diag]
+    L = np.linalg.cholesky(D)                      # raises LinAlgError if not SPD
+    W = np.transpose(np.linalg.inv(L), (0, 2, 1))  # L^{-T}
+    scaled = np.einsum("bki,bkl,blj->bij", W[brows], val, W[bcol])
+    return scaled, W, L
+
+
 def jacobi_scale_stencil7(c0, cx, cy, cz):
     """Constant diagonal c0: the scaled stencil is (1, cx/c0, cy/c0, cz/c0)."""
     if c0 <= 0.0:
