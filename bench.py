@@ -346,6 +346,29 @@ def run_system(args, spec, rank, world, local_rank):
             Sm.close()
         del B, X
 
+    # two-level variant (Sec. 6): block-Jacobi first level W = blockdiag(L_i^{-T})
+    two_level = None
+    if not args.no_modes and spec["kind"] == "bsr3" and world == 1:
+        two_level = {}
+        Mb = nc.nc_matrix_block_jacobi(M0)
+        v0 = torch.from_numpy(W.uniform_vector(n, seed=SEED_V0)).to(dev)
+        lo_b, hi_b, _, _ = nc.nc_bounds_lanczos(Mb, 20, v0)
+        for mode in ("f64", "f32"):
+            Sb = nc.pcg_setup(Mb, lo_b, hi_b, k, spec["s"], apply_dtype=mode, x0_is_zero=True,
+                              rr_period=spec["rr_mixed"] if mode != "f64" else 0)
+            nc.pcg_solve(Sb, bs[0], x, TOL, MAXIT)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rb = nc.pcg_solve(Sb, bs[0], x, TOL, MAXIT)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            two_level[mode] = {"solves_per_s": round(1e3 / e0.elapsed_time(e1), 3), "iters": rb["iters"],
+                               "true_relres": rb["true_relres"], "converged": rb["status"] == 0,
+                               "bounds": [lo_b, hi_b]}
+            Sb.close()
+        del Mb
+
     # the configuration's other degrees (same system, FP64 unless --apply)
     degrees = None
     if not args.no_modes and args.workload == "c2" and world == 1:
@@ -441,6 +464,7 @@ def run_system(args, spec, rank, world, local_rank):
         "all_converged": rec["all_converged"], "max_relres": rec["max_relres"],
         "clocks": main["clocks"], "e2e": e2e, "gpu_launches": launches_per_solve * args.steps,
         "roofline": roofline, "cpu_baseline": cpu, "modes": out_modes, "multi_rhs": multi, "degrees": degrees,
+        "two_level_block_jacobi": two_level,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

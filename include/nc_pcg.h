@@ -187,6 +187,19 @@ NC_API nc_status nc_matrix_stencil7(int nx, int ny, int nz, double c0, double cx
  * already a scaled handle. */
 NC_API nc_status nc_matrix_jacobi(nc_matrix A, void* stream, nc_matrix* out);
 
+/* Two-level variant (Sec. 6, conclusions: a first-level preconditioner in
+ * factored form P_0 = W W^T, the Newton-Chebyshev polynomial applied to
+ * W^T A W), with block Jacobi as the first level of a 3x3-block matrix:
+ * W = blockdiag(L_i^{-T}), A_ii = L_i L_i^T the Cholesky factor of each
+ * diagonal block, so W W^T = blockdiag(A_ii^{-1}) and W^T A W has identity
+ * diagonal blocks.  Returns a new owning handle of W^T A W (same block
+ * pattern, the parent's index arrays borrowed); a solver built on it takes
+ * the original b and returns the original x (b_s = W^T b, x = W y), and the
+ * bounds passed to pcg_setup refer to W^T A W.  NC_ERR_ARG for a handle that
+ * is not an unscaled BSR3 matrix or has a block row without a positive
+ * definite diagonal block. */
+NC_API nc_status nc_matrix_block_jacobi(nc_matrix A, void* stream, nc_matrix* out);
+
 /* y_dev = A x_dev for the handle's operator.  x_dev, y_dev: n float64,
  * distinct buffers. */
 NC_API nc_status nc_matvec(nc_matrix A, const double* x_dev, double* y_dev, void* stream);

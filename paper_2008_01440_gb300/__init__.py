@@ -40,6 +40,7 @@ from .binding import (  # noqa: F401
     nc_matrix_bsr3,
     nc_matrix_csr,
     nc_matrix_destroy,
+    nc_matrix_block_jacobi,
     nc_matrix_jacobi,
     nc_matrix_stencil7,
     nc_matvec,

@@ -67,6 +67,7 @@ _SIGS = {
     "nc_last_cuda_error": (ctypes.c_char_p, []),
     "nc_matrix_csr": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "nc_matrix_jacobi": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "nc_matrix_block_jacobi": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
     "nc_matrix_bsr3": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "nc_matrix_stencil7": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dbl, _dbl, _dbl, _dbl,
                                           ctypes.POINTER(_vp)]),
@@ -217,6 +218,14 @@ def nc_matrix_stencil7(nx: int, ny: int, nz: int, c0: float, cx: float, cy: floa
 def nc_matrix_jacobi(A: Matrix, stream=None) -> Matrix:
     h = _vp()
     _check(lib.nc_matrix_jacobi(A.handle, _stream(stream), ctypes.byref(h)), "nc_matrix_jacobi")
+    return Matrix(h.value, A.n, A.keep, parent=A)
+
+
+def nc_matrix_block_jacobi(A: Matrix, stream=None) -> Matrix:
+    """W^T A W with W = blockdiag(L_i^{-T}) (block-Jacobi first level) for a
+    3x3-block matrix; solvers on it take the original b and return the original x."""
+    h = _vp()
+    _check(lib.nc_matrix_block_jacobi(A.handle, _stream(stream), ctypes.byref(h)), "nc_matrix_block_jacobi")
     return Matrix(h.value, A.n, A.keep, parent=A)
 
 

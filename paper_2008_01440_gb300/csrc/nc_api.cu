@@ -31,6 +31,8 @@ struct nc_matrix_s {
     double* dis = nullptr;          // d^{-1/2} of the scaling, owned (CSR)
     bool scaled = false;            // built by nc_matrix_jacobi
     double dis_scalar = 1.0;        // constant d^{-1/2} (stencil)
+    double* wblk = nullptr;         // two-level first level (BSR3): W_i = L_i^{-T}, owned
+    double* lblk = nullptr;         // and L_i (A_ii = L_i L_i^T), owned
     StencilGeom geom{0, 0, 0};      // stencil grid
     double c4[4] = {0, 0, 0, 0};    // stencil coefficients c0, cx, cy, cz
 };
@@ -467,6 +469,20 @@ nc_status build_graph(nc_solver S) {
     return st;
 }
 
+// Into the scaled system: bs = W^T b, xs = W^{-1} x (or 0) -- a diagonal W
+// (Jacobi, or none) or the block W of the two-level variant.
+cudaError_t mat_copy_in(nc_matrix A, const double* b, const double* x, int zero, double* bs, double* xs,
+                        cudaStream_t st) {
+    if (A->wblk) return launch_bsr3_block_copy_in((int)(A->n / 3), b, x, A->wblk, A->lblk, zero, bs, xs, st);
+    return launch_copy_in((int)A->n, b, x, A->dis, A->dis_scalar, zero, bs, xs, st);
+}
+
+// Back to the original system: x = W ys (0 when b = 0)
+cudaError_t mat_copy_out(nc_matrix A, const double* ys, const PcgScalars* S, double* x, cudaStream_t st) {
+    if (A->wblk) return launch_bsr3_block_copy_out((int)(A->n / 3), ys, A->wblk, S, x, st);
+    return launch_copy_out((int)A->n, ys, A->dis, A->dis_scalar, S, x, st);
+}
+
 nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol, int maxit,
                     cudaStream_t st, nc_result* res) {
     const int n = (int)S->n;
@@ -481,7 +497,7 @@ nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
     // synchronised the stream, so it is free
     *S->h_io = init;
     NC_CU(cudaMemcpyAsync(S->S, S->h_io, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
-    NC_CU(launch_copy_in(n, b_dev, x_dev, S->A->dis, S->A->dis_scalar, S->opt.x0_is_zero, S->b, S->x, st));
+    NC_CU(mat_copy_in(S->A, b_dev, x_dev, S->opt.x0_is_zero, S->b, S->x, st));
     if (S->persistent) {
         NC_CU(launch_cluster_pcg(S->plan, n, S->k, S->opt.x0_is_zero, maxit, tol * tol, S->shift, S->op64.ptr,
                                  S->op64.col, static_cast<const double*>(S->op64.val), S->pcoef, S->b, S->x, S->S,
@@ -508,7 +524,7 @@ nc_status run_solve(nc_solver S, const double* b_dev, double* x_dev, double tol,
     const Reduce none = make_reduce(S->partials, S->counter, S->S, nullptr, FIN_NONE);
     NC_CU(op64_apply(S, S->x, S->b, S->q, 1.0, -1.0, 0, none, nullptr, st));
     NC_CU(launch_dot(n, S->q, S->q, make_reduce(S->partials, S->counter, S->S, nullptr, FIN_TRUE), nullptr, st));
-    NC_CU(launch_copy_out(n, S->x, S->A->dis, S->A->dis_scalar, S->S, x_dev, st));
+    NC_CU(mat_copy_out(S->A, S->x, S->S, x_dev, st));
     NC_CU(cudaMemcpyAsync(S->h_io, S->S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
     NC_CU(cudaStreamSynchronize(st));
     const PcgScalars& o = *S->h_io;
@@ -1094,6 +1110,50 @@ nc_status nc_matrix_jacobi(nc_matrix A, void* stream, nc_matrix* out) {
     return NC_OK;
 }
 
+nc_status nc_matrix_block_jacobi(nc_matrix A, void* stream, nc_matrix* out) {
+    if (!A || !out) return NC_ERR_ARG;
+    *out = nullptr;
+    if (A->scaled || A->kind != MAT_BSR3) return NC_ERR_ARG;
+    cudaStream_t st = as_stream(stream);
+    const int nb = (int)(A->n / 3);
+    nc_matrix B = new (std::nothrow) nc_matrix_s(*A);
+    if (!B) return NC_ERR_OOM;
+    B->owned_val = nullptr;
+    B->dis = nullptr;
+    B->wblk = B->lblk = nullptr;
+    int* bad = nullptr;
+    int h_bad = 0;
+    nc_status s = NC_OK;
+    do {
+        if ((s = dev_alloc_n(&B->owned_val, 9 * (A->nnz > 0 ? A->nnz : 1))) || (s = dev_alloc_n(&B->wblk, 9 * (int64_t)(nb > 0 ? nb : 1))) ||
+            (s = dev_alloc_n(&B->lblk, 9 * (int64_t)(nb > 0 ? nb : 1))) || (s = dev_alloc_n(&bad, 1)))
+            break;
+        cudaError_t e;
+        if ((e = cudaMemsetAsync(bad, 0, sizeof(int), st)) ||
+            (e = launch_bsr3_block_factor(nb, A->rowptr, A->col, A->val, B->wblk, B->lblk, bad, st)) ||
+            (e = launch_bsr3_block_scale(nb, A->rowptr, A->col, A->val, B->wblk, B->owned_val, st)) ||
+            (e = cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st))) {
+            g_last_cuda = e;
+            s = NC_ERR_CUDA;
+            break;
+        }
+        if (h_bad) s = NC_ERR_ARG;
+    } while (0);
+    dev_free(bad);
+    if (s != NC_OK) {
+        dev_free(B->owned_val);
+        dev_free(B->wblk);
+        dev_free(B->lblk);
+        delete B;
+        return s;
+    }
+    B->val = B->owned_val;
+    B->scaled = true;
+    *out = B;
+    return NC_OK;
+}
+
 nc_status nc_matvec(nc_matrix A, const double* x_dev, double* y_dev, void* stream) {
     if (!A || (A->n > 0 && (!x_dev || !y_dev)) || x_dev == y_dev) return NC_ERR_ARG;
     const Reduce none = make_reduce(nullptr, nullptr, nullptr, nullptr, FIN_NONE);
@@ -1262,6 +1322,8 @@ nc_status nc_matrix_destroy(nc_matrix A) {
     if (!A) return NC_ERR_ARG;
     dev_free(A->owned_val);
     dev_free(A->dis);
+    dev_free(A->wblk);
+    dev_free(A->lblk);
     delete A;
     return NC_OK;
 }
@@ -1418,7 +1480,7 @@ nc_status pcg_solve_multi(nc_solver S, int m, const double* B_dev, double* X_dev
     }
     NC_CU(cudaMemcpyAsync(S->mS, S->mh, sizeof(PcgScalars) * m, cudaMemcpyHostToDevice, st));
     for (int c = 0; c < m; ++c)
-        NC_CU(launch_copy_in(n, B_dev + c * cn, X_dev + c * cn, S->A->dis, S->A->dis_scalar, S->opt.x0_is_zero,
+        NC_CU(mat_copy_in(S->A, B_dev + c * cn, X_dev + c * cn, S->opt.x0_is_zero,
                              S->mb + c * cn, S->mx + c * cn, st));
     bool graph = S->opt.use_graph && !S->mgraph_failed;
     if (graph && (S->mexec == nullptr || S->mexec_m != m) && mbuild_graph(S, m) != NC_OK) {
@@ -1443,7 +1505,7 @@ nc_status pcg_solve_multi(nc_solver S, int m, const double* B_dev, double* X_dev
         NC_CU(op64_apply(S, S->mx + c * cn, S->mb + c * cn, S->mq + c * cn, 1.0, -1.0, 0, none, nullptr, st));
         NC_CU(launch_dot(n, S->mq + c * cn, S->mq + c * cn,
                          make_reduce(S->partials, S->counter, S->mS + c, nullptr, FIN_TRUE), nullptr, st));
-        NC_CU(launch_copy_out(n, S->mx + c * cn, S->A->dis, S->A->dis_scalar, S->mS + c, X_dev + c * cn, st));
+        NC_CU(mat_copy_out(S->A, S->mx + c * cn, S->mS + c, X_dev + c * cn, st));
     }
     NC_CU(cudaMemcpyAsync(S->mh, S->mS, sizeof(PcgScalars) * m, cudaMemcpyDeviceToHost, st));
     NC_CU(cudaStreamSynchronize(st));

@@ -171,6 +171,99 @@ __global__ void bsr3_scale_kernel(int nb, const int32_t* __restrict__ browptr, c
     }
 }
 
+// First level of the two-level variant (Sec. 6, conclusions): P_0 = W W^T
+// with W = blockdiag(L_i^{-T}), A_ii = L_i L_i^T.  One thread per block row:
+// the 3x3 Cholesky factor of the diagonal block and its triangular inverse
+// (written out from the definitions; sqrt and division are CUDA's).  W_i and
+// L_i are stored row-major; *bad is set when a block is not positive
+// definite or has no diagonal block.
+__global__ void bsr3_block_factor_kernel(int nb, const int32_t* __restrict__ browptr,
+                                         const int32_t* __restrict__ bcol, const double* __restrict__ val,
+                                         double* __restrict__ wblk, double* __restrict__ lblk,
+                                         int* __restrict__ bad) {
+    const int br = blockIdx.x * blockDim.x + threadIdx.x;
+    if (br >= nb) return;
+    const double* d = nullptr;
+    for (int p = browptr[br]; p < browptr[br + 1]; ++p)
+        if (bcol[p] == br) d = val + (long long)p * 9;
+    double* W = wblk + (long long)br * 9;
+    double* L = lblk + (long long)br * 9;
+    for (int e = 0; e < 9; ++e) W[e] = L[e] = 0.0;
+    if (d == nullptr) { atomicOr(bad, 1); return; }
+    const double p0 = d[0];
+    if (!(p0 > 0.0)) { atomicOr(bad, 1); return; }
+    const double l00 = sqrt(p0);
+    const double l10 = d[3] / l00, l20 = d[6] / l00;
+    const double p1 = d[4] - l10 * l10;
+    if (!(p1 > 0.0)) { atomicOr(bad, 1); return; }
+    const double l11 = sqrt(p1);
+    const double l21 = (d[7] - l20 * l10) / l11;
+    const double p2 = d[8] - l20 * l20 - l21 * l21;
+    if (!(p2 > 0.0) || !isfinite(p2)) { atomicOr(bad, 1); return; }
+    const double l22 = sqrt(p2);
+    // M = L^{-1} (lower): M L = I
+    const double m00 = 1.0 / l00, m11 = 1.0 / l11, m22 = 1.0 / l22;
+    const double m10 = -l10 * m00 / l11;
+    const double m21 = -l21 * m11 / l22;
+    const double m20 = -(l20 * m00 + l21 * m10) / l22;
+    // W = M^T (upper)
+    W[0] = m00; W[1] = m10; W[2] = m20;
+    W[4] = m11; W[5] = m21;
+    W[8] = m22;
+    L[0] = l00;
+    L[3] = l10; L[4] = l11;
+    L[6] = l20; L[7] = l21; L[8] = l22;
+}
+
+// out_p = W_i^T A_p W_j for block p in row i, column j
+__global__ void bsr3_block_scale_kernel(int nb, const int32_t* __restrict__ browptr,
+                                        const int32_t* __restrict__ bcol, const double* __restrict__ val,
+                                        const double* __restrict__ wblk, double* __restrict__ out) {
+    const int br = blockIdx.x * blockDim.x + threadIdx.x;
+    if (br >= nb) return;
+    const double* Wi = wblk + (long long)br * 9;
+    for (int p = browptr[br]; p < browptr[br + 1]; ++p) {
+        const double* Wj = wblk + (long long)bcol[p] * 9;
+        const double* a = val + (long long)p * 9;
+        double t[9];   // A_p W_j
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                t[3 * r + c] = a[3 * r] * Wj[c] + a[3 * r + 1] * Wj[3 + c] + a[3 * r + 2] * Wj[6 + c];
+        double* o = out + (long long)p * 9;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                o[3 * r + c] = Wi[r] * t[c] + Wi[3 + r] * t[3 + c] + Wi[6 + r] * t[6 + c];
+    }
+}
+
+// Transforms between the original and the scaled system, per block row:
+// copy in bs = W^T b, xs = L^T x (= W^{-1} x, or 0); copy out x = W y
+// (0 when b = 0).
+__global__ void bsr3_block_copy_in_kernel(int nb, const double* __restrict__ b, const double* __restrict__ x,
+                                          const double* __restrict__ wblk, const double* __restrict__ lblk,
+                                          int zero, double* __restrict__ bs, double* __restrict__ xs) {
+    for (int br = blockIdx.x * blockDim.x + threadIdx.x; br < nb; br += gridDim.x * blockDim.x) {
+        const double* W = wblk + (long long)br * 9;
+        const double* L = lblk + (long long)br * 9;
+        const long long o = 3LL * br;
+        for (int t = 0; t < 3; ++t) {
+            bs[o + t] = W[t] * b[o] + W[3 + t] * b[o + 1] + W[6 + t] * b[o + 2];
+            xs[o + t] = zero ? 0.0 : L[t] * x[o] + L[3 + t] * x[o + 1] + L[6 + t] * x[o + 2];
+        }
+    }
+}
+
+__global__ void bsr3_block_copy_out_kernel(int nb, const double* __restrict__ ys, const double* __restrict__ wblk,
+                                           const PcgScalars* __restrict__ S, double* __restrict__ x) {
+    const bool zero = S->bb == 0.0;
+    for (int br = blockIdx.x * blockDim.x + threadIdx.x; br < nb; br += gridDim.x * blockDim.x) {
+        const double* W = wblk + (long long)br * 9;
+        const long long o = 3LL * br;
+        for (int t = 0; t < 3; ++t)
+            x[o + t] = zero ? 0.0 : W[3 * t] * ys[o] + W[3 * t + 1] * ys[o + 1] + W[3 * t + 2] * ys[o + 2];
+    }
+}
+
 __global__ void bsr3_gershgorin_kernel(int nb, const int32_t* __restrict__ browptr, const double* __restrict__ val,
                                        unsigned long long* __restrict__ out_bits) {
     const int br = blockIdx.x * blockDim.x + threadIdx.x;
@@ -277,6 +370,34 @@ cudaError_t launch_bsr3_scale(int nb, const int32_t* browptr, const int32_t* bco
                               const double* dis, double* out, cudaStream_t st) {
     if (nb <= 0) return cudaSuccess;
     bsr3_scale_kernel<<<(nb + 255) / 256, 256, 0, st>>>(nb, browptr, bcol, val, dis, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bsr3_block_factor(int nb, const int32_t* browptr, const int32_t* bcol, const double* val,
+                                     double* wblk, double* lblk, int* bad, cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    bsr3_block_factor_kernel<<<(nb + 255) / 256, 256, 0, st>>>(nb, browptr, bcol, val, wblk, lblk, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bsr3_block_scale(int nb, const int32_t* browptr, const int32_t* bcol, const double* val,
+                                    const double* wblk, double* out, cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    bsr3_block_scale_kernel<<<(nb + 255) / 256, 256, 0, st>>>(nb, browptr, bcol, val, wblk, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bsr3_block_copy_in(int nb, const double* b, const double* x, const double* wblk,
+                                      const double* lblk, int zero, double* bs, double* xs, cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    bsr3_block_copy_in_kernel<<<vec_grid(nb), 256, 0, st>>>(nb, b, x, wblk, lblk, zero, bs, xs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bsr3_block_copy_out(int nb, const double* ys, const double* wblk, const PcgScalars* S, double* x,
+                                       cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    bsr3_block_copy_out_kernel<<<vec_grid(nb), 256, 0, st>>>(nb, ys, wblk, S, x);
     return cudaGetLastError();
 }
 

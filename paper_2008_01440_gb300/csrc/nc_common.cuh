@@ -209,6 +209,19 @@ cudaError_t launch_bsr3_diag(int nb, const int32_t* browptr, const int32_t* bcol
                              int* bad, cudaStream_t st);
 cudaError_t launch_bsr3_scale(int nb, const int32_t* browptr, const int32_t* bcol, const double* val,
                               const double* dis, double* out, cudaStream_t st);
+// Two-level variant, first level block Jacobi: W_i = L_i^{-T}, L_i the
+// Cholesky factor of diagonal block i (row-major 3x3 each); *bad set when a
+// block is missing or not positive definite
+cudaError_t launch_bsr3_block_factor(int nb, const int32_t* browptr, const int32_t* bcol, const double* val,
+                                     double* wblk, double* lblk, int* bad, cudaStream_t st);
+// out_p = W_i^T A_p W_j
+cudaError_t launch_bsr3_block_scale(int nb, const int32_t* browptr, const int32_t* bcol, const double* val,
+                                    const double* wblk, double* out, cudaStream_t st);
+// bs = W^T b, xs = L^T x (or 0); and x = W ys (0 when S->bb == 0)
+cudaError_t launch_bsr3_block_copy_in(int nb, const double* b, const double* x, const double* wblk,
+                                      const double* lblk, int zero, double* bs, double* xs, cudaStream_t st);
+cudaError_t launch_bsr3_block_copy_out(int nb, const double* ys, const double* wblk, const PcgScalars* S, double* x,
+                                       cudaStream_t st);
 cudaError_t launch_bsr3_gershgorin(int nb, const int32_t* browptr, const double* val, unsigned long long* out_bits,
                                    cudaStream_t st);
 cudaError_t launch_bsell3_lengths(int nb, const int32_t* browptr, int32_t* slice_len, cudaStream_t st);
