@@ -686,6 +686,28 @@ def run_c4(args, rank, world, local_rank):
     tot_bytes = sum((16 * p[0]["k"] + 92) * p[0]["st"].n * max(r["iters"], 1) for p, r in zip(pairs, res))
     peak, src = peak_hbm()
     achieved = tot_bytes / t_step / 1e9
+    # the same batch with the float64 apply (NC_BATCH_F64_APPLY): batching at equal precision
+    eng.close()
+    eng64 = nc.pcg_batch_create(len(pairs), units, 32, f64_apply=True)
+    f64_times, res64 = [], None
+    for rep_ in range(2):
+        slots64 = [nc.pcg_batch_add(eng64, p_["st"].nx, p_["st"].ny, p_["st"].nz, p_["st"].c0, p_["st"].cx,
+                                    p_["st"].cy, p_["st"].cz, p_["lo"], p_["hi"], p_["k"], S_THETA, b_)
+                   for p_, b_ in pairs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nc.pcg_batch_run(eng64, TOL, MAXIT, 0)
+        torch.cuda.synchronize()
+        f64_times.append(time.perf_counter() - t0)
+        res64 = [nc.pcg_batch_status(eng64, sl)[1] for sl in slots64]
+        for sl in slots64:
+            nc.pcg_batch_release(eng64, sl)
+    eng64.close()
+    t64 = f64_times[-1]
+    f64_apply = {"solves_per_s_engine_run": round(len(pairs) / t64, 3),
+                 "iters_range": [min(r["iters"] for r in res64), max(r["iters"] for r in res64)],
+                 "all_converged": all(r["status"] == 0 for r in res64)}
+
     # plain FP64 one system at a time (same right-hand sides), bounded sample
     t_budget = 90.0
     t0 = time.perf_counter()
@@ -724,7 +746,7 @@ def run_c4(args, rank, world, local_rank):
             "speedup_vs_plain_f64": round((len(pairs) / t_step) / plain_batch_rate, 2),
             "e2e": {"value": round(len(pairs) / t_e2e, 3), "unit": "solves/s", "h2d_bytes_per_step": e2e_bytes,
                     "d2h_bytes_per_step": e2e_bytes},
-            "gpu_launches": launches}
+            "gpu_launches": launches, "f64_apply": f64_apply}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -848,6 +870,10 @@ def run_c5(args, rank, world, local_rank):
     # algorithmic bytes as for the batched workload: per request and iteration,
     # k float32 stencil steps (16 B per unknown) and the float64 outer loop (92 B)
     c5_bytes = sum((16 * r.k + 92) * r.n * max(r.result["iters"], 1) for r in reqs)
+    reqs64 = [clone(r) for r in reqs]
+    span_64 = serving.serve_continuous(reqs64, budget, 64, 31, TOL, MAXIT, iters_per_tick=2, f64_apply=True)
+    lat_64 = [r.t_done - r.arrival for r in reqs64]
+    ok_64 = all(r.result.get("status") == 0 and r.result.get("true_relres", 1) <= 2 * TOL for r in reqs64)
     plain = [clone(r) for r in reqs]
     span_pl = serving.serve_one_at_a_time_fp64(plain, TOL, MAXIT)
     lat_pl = [r.t_done - r.arrival for r in plain]
@@ -873,6 +899,9 @@ def run_c5(args, rank, world, local_rank):
                                         "p99_ms": round(1e3 * float(np.percentile(lat_pl, 99)), 2),
                                         "all_converged": ok_pl},
             "max_rel_diff_vs_plain_f64_first16": err,
+            "f64_apply": {"solves_per_s": round(len(reqs64) / span_64, 3),
+                          "p50_ms": round(1e3 * float(np.percentile(lat_64, 50)), 2),
+                          "p99_ms": round(1e3 * float(np.percentile(lat_64, 99)), 2), "all_converged": ok_64},
             "gpu_launches": eng_stats.get("launches"),
             "roofline": {"bound": "hbm", "achieved": round(c5_bytes / span_cb / 1e9, 1), "peak": peak_hbm()[0],
                          "unit": "GB/s", "frac": round(c5_bytes / span_cb / 1e9 / peak_hbm()[0], 4), "traffic": None,

@@ -325,6 +325,10 @@ NC_API nc_status pcg_destroy(nc_solver S);
  *   enqueued on `stream` still read it first).
  * pcg_batch_free_units: largest contiguous and total free pooled unknowns. */
 #define NC_BATCH_HOST_LOOP 1
+/* flags: NC_BATCH_F64_APPLY applies P_k in float64 (3 float64 work vectors
+ * per unknown instead of 4 float32; 72 instead of 64 bytes per pooled
+ * unknown) rather than the default float32 apply with float64 outer CG. */
+#define NC_BATCH_F64_APPLY 2
 NC_API nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, int flags, void* stream,
                                   nc_batch* out);
 NC_API nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx, double cy, double cz,

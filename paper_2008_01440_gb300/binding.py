@@ -395,11 +395,13 @@ class Batch:
 
 
 NC_BATCH_HOST_LOOP = 1
+NC_BATCH_F64_APPLY = 2
 
 
-def pcg_batch_create(max_slots: int, max_unknowns: int, kmax: int, stream=None, host_loop: bool = False) -> Batch:
+def pcg_batch_create(max_slots: int, max_unknowns: int, kmax: int, stream=None, host_loop: bool = False,
+                     f64_apply: bool = False) -> Batch:
     h = _vp()
-    flags = NC_BATCH_HOST_LOOP if host_loop else 0
+    flags = (NC_BATCH_HOST_LOOP if host_loop else 0) | (NC_BATCH_F64_APPLY if f64_apply else 0)
     _check(lib.pcg_batch_create(int(max_slots), int(max_unknowns), int(kmax), flags, _stream(stream),
                                 ctypes.byref(h)), "pcg_batch_create")
     return Batch(h.value)

@@ -55,7 +55,8 @@ struct BDesc {
     int tile0, tile1, vch0, vch1;
     double c0, cx, cy, cz;
     double *b, *x, *r, *z, *p, *q;
-    float *t0, *t1, *t2, *r32;
+    float *t0, *t1, *t2, *r32;      // float32 apply (NC_BATCH_F64_APPLY unset)
+    double *dt0, *dt1, *dt2;        // float64 apply: the Chebyshev vectors, r read directly
 };
 
 struct BState {
@@ -67,6 +68,7 @@ struct BState {
 struct BCoef {
     float e0, ex, ey, ez, cb, cc;
     int terms, pad;
+    double e0d, exd, eyd, ezd, cbd, ccd;   // the same in float64 (float64 apply)
 };
 
 struct BTile {
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(256) bk_axpy(const BDesc* __restrict__ D, BSta
                 d.x[i] = fma(a, d.p[i], d.x[i]);
                 const double ri = fma(-a, d.q[i], d.r[i]);
                 d.r[i] = ri;
-                d.r32[i] = (float)ri;
+                if (d.r32) d.r32[i] = (float)ri;
                 acc = fma(ri, ri, acc);
             }
         } else {
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(256) bk_axpy(const BDesc* __restrict__ D, BSta
                 const double bi = d.b[i];
                 d.x[i] = 0.0;
                 d.r[i] = bi;
-                d.r32[i] = (float)bi;
+                if (d.r32) d.r32[i] = (float)bi;
                 acc = fma(bi, bi, acc);
             }
         }
@@ -223,6 +225,9 @@ __global__ void __launch_bounds__(256) bk_axpy(const BDesc* __restrict__ D, BSta
     }
 }
 
+// F64: the float64 apply (NC_BATCH_F64_APPLY), a separate instantiation so
+// that the float32 kernel keeps its register count
+template <bool F64>
 __global__ void __launch_bounds__(256) bk_cheb(const BDesc* __restrict__ D, BState* S, const BTile* __restrict__ T,
                                                const BCoef* __restrict__ C, BCtl* ctl, double* partials, int j,
                                                const int* __restrict__ ntile_step) {
@@ -238,6 +243,29 @@ __global__ void __launch_bounds__(256) bk_cheb(const BDesc* __restrict__ D, BSta
         const BDesc& d = D[tl.pair];
         if (j > d.k) continue;
         const BCoef bc = C[d.coef0 + j - 1];
+        const int k0 = tl.bz * kZC, k1 = min(k0 + kZC, d.nz);
+        if constexpr (F64) {
+            // float64 apply
+            StencilCoef<double> c;
+            c.e0 = bc.e0d;
+            c.ex = bc.exd;
+            c.ey = bc.eyd;
+            c.ez = bc.ezd;
+            c.cb = bc.cbd;
+            c.cc = bc.ccd;
+            c.terms = bc.terms;
+            double* tb[3] = {d.dt0, d.dt1, d.dt2};
+            const double* u = (j == 1) ? d.r : tb[(j - 1) % 3];
+            const double* w = (j >= 3) ? tb[(j - 2) % 3] : nullptr;
+            if (j == d.k) {
+                const double dv = stencil_flat<double, double, 1>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r, d.z,
+                                                                  c, d.r, tid);
+                reduce_slot(dv, partials, t, d.tile0, d.tile1 - d.tile0, st, ctl, BF_RZ);
+            } else {
+                stencil_flat<double, double, 0>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r, tb[j % 3], c, nullptr,
+                                                tid);
+            }
+        } else {
         StencilCoef<float> c;
         c.e0 = bc.e0;
         c.ex = bc.ex;
@@ -249,13 +277,13 @@ __global__ void __launch_bounds__(256) bk_cheb(const BDesc* __restrict__ D, BSta
         float* tb[3] = {d.t0, d.t1, d.t2};
         const float* u = (j == 1) ? d.r32 : tb[(j - 1) % 3];
         const float* w = (j >= 3) ? tb[(j - 2) % 3] : nullptr;
-        const int k0 = tl.bz * kZC, k1 = min(k0 + kZC, d.nz);
         if (j == d.k) {
             const double dv = stencil_flat<float, double, 1>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r32, d.z, c,
                                                              d.r, tid);
             reduce_slot(dv, partials, t, d.tile0, d.tile1 - d.tile0, st, ctl, BF_RZ);
         } else {
             stencil_flat<float, float, 0>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r32, tb[j % 3], c, nullptr, tid);
+        }
         }
     }
 }
@@ -432,9 +460,14 @@ void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, c
     const dim3 tb(kTX, kTY);
     bk_opq<<<kBatchGrid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
     bk_axpy<<<kBatchGrid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
-    for (int j = 1; j <= B->kmax; ++j)
-        bk_cheb<<<kBatchGrid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_coef, B->d_ctl, B->d_partials, j,
-                                           B->d_ntile_step);
+    for (int j = 1; j <= B->kmax; ++j) {
+        if (B->flags & NC_BATCH_F64_APPLY)
+            bk_cheb<true><<<kBatchGrid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_coef, B->d_ctl,
+                                                     B->d_partials, j, B->d_ntile_step);
+        else
+            bk_cheb<false><<<kBatchGrid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_coef, B->d_ctl,
+                                                      B->d_partials, j, B->d_ntile_step);
+    }
     bk_pupd<<<kBatchGrid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
     bk_true<<<kBatchGrid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
     bk_cond<<<1, 1, 0, st>>>(B->d_ctl, h, use_cond);
@@ -545,7 +578,9 @@ const char* nc_batch_last_cuda_error(void) { return cudaGetErrorString(g_batch_e
 nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, int flags, void* stream, nc_batch* out) {
     if (!out) return NC_ERR_ARG;
     *out = nullptr;
-    if (max_slots < 1 || max_unknowns < 1 || kmax < 1 || kmax > 4096 || (flags & ~NC_BATCH_HOST_LOOP)) return NC_ERR_ARG;
+    if (max_slots < 1 || max_unknowns < 1 || kmax < 1 || kmax > 4096 ||
+        (flags & ~(NC_BATCH_HOST_LOOP | NC_BATCH_F64_APPLY)))
+        return NC_ERR_ARG;
     nc_batch B = new (std::nothrow) nc_batch_s();
     if (!B) return NC_ERR_OOM;
     B->flags = flags;
@@ -567,7 +602,12 @@ nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, int fl
         if ((s = balloc(reinterpret_cast<void**>(&B->d_ctl), sizeof(BCtl)))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->d_ntile_step), sizeof(int) * (kmax + 1)))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->pool64), sizeof(double) * 6 * (size_t)max_unknowns))) break;
-        if ((s = balloc(reinterpret_cast<void**>(&B->pool32), sizeof(float) * 4 * (size_t)max_unknowns))) break;
+        // apply vectors: 4 float32 per unknown (t0..t2, r32), or 3 float64 (+ slack
+        // for the 16-byte rounding of the split below)
+        if ((s = balloc(reinterpret_cast<void**>(&B->pool32),
+                        (flags & NC_BATCH_F64_APPLY) ? sizeof(double) * 3 * (size_t)max_unknowns
+                                                     : sizeof(float) * 4 * (size_t)max_unknowns)))
+            break;
         cudaError_t e;
         if ((e = cudaMallocHost(&B->h_state, sizeof(BState) * max_slots)) ||
             (e = cudaMallocHost(&B->h_ctl, sizeof(BCtl))) ||
@@ -613,10 +653,15 @@ nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx
     d.nx = nx; d.ny = ny; d.nz = nz; d.n = (int)n; d.k = degree_k;
     d.c0 = 1.0; d.cx = cx / c0; d.cy = cy / c0; d.cz = cz / c0;
     double* base64 = B->pool64 + 6 * o;
-    float* base32 = B->pool32 + 4 * o;
     d.b = base64; d.x = base64 + n; d.r = base64 + 2 * n; d.z = base64 + 3 * n; d.p = base64 + 4 * n;
     d.q = base64 + 5 * n;
-    d.t0 = base32; d.t1 = base32 + n; d.t2 = base32 + 2 * n; d.r32 = base32 + 3 * n;
+    if (B->flags & NC_BATCH_F64_APPLY) {
+        double* baseP = reinterpret_cast<double*>(B->pool32) + 3 * o;
+        d.dt0 = baseP; d.dt1 = baseP + n; d.dt2 = baseP + 2 * n;
+    } else {
+        float* base32 = B->pool32 + 4 * o;
+        d.t0 = base32; d.t1 = base32 + n; d.t2 = base32 + 2 * n; d.r32 = base32 + 3 * n;
+    }
     // Chebyshev step coefficients (Eq. rhocheb, theta' = s theta) folded into
     // the stencil form: e0 = a_j + d_j c0, e_a = -d_j c_a
     const double theta = theta_scale * (lambda_max + lambda_min) / 2.0;
@@ -641,6 +686,12 @@ nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx
         c.cb = (float)cb;
         c.cc = (float)cc;
         c.terms = (cb != 0.0 ? kTermW : 0) | (cc != 0.0 ? kTermR : 0);
+        c.e0d = ca + cd * d.c0;
+        c.exd = -cd * d.cx;
+        c.eyd = -cd * d.cy;
+        c.ezd = -cd * d.cz;
+        c.cbd = cb;
+        c.ccd = cc;
         cf[j - 1] = c;
         rho_prev = rho;
     }

@@ -53,13 +53,14 @@ def _wait_until(t0: float, t: float):
 
 
 def serve_continuous(reqs, budget_unknowns: int, max_slots: int, kmax: int, tol: float = 1e-8,
-                     maxit: int = 5000, iters_per_tick: int = 2, stream=None, stats=None):
+                     maxit: int = 5000, iters_per_tick: int = 2, stream=None, stats=None, f64_apply: bool = False):
     """Serve `reqs` (sorted by arrival) with continuous batching; returns the
     wall-clock span of the run.  Fills each request's x, result, t_done (the
     time its solution is in x).  `stats` (a dict, optional) receives the
-    engine's iteration and kernel-launch counts."""
+    engine's iteration and kernel-launch counts.  `f64_apply` runs P_k in
+    float64 (default: float32 apply, float64 outer CG)."""
     import torch
-    eng = nc.pcg_batch_create(max_slots, budget_unknowns, kmax, stream)
+    eng = nc.pcg_batch_create(max_slots, budget_unknowns, kmax, stream, f64_apply=f64_apply)
     for r in reqs:
         if r.n > budget_unknowns:
             raise ValueError(f"request {r.rid} ({r.n} unknowns) exceeds the budget")
