@@ -98,7 +98,9 @@ def serve_continuous(reqs, budget_unknowns: int, max_slots: int, kmax: int, tol:
                 finished.append(slot)
         if finished:
             # the collects are enqueued: a solution counts as delivered when its copy is done
-            if stream is None:
+            if not torch.cuda.is_available():
+                pass                       # no device work to wait for
+            elif stream is None:
                 torch.cuda.current_stream().synchronize()
             elif hasattr(stream, "synchronize"):
                 stream.synchronize()
