@@ -38,6 +38,21 @@ class Candidate:
     predicted_ms: float
 
 
+def predict_iterations(ia: int, rel_a: float, ib: int, rel_b: float, tol: float):
+    """(rho, predicted iterations to ||r||/||b|| <= tol) from two probes:
+    relative residuals rel_a after ia iterations and rel_b after ib > ia.
+    The contraction rho is taken over the later window; when the short probe
+    already met tol, from its start instead."""
+    rel_a, rel_b = max(rel_a, 1e-300), max(rel_b, 1e-300)
+    if rel_a <= tol:
+        rho = rel_a ** (1.0 / max(ia, 1))
+        return rho, (math.log(tol) / math.log(rho) if 0.0 < rho < 1.0 else float(ia))
+    rho = (rel_b / rel_a) ** (1.0 / max(ib - ia, 1))
+    # the crossing of tol, from whichever probe end lies above it
+    ref_i, ref_r = (ia, rel_a) if rel_b <= tol else (ib, rel_b)
+    return rho, (ref_i + math.log(tol / ref_r) / math.log(rho) if 0.0 < rho < 1.0 else math.inf)
+
+
 def tune_degree(A, lmin: float, lmax: float, degrees=(0, 2, 4, 8, 12, 16, 20, 30, 40),
                 scales=(1.0, 1.001, 1.01), tol: float = 1e-8, probe_iters: int = 8, apply_dtype: str = "f64",
                 seed: int = 17, stream=None) -> list:
@@ -75,16 +90,7 @@ def tune_degree(A, lmin: float, lmax: float, degrees=(0, 2, 4, 8, 12, 16, 20, 30
                 S.close()
             ia, ib = ra["iters"], rb["iters"]
             ms = (tb - ta) / max(ib - ia, 1)
-            rel_a, rel_b = max(ra["relres"], 1e-300), max(rb["relres"], 1e-300)
-            if rel_a <= tol:
-                # converged within the short probe: interpolate from its start
-                rho = rel_a ** (1.0 / max(ia, 1))
-                pred = math.log(tol) / math.log(rho) if 0.0 < rho < 1.0 else float(ia)
-            else:
-                rho = (rel_b / rel_a) ** (1.0 / max(ib - ia, 1))
-                # the crossing of tol, from whichever probe end lies above it
-                ref_i, ref_r = (ia, rel_a) if rel_b <= tol else (ib, rel_b)
-                pred = ref_i + math.log(tol / ref_r) / math.log(rho) if 0.0 < rho < 1.0 else math.inf
+            rho, pred = predict_iterations(ia, ra["relres"], ib, rb["relres"], tol)
             out.append(Candidate(k, s, ib, rho, ms, pred, pred * ms))
     out.sort(key=lambda c: c.predicted_ms)
     return out
