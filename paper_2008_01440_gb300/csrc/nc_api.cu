@@ -305,6 +305,38 @@ void setup_coefficients(nc_solver S) {
     }
 }
 
+// Coefficients of the fused steps as the kernels take them, for the stored
+// iterates y_j = x_j / g_j.  In float64 the scale g_j = cd_j g_{j-1} makes the
+// coefficient of the product exactly 1, so the step kernels drop one float64
+// multiply per row (their bound is the float64 pipe); the last step keeps
+// g_k = 1 so z itself is stored, and g falls back to 1 at any step where it
+// would leave [2^-64, 2^64].  The mixed-precision path stores x_j itself.
+// Entry j = step j (index 0 unused); the x_{k-1} term is dropped for the
+// shifted operator (see enqueue_poly).
+struct StepC {
+    double ca, cb, cc, cd;
+};
+
+std::vector<StepC> step_coefs(const nc_solver S) {
+    const int k = S->k;
+    std::vector<StepC> out(k + 1, StepC{0.0, 0.0, 0.0, 0.0});
+    std::vector<double> g(k + 1, 1.0);
+    for (int j = 1; j <= k; ++j) {
+        double ca = S->ca[j];
+        if (S->shift != 0.0) ca = (j == 1) ? S->ca1_shifted : 0.0;
+        const double gu = (j == 1) ? 1.0 : g[j - 1];   // scale of u (r at step 1)
+        const double gw = (j >= 3) ? g[j - 2] : 1.0;   // scale of w = y_{j-2}
+        const double t = S->cd[j] * gu;
+        const bool unit = !S->mixed && j < k && std::fabs(t) >= 0x1p-64 && std::fabs(t) <= 0x1p64;
+        g[j] = unit ? t : 1.0;
+        out[j].ca = ca * gu / g[j];
+        out[j].cb = S->cb[j] * gw / g[j];
+        out[j].cc = S->cc[j] / g[j];
+        out[j].cd = unit ? 1.0 : t;
+    }
+    return out;
+}
+
 // z = P_k(A) r.  r64: float64 residual; the mixed path reads S->r32 (which
 // must already hold (float) r64).  fin: reduction of (r, z) or FIN_NONE.
 // out = g P_j v (+ w_coef w when w is non-null) by the recursion of
@@ -358,19 +390,18 @@ cudaError_t enqueue_poly(nc_solver S, const double* r64, double* z, int fin, con
     if (S->nlev >= 1)
         return enqueue_newton(S, S->nlev, r64, z, 1.0, nullptr, 0.0, fin != FIN_NONE ? r64 : nullptr, R, done, st);
     const void* rx = S->mixed ? static_cast<const void*>(S->r32) : static_cast<const void*>(r64);
+    // with the shifted operator A' = A - theta' I the x_{k-1} term of every
+    // step k >= 2 vanishes (a_k + d_k theta' = 0 exactly) and step 1 keeps
+    // (4 rho_1 - 2 rho_1)/delta = 2 rho_1/delta on r
+    const std::vector<StepC> cf = step_coefs(S);
     for (int j = 1; j <= S->k; ++j) {
         const void* u = (j == 1) ? rx : S->buf[(j - 1) % 3];
         const void* w = (j >= 3) ? S->buf[(j - 2) % 3] : nullptr;
         const bool last = (j == S->k);
         void* y = last ? static_cast<void*>(z) : S->buf[j % 3];
         const int dot = (last && fin != FIN_NONE) ? 1 : 0;
-        // with the shifted operator A' = A - theta' I the x_{k-1} term of
-        // every step k >= 2 vanishes (a_k + d_k theta' = 0 exactly) and step 1
-        // keeps (4 rho_1 - 2 rho_1)/delta = 2 rho_1/delta on r
-        double ca = S->ca[j];
-        if (S->shift != 0.0) ca = (j == 1) ? S->ca1_shifted : 0.0;
-        cudaError_t e = op_step(S->opP, S->mixed, last || !S->mixed, u, w, rx, y, ca, S->cb[j], S->cc[j],
-                                S->cd[j], dot, r64, R, done, st);
+        cudaError_t e = op_step(S->opP, S->mixed, last || !S->mixed, u, w, rx, y, cf[j].ca, cf[j].cb, cf[j].cc,
+                                cf[j].cd, dot, r64, R, done, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -561,16 +592,15 @@ cudaError_t menqueue_poly(nc_solver S, int m, int fin, cudaStream_t st) {
         return cudaSuccess;
     }
     const void* rx = S->mixed ? static_cast<const void*>(S->mr32) : static_cast<const void*>(S->mr);
+    const std::vector<StepC> cf = step_coefs(S);
     for (int j = 1; j <= S->k; ++j) {
         const void* u = (j == 1) ? rx : S->mbuf[(j - 1) % 3];
         const void* w = (j >= 3) ? S->mbuf[(j - 2) % 3] : nullptr;
         const bool last = (j == S->k);
         void* y = last ? static_cast<void*>(S->mz) : S->mbuf[j % 3];
-        double ca = S->ca[j];
-        if (S->shift != 0.0) ca = (j == 1) ? S->ca1_shifted : 0.0;
         cudaError_t e = launch_sell_mstep(n, m, n, S->opP.ptr, S->opP.col, S->opP.val, S->opP.vdt, S->mixed,
-                                          last || !S->mixed, u, w, rx, y, ca, S->cb[j], S->cc[j], S->cd[j], S->mS,
-                                          st);
+                                          last || !S->mixed, u, w, rx, y, cf[j].ca, cf[j].cb, cf[j].cc, cf[j].cd,
+                                          S->mS, st);
         if (e) return e;
     }
     if (fin == FIN_NONE) return cudaSuccess;
@@ -1410,13 +1440,12 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
             // one-cluster solve: per-step coefficients of the shifted operator
             std::vector<double> cf(4 * (size_t)(S->k + 1), 0.0);
             if (S->k == 0) cf[0] = 1.0 / S->theta;
+            const std::vector<StepC> sc = step_coefs(S);
             for (int j = 1; j <= S->k; ++j) {
-                double ca = S->ca[j];
-                if (S->shift != 0.0) ca = (j == 1) ? S->ca1_shifted : 0.0;
-                cf[4 * j] = ca;
-                cf[4 * j + 1] = S->cb[j];
-                cf[4 * j + 2] = S->cc[j];
-                cf[4 * j + 3] = S->cd[j];
+                cf[4 * j] = sc[j].ca;
+                cf[4 * j + 1] = sc[j].cb;
+                cf[4 * j + 2] = sc[j].cc;
+                cf[4 * j + 3] = sc[j].cd;
             }
             if ((s = dev_alloc_n(&S->pcoef, (int64_t)cf.size()))) break;
             if ((e = cudaMemcpyAsync(S->pcoef, cf.data(), sizeof(double) * cf.size(), cudaMemcpyHostToDevice, st)) ||

@@ -38,7 +38,8 @@ struct ClusterArgs {
     const int32_t* sptr;
     const int32_t* col;
     const double* val;
-    const double* coef;   // 4*(k+1): (a, b, c, d) of step j at 4j, shifted-operator form; coef[0] = 1/theta'
+    const double* coef;   // 4*(k+1): (a, b, c, d) of step j at 4j (shifted operator, scaled iterates: d = 1
+                          // takes the product as it is); coef[0] = 1/theta'
     const double* b;
     double* x;
     PcgScalars* S;
@@ -191,13 +192,14 @@ __global__ void __launch_bounds__(kCT) cluster_pcg_kernel(const ClusterArgs a) {
             const double ca = a.coef[4 * j], cb = a.coef[4 * j + 1], cc = a.coef[4 * j + 2], cd = a.coef[4 * j + 3];
             // which optional terms the step has, decided once (a float64
             // compare per row would occupy the float64 pipe)
-            const bool ha = ca != 0.0, hb = cb != 0.0, hc = cc != 0.0;
+            const bool ha = ca != 0.0, hb = cb != 0.0, hc = cc != 0.0, hd = cd != 1.0;
             const double* U = vec + (size_t)us * R;
             const double* Wv = vec + (size_t)ws * R;
             double* Y = vec + (size_t)ys * R;
             const uint32_t uoff = (uint32_t)us * vstride;
             for (int i = threadIdx.x; i < nloc; i += kCT) {
-                double o = cd * row_product(i, lptr, mval, maddr, uoff, 0.0);
+                double o = row_product(i, lptr, mval, maddr, uoff, 0.0);
+                if (hd) o *= cd;
                 if (hc) o = fma(cc, Rv[i], o);
                 if (hb) o = fma(cb, Wv[i], o);
                 if (ha) o = fma(ca, U[i], o);

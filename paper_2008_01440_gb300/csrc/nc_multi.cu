@@ -74,7 +74,7 @@ sell_mstep_kernel(const int n, const int ld, const int32_t* __restrict__ slice_p
 #pragma unroll
     for (int c = 0; c < M; ++c) {
         const size_t o = (size_t)c * ld;
-        AT v = cf.cd * acc[c];
+        AT v = (cf.terms & kUnitD) ? acc[c] : cf.cd * acc[c];
         if (cf.terms & kTermR) v = fma(cf.cc, (AT)r[o + row], v);
         if (cf.terms & kTermW) v = fma(cf.cb, (AT)w[o + row], v);
         if (cf.terms & kTermU) v = fma(cf.ca, (AT)u[o + row], v);

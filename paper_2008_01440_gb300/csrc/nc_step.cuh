@@ -8,6 +8,7 @@
 namespace nc {
 
 constexpr int kTermU = 1, kTermW = 2, kTermR = 4;
+constexpr int kUnitD = 8;   // cd == 1: the product is taken as it is
 
 template <typename T> struct AccOf { using type = float; };
 template <> struct AccOf<double> { using type = double; };
@@ -41,7 +42,8 @@ inline StepCoef<AT> make_coef(double ca, double cb, double cc, double cd) {
     c.cb = (AT)cb;
     c.cc = (AT)cc;
     c.cd = (AT)cd;
-    c.terms = (ca != 0.0 ? kTermU : 0) | (cb != 0.0 ? kTermW : 0) | (cc != 0.0 ? kTermR : 0);
+    c.terms = (ca != 0.0 ? kTermU : 0) | (cb != 0.0 ? kTermW : 0) | (cc != 0.0 ? kTermR : 0) |
+              (cd == 1.0 ? kUnitD : 0);
     return c;
 }
 
@@ -51,7 +53,7 @@ __device__ __forceinline__ double step_row_out(int row, AT acc, const StepCoef<A
                                                const XT* __restrict__ u, const XT* __restrict__ w,
                                                const XT* __restrict__ r, YT* __restrict__ y,
                                                const double* __restrict__ rdot) {
-    AT o = c.cd * acc;
+    AT o = (c.terms & kUnitD) ? acc : c.cd * acc;
     if (c.terms & kTermR) o = fma(c.cc, (AT)r[row], o);
     if (c.terms & kTermW) o = fma(c.cb, (AT)w[row], o);
     if (c.terms & kTermU) o = fma(c.ca, (AT)u[row], o);
