@@ -36,6 +36,8 @@ sell_mstep_kernel(const int n, const int ld, const int32_t* __restrict__ slice_p
     using AT = typename AccOf<XT>::type;
     constexpr int G = M >= 8 ? 2 : (M >= 4 ? 4 : 8);
     if (Sm != nullptr && all_done(Sm, M)) return;
+    if constexpr (sizeof(AT) == 4)
+        if (threadIdx.x == 0) prefetch_sell_tile((int)blockIdx.x + kPrefetchAhead, n, slice_ptr, col, val);
     const int row = blockIdx.x * kBlock + threadIdx.x;
     if (row >= n) return;
     const int s = row >> 5;

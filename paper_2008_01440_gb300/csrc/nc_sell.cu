@@ -104,6 +104,8 @@ sell_step_kernel(const int n, const int32_t* __restrict__ slice_ptr, const int32
     if (done != nullptr && *done) return;
     if constexpr (DOT == 0) {
         // one 256-row tile per CTA
+        if constexpr (sizeof(typename AccOf<XT>::type) == 4)
+            if (threadIdx.x == 0) prefetch_sell_tile((int)blockIdx.x + kPrefetchAhead, n, slice_ptr, col, val);
         const int row = blockIdx.x * kBlock + threadIdx.x;
         if (row < n) sell_row<VT, XT, YT, 0>(row, slice_ptr, col, val, u, w, r, y, c, rdot);
     } else {
@@ -112,6 +114,8 @@ sell_step_kernel(const int n, const int32_t* __restrict__ slice_ptr, const int32
         double dv = 0.0;
         const int ntiles = (n + kBlock - 1) / kBlock;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            if constexpr (sizeof(typename AccOf<XT>::type) == 4)
+                if (threadIdx.x == 0) prefetch_sell_tile(tile + (int)gridDim.x, n, slice_ptr, col, val);
             const int row = tile * kBlock + threadIdx.x;
             if (row < n) dv += sell_row<VT, XT, YT, DOT>(row, slice_ptr, col, val, u, w, r, y, c, rdot);
         }
