@@ -68,8 +68,23 @@ typedef enum { NC_F64 = 0, NC_F32 = 1, NC_BF16 = 2 } nc_dtype;
  * picks SELL when the padding is at most 1.5x the nonzeros, else CSR (plain
  * block CSR for BSR3); TUNE builds SELL (padding up to 4x), times one fused
  * step in each layout on this matrix during pcg_setup and keeps the faster
- * (timings in nc_solver_info).  Stencil handles ignore the option. */
-typedef enum { NC_FORMAT_AUTO = 0, NC_FORMAT_CSR = 1, NC_FORMAT_SELL = 2, NC_FORMAT_TUNE = 3 } nc_format;
+ * (timings in nc_solver_info).  PSELL (scalar CSR matrices only): SELL
+ * whose slices store no column indices; slice s holds the columns
+ * row + o for the sorted set of offsets o = col - row of its 32 rows (rows
+ * lacking an offset store a 0 there), and each distinct set is kept once.
+ * It applies when every row's columns increase, a slice has at most 64
+ * offsets, the padding is at most 1.5x and the distinct sets hold at most
+ * 16384 offsets in all (regularly numbered grid matrices); otherwise the
+ * solver falls back to SELL.  AUTO tries PSELL first for CSR matrices,
+ * except with use_graph = 2 (the cluster solve reads plain SELL).  Stencil
+ * handles ignore the option. */
+typedef enum {
+    NC_FORMAT_AUTO = 0,
+    NC_FORMAT_CSR = 1,
+    NC_FORMAT_SELL = 2,
+    NC_FORMAT_TUNE = 3,
+    NC_FORMAT_PSELL = 4
+} nc_format;
 
 /* How the preconditioner is evaluated.  CHEBYSHEV: the three-term recurrence
  * of Algorithm 2 (Sec. 3, Eq. rhocheb), any degree k, one fused product step
@@ -110,7 +125,7 @@ typedef struct {
 typedef struct {
     int64_t n;
     int32_t degree_k;
-    int32_t spmv_format;  /* NC_FORMAT_CSR or NC_FORMAT_SELL (after AUTO)      */
+    int32_t spmv_format;  /* NC_FORMAT_CSR, _SELL or _PSELL (after AUTO)      */
     int32_t apply_dtype;
     int32_t persistent;   /* 1: solves run as one kernel on one cluster     */
     double padding;       /* stored entries / nonzeros of the chosen layout    */
@@ -120,6 +135,7 @@ typedef struct {
                              recursion, Sec. 3), 0 = A itself               */
     double tune_us_plain; /* TUNE: measured step time, plain layout (us)   */
     double tune_us_sliced;/* TUNE: measured step time, sliced layout (us)  */
+    int64_t patterns;     /* PSELL: distinct offset sets stored; else 0     */
 } nc_solver_info;
 
 typedef struct {

@@ -29,8 +29,9 @@ _DTYPES = {"f64": NC_F64, "f32": NC_F32, "bf16": NC_BF16}
 SOLVE_STATUSES = (NC_OK, NC_ERR_MAXIT, NC_ERR_INDEFINITE, NC_ERR_BREAKDOWN)
 
 
-NC_FORMAT_AUTO, NC_FORMAT_CSR, NC_FORMAT_SELL, NC_FORMAT_TUNE = 0, 1, 2, 3
-_FORMATS = {"auto": NC_FORMAT_AUTO, "csr": NC_FORMAT_CSR, "sell": NC_FORMAT_SELL, "tune": NC_FORMAT_TUNE}
+NC_FORMAT_AUTO, NC_FORMAT_CSR, NC_FORMAT_SELL, NC_FORMAT_TUNE, NC_FORMAT_PSELL = 0, 1, 2, 3, 4
+_FORMATS = {"auto": NC_FORMAT_AUTO, "csr": NC_FORMAT_CSR, "sell": NC_FORMAT_SELL, "tune": NC_FORMAT_TUNE,
+            "psell": NC_FORMAT_PSELL}
 
 
 class nc_options(ctypes.Structure):
@@ -43,7 +44,8 @@ class nc_solver_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("degree_k", ctypes.c_int32), ("spmv_format", ctypes.c_int32),
                 ("apply_dtype", ctypes.c_int32), ("persistent", ctypes.c_int32), ("padding", ctypes.c_double),
                 ("theta", ctypes.c_double), ("delta", ctypes.c_double), ("sigma", ctypes.c_double),
-                ("shift", ctypes.c_double), ("tune_us_plain", ctypes.c_double), ("tune_us_sliced", ctypes.c_double)]
+                ("shift", ctypes.c_double), ("tune_us_plain", ctypes.c_double), ("tune_us_sliced", ctypes.c_double),
+                ("patterns", ctypes.c_int64)]
 
 
 class nc_result(ctypes.Structure):
@@ -290,7 +292,8 @@ def pcg_get_info(S: Solver) -> dict:
     _check(lib.pcg_get_info(S.handle, ctypes.byref(info)), "pcg_get_info")
     d = {f: getattr(info, f) for f, _ in info._fields_}
     d["persistent"] = bool(d["persistent"])
-    d["spmv_format"] = {NC_FORMAT_CSR: "csr", NC_FORMAT_SELL: "sell"}.get(d["spmv_format"], d["spmv_format"])
+    d["spmv_format"] = {NC_FORMAT_CSR: "csr", NC_FORMAT_SELL: "sell", NC_FORMAT_PSELL: "psell"}.get(
+        d["spmv_format"], d["spmv_format"])
     return d
 
 

@@ -13,6 +13,8 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "nc_common.cuh"
@@ -49,6 +51,7 @@ struct OpView {
     int vdt = NC_F64;
     StencilGeom geom{0, 0, 0};      // OP_STENCIL
     double c4[4] = {0, 0, 0, 0};
+    SellPat pat;                    // OP_SELL with offset patterns (pat.pstart set): col unused
 };
 
 struct nc_solver_s {
@@ -86,6 +89,9 @@ struct nc_solver_s {
     void* lval = nullptr;                 // converted CSR values (F32/BF16), owned
     int32_t* sell_ptr = nullptr;          // SELL-32 arrays, owned
     int32_t* sell_col = nullptr;
+    int32_t* psell_start = nullptr;       // offset-pattern layout: per-slice start in psell_off, owned
+    int32_t* psell_off = nullptr;         // the distinct offset sets, owned
+    int64_t npatterns = 0;
     double* sell_val64 = nullptr;
     void* sell_valP = nullptr;
     double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
@@ -203,8 +209,8 @@ cudaError_t op_step(const OpView& op, bool x_f32, bool y_f64, const void* u, con
                     void* y, double ca, double cb, double cc, double cd, int dot, const double* rdot,
                     const Reduce& R, const int* done, cudaStream_t st) {
     if (op.kind == OP_SELL)
-        return launch_sell_step(op.n, op.ptr, op.col, op.val, op.vdt, x_f32, y_f64, u, w, r, y, ca, cb, cc, cd,
-                                dot, rdot, R, done, st);
+        return launch_sell_step(op.n, op.ptr, op.col, op.pat, op.val, op.vdt, x_f32, y_f64, u, w, r, y, ca, cb, cc,
+                                cd, dot, rdot, R, done, st);
     if (op.kind == OP_STENCIL)
         return launch_stencil_step(op.geom, op.c4, x_f32, y_f64, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done,
                                    st);
@@ -598,9 +604,9 @@ cudaError_t menqueue_poly(nc_solver S, int m, int fin, cudaStream_t st) {
         const void* w = (j >= 3) ? S->mbuf[(j - 2) % 3] : nullptr;
         const bool last = (j == S->k);
         void* y = last ? static_cast<void*>(S->mz) : S->mbuf[j % 3];
-        cudaError_t e = launch_sell_mstep(n, m, n, S->opP.ptr, S->opP.col, S->opP.val, S->opP.vdt, S->mixed,
-                                          last || !S->mixed, u, w, rx, y, cf[j].ca, cf[j].cb, cf[j].cc, cf[j].cd,
-                                          S->mS, st);
+        cudaError_t e = launch_sell_mstep(n, m, n, S->opP.ptr, S->opP.col, S->opP.pat, S->opP.val, S->opP.vdt,
+                                          S->mixed, last || !S->mixed, u, w, rx, y, cf[j].ca, cf[j].cb, cf[j].cc,
+                                          cf[j].cd, S->mS, st);
         if (e) return e;
     }
     if (fin == FIN_NONE) return cudaSuccess;
@@ -640,8 +646,8 @@ cudaError_t menqueue_body(nc_solver S, int m, cudaGraphConditionalHandle h, int 
     const size_t cn = (size_t)n;
     cudaError_t e;
     // q = A p for all columns (A' p + shift p with the shifted operator)
-    if ((e = launch_sell_mstep(n, m, n, S->op64.ptr, S->op64.col, S->op64.val, NC_F64, false, true, S->mp, nullptr,
-                               nullptr, S->mq, S->shift, 0.0, 0.0, 1.0, S->mS, st)))
+    if ((e = launch_sell_mstep(n, m, n, S->op64.ptr, S->op64.col, S->op64.pat, S->op64.val, NC_F64, false, true,
+                               S->mp, nullptr, nullptr, S->mq, S->shift, 0.0, 0.0, 1.0, S->mS, st)))
         return e;
     for (int c = 0; c < m; ++c) {
         PcgScalars* Sc = S->mS + c;
@@ -872,6 +878,156 @@ nc_status setup_operator_bsr3(nc_solver S, cudaStream_t st, size_t eb) {
     return NC_OK;
 }
 
+// Offset-pattern layout (NC_FORMAT_PSELL) from the CSR arrays.  Returns
+// NC_ERR_UNSUPPORTED, with nothing left allocated, when the matrix does not
+// qualify: a row whose columns do not increase, a slice with more than 64
+// offsets, padding above kSellMaxPadding, or distinct offset sets holding
+// more than kPatMaxTable offsets in all.
+constexpr int64_t kPatMaxTable = 16384;
+
+nc_status setup_psell(nc_solver S, cudaStream_t st, size_t eb) {
+    nc_matrix A = S->A;
+    const int n = (int)S->n;
+    const int nslices = (n + 31) / 32;
+    int32_t *dcnt = nullptr, *dopos = nullptr, *doff = nullptr;
+    int* dbad = nullptr;
+    nc_status ret = NC_ERR_UNSUPPORTED;
+    std::vector<int32_t> hp32;
+    do {
+        if ((ret = dev_alloc_n(&dcnt, nslices)) != NC_OK || (ret = dev_alloc_n(&dbad, 1)) != NC_OK) break;
+        ret = NC_ERR_UNSUPPORTED;
+        std::vector<int32_t> cnt(nslices);
+        int bad = 0;
+        cudaError_t e;
+        if ((e = cudaMemsetAsync(dbad, 0, sizeof(int), st)) ||
+            (e = launch_psell_merge(n, A->rowptr, A->col, nullptr, dcnt, nullptr, dbad, st)) ||
+            (e = cudaMemcpyAsync(cnt.data(), dcnt, sizeof(int32_t) * nslices, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st))) {
+            g_last_cuda = e;
+            ret = NC_ERR_CUDA;
+            break;
+        }
+        if (bad) break;
+        std::vector<int32_t> opos(nslices + 1);
+        hp32.assign(nslices + 1, 0);
+        int64_t noff = 0, total = 0;
+        for (int i = 0; i < nslices; ++i) {
+            opos[i] = (int32_t)noff;
+            hp32[i] = (int32_t)total;
+            noff += cnt[i];
+            total += 32 * (int64_t)cnt[i];
+            if (total >= ((int64_t)1 << 31)) break;
+        }
+        if (total >= ((int64_t)1 << 31)) break;
+        opos[nslices] = (int32_t)noff;
+        hp32[nslices] = (int32_t)total;
+        const double padding = A->nnz > 0 ? (double)total / (double)A->nnz : 1.0;
+        if (padding > kSellMaxPadding) break;
+        // the sets themselves, then each distinct set stored once
+        if ((ret = dev_alloc_n(&dopos, nslices + 1)) != NC_OK || (ret = dev_alloc_n(&doff, noff)) != NC_OK) break;
+        ret = NC_ERR_UNSUPPORTED;
+        std::vector<int32_t> off((size_t)noff);
+        if ((e = cudaMemcpyAsync(dopos, opos.data(), sizeof(int32_t) * (nslices + 1), cudaMemcpyHostToDevice, st)) ||
+            (e = launch_psell_merge(n, A->rowptr, A->col, dopos, nullptr, doff, dbad, st)) ||
+            (e = cudaMemcpyAsync(off.data(), doff, sizeof(int32_t) * (size_t)noff, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st))) {
+            g_last_cuda = e;
+            ret = NC_ERR_CUDA;
+            break;
+        }
+        std::unordered_map<std::string, int32_t> seen;
+        std::vector<int32_t> table, pstart(nslices);
+        bool fits = true;
+        for (int i = 0; i < nslices && fits; ++i) {
+            std::string key(sizeof(int32_t) * (size_t)cnt[i], '\0');
+            if (cnt[i] > 0) std::memcpy(&key[0], off.data() + opos[i], key.size());
+            auto it = seen.find(key);
+            if (it == seen.end()) {
+                if ((int64_t)table.size() + cnt[i] > kPatMaxTable) {
+                    fits = false;
+                    break;
+                }
+                it = seen.emplace(std::move(key), (int32_t)table.size()).first;
+                table.insert(table.end(), off.begin() + opos[i], off.begin() + opos[i] + cnt[i]);
+            }
+            pstart[i] = it->second;
+        }
+        if (!fits) break;
+        // the layout itself (solver-owned)
+        if ((ret = dev_alloc_n(&S->sell_ptr, nslices + 1)) != NC_OK ||
+            (ret = dev_alloc_n(&S->psell_start, nslices)) != NC_OK ||
+            (ret = dev_alloc_n(&S->psell_off, (int64_t)table.size())) != NC_OK ||
+            (ret = dev_alloc_n(&S->sell_val64, total)) != NC_OK)
+            break;
+        int h_nodiag = 0;
+        S->shift = S->k >= 1 ? S->theta : 0.0;
+        if ((e = cudaMemsetAsync(dbad, 0, sizeof(int), st)) ||
+            (e = cudaMemcpyAsync(S->sell_ptr, hp32.data(), sizeof(int32_t) * (nslices + 1), cudaMemcpyHostToDevice,
+                                 st)) ||
+            (e = cudaMemcpyAsync(S->psell_start, pstart.data(), sizeof(int32_t) * nslices, cudaMemcpyHostToDevice,
+                                 st)) ||
+            (!table.empty() && (e = cudaMemcpyAsync(S->psell_off, table.data(), sizeof(int32_t) * table.size(),
+                                                    cudaMemcpyHostToDevice, st))) ||
+            (e = launch_psell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, S->psell_start, S->psell_off, NC_F64,
+                                   S->shift, S->sell_val64, dbad, st)) ||
+            (e = cudaMemcpyAsync(&h_nodiag, dbad, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st))) {
+            g_last_cuda = e;
+            ret = NC_ERR_CUDA;
+            break;
+        }
+        if (h_nodiag) {   // a row without a diagonal entry: store A itself
+            S->shift = 0.0;
+            if ((e = launch_psell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, S->psell_start, S->psell_off,
+                                       NC_F64, 0.0, S->sell_val64, nullptr, st))) {
+                g_last_cuda = e;
+                ret = NC_ERR_CUDA;
+                break;
+            }
+        }
+        S->op64 = OpView{OP_SELL, n, S->sell_ptr, nullptr, S->sell_val64, NC_F64};
+        S->op64.pat = SellPat{S->psell_start, S->psell_off};
+        S->opP = S->op64;
+        if (S->mixed) {
+            if ((ret = dev_alloc(&S->sell_valP, eb * (size_t)(total > 0 ? total : 1))) != NC_OK) break;
+            if ((e = launch_psell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, S->psell_start, S->psell_off,
+                                       S->vdt, S->shift, S->sell_valP, nullptr, st))) {
+                g_last_cuda = e;
+                ret = NC_ERR_CUDA;
+                break;
+            }
+            S->opP.val = S->sell_valP;
+            S->opP.vdt = S->vdt;
+        }
+        if ((e = cudaStreamSynchronize(st))) {   // the host arrays must outlive the copies
+            g_last_cuda = e;
+            ret = NC_ERR_CUDA;
+            break;
+        }
+        S->padding = padding;
+        S->npatterns = (int64_t)seen.size();
+        S->h_sell_ptr = hp32;
+        ret = NC_OK;
+    } while (0);
+    if (ret != NC_OK) cudaStreamSynchronize(st);   // no copy may still read a host vector
+    dev_free(dcnt);
+    dev_free(dopos);
+    dev_free(doff);
+    dev_free(dbad);
+    if (ret != NC_OK) {
+        dev_free(S->sell_ptr); dev_free(S->psell_start); dev_free(S->psell_off);
+        dev_free(S->sell_val64); dev_free(S->sell_valP);
+        S->sell_ptr = nullptr; S->psell_start = nullptr; S->psell_off = nullptr;
+        S->sell_val64 = nullptr; S->sell_valP = nullptr;
+        S->op64 = OpView{};
+        S->opP = OpView{};
+        S->shift = 0.0;
+        S->npatterns = 0;
+    }
+    return ret;
+}
+
 nc_status setup_operator(nc_solver S, cudaStream_t st) {
     nc_matrix A = S->A;
     const int n = (int)S->n;
@@ -885,6 +1041,11 @@ nc_status setup_operator(nc_solver S, cudaStream_t st) {
     }
     const size_t eb = S->vdt == NC_F64 ? 8 : (S->vdt == NC_F32 ? 4 : 2);
     if (A->kind == MAT_BSR3) return setup_operator_bsr3(S, st, eb);
+    if (n > 0 && (S->opt.spmv_format == NC_FORMAT_PSELL ||
+                  (S->opt.spmv_format == NC_FORMAT_AUTO && S->opt.use_graph != 2))) {
+        const nc_status ps = setup_psell(S, st, eb);
+        if (ps != NC_ERR_UNSUPPORTED) return ps;   // built, or a CUDA / memory error
+    }
     bool sell = S->opt.spmv_format != NC_FORMAT_CSR && n > 0;
     std::vector<int64_t> hptr;
     if (sell) {
@@ -1372,7 +1533,7 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
     if (opt) o = *opt;
     if (o.apply_dtype != NC_F64 && o.apply_dtype != NC_F32 && o.apply_dtype != NC_BF16) return NC_ERR_ARG;
     if (o.rr_period < 0) return NC_ERR_ARG;
-    if (o.spmv_format < NC_FORMAT_AUTO || o.spmv_format > NC_FORMAT_TUNE) return NC_ERR_ARG;
+    if (o.spmv_format < NC_FORMAT_AUTO || o.spmv_format > NC_FORMAT_PSELL) return NC_ERR_ARG;
     int nlev = -1;
     if (o.poly_form == NC_POLY_NEWTON) {
         // Algorithm 1 builds P of degree 2^nlev - 1 only; float64 only
@@ -1435,7 +1596,8 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
         }
         if ((e = cudaMallocHost(&S->h_io, sizeof(PcgScalars)))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
         if ((e = cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking))) { g_last_cuda = e; s = NC_ERR_CUDA; break; }
-        if (o.use_graph == 2 && S->op64.kind == OP_SELL && !S->mixed && o.rr_period == 0 && S->nlev < 0 &&
+        if (o.use_graph == 2 && S->op64.kind == OP_SELL && S->op64.pat.pstart == nullptr && !S->mixed &&
+            o.rr_period == 0 && S->nlev < 0 &&
             plan_cluster_pcg(n, S->h_sell_ptr.data(), &S->plan)) {
             // one-cluster solve: per-step coefficients of the shifted operator
             std::vector<double> cf(4 * (size_t)(S->k + 1), 0.0);
@@ -1580,6 +1742,8 @@ nc_status pcg_get_info(nc_solver S, nc_solver_info* info) {
     info->n = S->n;
     info->degree_k = S->k;
     info->spmv_format = (S->op64.kind == OP_SELL || S->op64.kind == OP_BSELL3) ? NC_FORMAT_SELL : NC_FORMAT_CSR;
+    if (S->op64.pat.pstart != nullptr) info->spmv_format = NC_FORMAT_PSELL;
+    info->patterns = S->npatterns;
     info->apply_dtype = S->vdt;
     info->persistent = S->persistent ? 1 : 0;
     info->padding = S->padding;
@@ -1600,6 +1764,7 @@ nc_status pcg_destroy(nc_solver S) {
     for (int i = 0; i < 3; ++i) dev_free(S->buf[i]);
     dev_free(S->r32); dev_free(S->lval); dev_free(S->partials); dev_free(S->counter); dev_free(S->S);
     dev_free(S->sell_ptr); dev_free(S->sell_col); dev_free(S->sell_val64); dev_free(S->sell_valP);
+    dev_free(S->psell_start); dev_free(S->psell_off);
     dev_free(S->pcoef);
     for (double* bp : S->nbuf) dev_free(bp);
     if (S->mexec) cudaGraphExecDestroy(S->mexec);

@@ -176,11 +176,25 @@ cudaError_t launch_csr_step(int n, const int32_t* rowptr, const int32_t* col, co
                             int dot, const double* rdot, const Reduce& R, const int* done,
                             cudaStream_t st);
 
+// Offset patterns of a SELL-32 layout (pstart null: plain SELL, columns in
+// `col`): slice s takes the columns row + poff[pstart[s] + j], j < its slots.
+struct SellPat {
+    const int32_t* pstart = nullptr;
+    const int32_t* poff = nullptr;
+};
+
 // Same step for the SELL-32 layout (slice_ptr: nslices+1 int32 offsets).
-cudaError_t launch_sell_step(int n, const int32_t* slice_ptr, const int32_t* col, const void* val, int vdt,
-                             bool x_f32, bool y_f64, const void* u, const void* w, const void* r, void* y,
-                             double ca, double cb, double cc, double cd, int dot, const double* rdot,
-                             const Reduce& R, const int* done, cudaStream_t st);
+cudaError_t launch_sell_step(int n, const int32_t* slice_ptr, const int32_t* col, const SellPat& pat,
+                             const void* val, int vdt, bool x_f32, bool y_f64, const void* u, const void* w,
+                             const void* r, void* y, double ca, double cb, double cc, double cd, int dot,
+                             const double* rdot, const Reduce& R, const int* done, cudaStream_t st);
+// Pattern layout construction from CSR: per-slice offset sets (a counting
+// pass with off null, then a writing pass at opos), then the slot-major fill.
+cudaError_t launch_psell_merge(int n, const int32_t* rowptr, const int32_t* col, const int32_t* opos, int32_t* cnt,
+                               int32_t* off, int* bad, cudaStream_t st);
+cudaError_t launch_psell_fill(int n, const int32_t* rowptr, const int32_t* col, const double* val,
+                              const int32_t* slice_ptr, const int32_t* pstart, const int32_t* poff, int vdt,
+                              double shift, void* sval, int* nodiag, cudaStream_t st);
 // SELL-32 construction from CSR: longest row per slice, then the slot-major fill
 cudaError_t launch_sell_lengths(int n, const int32_t* rowptr, int32_t* slice_len, cudaStream_t st);
 // (diagonal entries stored as a_ii - shift; *nodiag set if a row lacks one)
@@ -281,10 +295,10 @@ cudaError_t launch_axpy_dot(int n, double a, const double* x, double* y, const R
 // the SELL matrix read once for all columns; returns at once when every
 // column's scalars (Sm[0..m)) say done.
 int max_rhs();
-cudaError_t launch_sell_mstep(int n, int m, int ld, const int32_t* slice_ptr, const int32_t* col, const void* val,
-                              int vdt, bool x_f32, bool y_f64, const void* u, const void* w, const void* r,
-                              void* y, double ca, double cb, double cc, double cd, const PcgScalars* Sm,
-                              cudaStream_t st);
+cudaError_t launch_sell_mstep(int n, int m, int ld, const int32_t* slice_ptr, const int32_t* col, const SellPat& pat,
+                              const void* val, int vdt, bool x_f32, bool y_f64, const void* u, const void* w,
+                              const void* r, void* y, double ca, double cb, double cc, double cd,
+                              const PcgScalars* Sm, cudaStream_t st);
 // loop condition of a multi-right-hand-side graph: some column not done
 cudaError_t launch_any_active(const PcgScalars* Sm, int m, cudaGraphConditionalHandle h, int use_cond, int* active,
                               cudaStream_t st);

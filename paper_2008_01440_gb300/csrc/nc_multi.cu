@@ -27,24 +27,30 @@ __device__ __forceinline__ bool all_done(const PcgScalars* Sm, int m) {
 // before this column's FMAs, one memory latency per column (measured: the
 // 8-column float step of the 128^3 system at 30 % of DRAM bandwidth, stalled
 // on loads).  G slots per group, so that about 16 gathers are in flight.
-template <typename VT, typename XT, typename YT, int M>
+// UNIT: the product's coefficient is exactly 1 (float64 scaled iterates), a
+// compile-time case so that no multiply is issued.
+template <typename VT, typename XT, typename YT, int M, bool PAT, bool UNIT>
 __global__ void __launch_bounds__(kBlock)
 sell_mstep_kernel(const int n, const int ld, const int32_t* __restrict__ slice_ptr,
-                  const int32_t* __restrict__ col, const VT* __restrict__ val, const XT* __restrict__ u,
-                  const XT* __restrict__ w, const XT* __restrict__ r, YT* __restrict__ y,
+                  const int32_t* __restrict__ col, const SellPat pat, const VT* __restrict__ val,
+                  const XT* __restrict__ u, const XT* __restrict__ w, const XT* __restrict__ r, YT* __restrict__ y,
                   const StepCoef<typename AccOf<XT>::type> cf, const PcgScalars* __restrict__ Sm) {
     using AT = typename AccOf<XT>::type;
     constexpr int G = M >= 8 ? 2 : (M >= 4 ? 4 : 8);
     if (Sm != nullptr && all_done(Sm, M)) return;
     if constexpr (sizeof(AT) == 4)
-        if (threadIdx.x == 0) prefetch_sell_tile((int)blockIdx.x + kPrefetchAhead, n, slice_ptr, col, val);
+        if (threadIdx.x == 0)
+            prefetch_sell_tile((int)blockIdx.x + kPrefetchAhead, n, slice_ptr, PAT ? nullptr : col, val);
     const int row = blockIdx.x * kBlock + threadIdx.x;
     if (row >= n) return;
     const int s = row >> 5;
     const int beg = slice_ptr[s];
     const int len = (slice_ptr[s + 1] - beg) >> 5;   // warp-uniform
     const VT* vp = val + beg + (row & 31);
-    const int32_t* cp = col + beg + (row & 31);
+    const int32_t* cp = nullptr;
+    const int32_t* op = nullptr;   // PAT: columns row + op[j] (clamped; padded slots have value 0)
+    if constexpr (PAT) op = pat.poff + __ldg(pat.pstart + s);
+    else cp = col + beg + (row & 31);
     AT acc[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) acc[c] = AT(0);
@@ -56,7 +62,8 @@ sell_mstep_kernel(const int n, const int ld, const int32_t* __restrict__ slice_p
             cj[t] = row;   // padding of a short group: a valid address, weight 0
             vj[t] = AT(0);
             if (j0 + t < len) {
-                cj[t] = ld_stream(cp + 32 * t);
+                if constexpr (PAT) cj[t] = min(max(row + __ldg(op + j0 + t), 0), n - 1);
+                else cj[t] = ld_stream(cp + 32 * t);
                 vj[t] = (AT)ld_stream(vp + 32 * t);
             }
         }
@@ -71,12 +78,14 @@ sell_mstep_kernel(const int n, const int ld, const int32_t* __restrict__ slice_p
             for (int t = 0; t < G; ++t)
                 if (j0 + t < len) acc[c] = fma(vj[t], xv[c][t], acc[c]);
         vp += 32 * G;
-        cp += 32 * G;
+        if constexpr (!PAT) cp += 32 * G;
     }
 #pragma unroll
     for (int c = 0; c < M; ++c) {
         const size_t o = (size_t)c * ld;
-        AT v = (cf.terms & kUnitD) ? acc[c] : cf.cd * acc[c];
+        AT v;
+        if constexpr (UNIT) v = acc[c];
+        else v = cf.cd * acc[c];
         if (cf.terms & kTermR) v = fma(cf.cc, (AT)r[o + row], v);
         if (cf.terms & kTermW) v = fma(cf.cb, (AT)w[o + row], v);
         if (cf.terms & kTermU) v = fma(cf.ca, (AT)u[o + row], v);
@@ -94,23 +103,44 @@ __global__ void any_active_kernel(const PcgScalars* __restrict__ Sm, int m, cuda
 }
 
 template <typename VT, typename XT, typename YT, int M>
-cudaError_t mstep_launch_m(int n, int ld, const int32_t* sptr, const int32_t* col, const void* val, const void* u,
-                           const void* w, const void* r, void* y, double ca, double cb, double cc, double cd,
-                           const PcgScalars* Sm, cudaStream_t st) {
+cudaError_t mstep_launch_m(int n, int ld, const int32_t* sptr, const int32_t* col, const SellPat& pat,
+                           const void* val, const void* u, const void* w, const void* r, void* y, double ca,
+                           double cb, double cc, double cd, const PcgScalars* Sm, cudaStream_t st) {
     using AT = typename AccOf<XT>::type;
     const StepCoef<AT> c = make_coef<AT>(ca, cb, cc, cd);
-    sell_mstep_kernel<VT, XT, YT, M><<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(
-        n, ld, sptr, col, static_cast<const VT*>(val), static_cast<const XT*>(u), static_cast<const XT*>(w),
-        static_cast<const XT*>(r), static_cast<YT*>(y), c, Sm);
+    const unsigned grid = (unsigned)((n + kBlock - 1) / kBlock);
+    const VT* v = static_cast<const VT*>(val);
+    const XT* uu = static_cast<const XT*>(u);
+    const XT* ww = static_cast<const XT*>(w);
+    const XT* rr = static_cast<const XT*>(r);
+    YT* yy = static_cast<YT*>(y);
+    if constexpr (sizeof(AT) == 8) {
+        if (cd == 1.0) {
+            if (pat.pstart != nullptr)
+                sell_mstep_kernel<VT, XT, YT, M, true, true><<<grid, kBlock, 0, st>>>(n, ld, sptr, col, pat, v, uu,
+                                                                                      ww, rr, yy, c, Sm);
+            else
+                sell_mstep_kernel<VT, XT, YT, M, false, true><<<grid, kBlock, 0, st>>>(n, ld, sptr, col, pat, v, uu,
+                                                                                       ww, rr, yy, c, Sm);
+            return cudaGetLastError();
+        }
+    }
+    if (pat.pstart != nullptr)
+        sell_mstep_kernel<VT, XT, YT, M, true, false><<<grid, kBlock, 0, st>>>(n, ld, sptr, col, pat, v, uu, ww, rr,
+                                                                               yy, c, Sm);
+    else
+        sell_mstep_kernel<VT, XT, YT, M, false, false><<<grid, kBlock, 0, st>>>(n, ld, sptr, col, pat, v, uu, ww, rr,
+                                                                                yy, c, Sm);
     return cudaGetLastError();
 }
 
 template <typename VT, typename XT, typename YT>
-cudaError_t mstep_launch(int n, int m, int ld, const int32_t* sptr, const int32_t* col, const void* val,
+cudaError_t mstep_launch(int n, int m, int ld, const int32_t* sptr, const int32_t* col, const SellPat& pat,
+                         const void* val,
                          const void* u, const void* w, const void* r, void* y, double ca, double cb, double cc,
                          double cd, const PcgScalars* Sm, cudaStream_t st) {
 #define NC_MSTEP(MM) \
-    case MM: return mstep_launch_m<VT, XT, YT, MM>(n, ld, sptr, col, val, u, w, r, y, ca, cb, cc, cd, Sm, st);
+    case MM: return mstep_launch_m<VT, XT, YT, MM>(n, ld, sptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, Sm, st);
     switch (m) {
         NC_MSTEP(1) NC_MSTEP(2) NC_MSTEP(3) NC_MSTEP(4) NC_MSTEP(5) NC_MSTEP(6) NC_MSTEP(7) NC_MSTEP(8)
     default: return cudaErrorInvalidValue;
@@ -122,27 +152,24 @@ cudaError_t mstep_launch(int n, int m, int ld, const int32_t* sptr, const int32_
 
 int max_rhs() { return kMaxRhs; }
 
-cudaError_t launch_sell_mstep(int n, int m, int ld, const int32_t* slice_ptr, const int32_t* col, const void* val,
-                              int vdt, bool x_f32, bool y_f64, const void* u, const void* w, const void* r,
-                              void* y, double ca, double cb, double cc, double cd, const PcgScalars* Sm,
-                              cudaStream_t st) {
+cudaError_t launch_sell_mstep(int n, int m, int ld, const int32_t* slice_ptr, const int32_t* col, const SellPat& pat,
+                              const void* val, int vdt, bool x_f32, bool y_f64, const void* u, const void* w,
+                              const void* r, void* y, double ca, double cb, double cc, double cd,
+                              const PcgScalars* Sm, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     if (m < 1 || m > kMaxRhs) return cudaErrorInvalidValue;
+#define NC_MSTEP_ARGS n, m, ld, slice_ptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, Sm, st
     if (!x_f32) {
         if (vdt != NC_F64) return cudaErrorInvalidValue;
-        return mstep_launch<double, double, double>(n, m, ld, slice_ptr, col, val, u, w, r, y, ca, cb, cc, cd, Sm,
-                                                    st);
+        return mstep_launch<double, double, double>(NC_MSTEP_ARGS);
     }
     if (vdt == NC_F32)
-        return y_f64 ? mstep_launch<float, float, double>(n, m, ld, slice_ptr, col, val, u, w, r, y, ca, cb, cc, cd,
-                                                          Sm, st)
-                     : mstep_launch<float, float, float>(n, m, ld, slice_ptr, col, val, u, w, r, y, ca, cb, cc, cd,
-                                                         Sm, st);
+        return y_f64 ? mstep_launch<float, float, double>(NC_MSTEP_ARGS)
+                     : mstep_launch<float, float, float>(NC_MSTEP_ARGS);
     if (vdt == NC_BF16)
-        return y_f64 ? mstep_launch<__nv_bfloat16, float, double>(n, m, ld, slice_ptr, col, val, u, w, r, y, ca, cb,
-                                                                  cc, cd, Sm, st)
-                     : mstep_launch<__nv_bfloat16, float, float>(n, m, ld, slice_ptr, col, val, u, w, r, y, ca, cb,
-                                                                 cc, cd, Sm, st);
+        return y_f64 ? mstep_launch<__nv_bfloat16, float, double>(NC_MSTEP_ARGS)
+                     : mstep_launch<__nv_bfloat16, float, float>(NC_MSTEP_ARGS);
+#undef NC_MSTEP_ARGS
     return cudaErrorInvalidValue;
 }
 

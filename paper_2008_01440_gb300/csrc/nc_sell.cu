@@ -20,6 +20,8 @@
 // Chebyshev step after the first needs no separate x_{k-1} term, one FP64
 // instruction less per row on GB300's narrow FP64 pipe; the outer products
 // add theta' u back (q = A' p + theta' p).
+#include <climits>
+
 #include "nc_step.cuh"
 
 namespace nc {
@@ -28,11 +30,14 @@ namespace {
 constexpr int kSellGroup = 8;
 
 // One row: the slot loop and the epilogue; returns the row's dot term.
-template <typename VT, typename XT, typename YT, int DOT>
-__device__ __forceinline__ double sell_row(const int row, const int32_t* __restrict__ slice_ptr,
-                                           const int32_t* __restrict__ col, const VT* __restrict__ val,
-                                           const XT* __restrict__ u, const XT* __restrict__ w,
-                                           const XT* __restrict__ r, YT* __restrict__ y,
+// PAT: the slice's columns are row + its pattern's offsets (clamped to the
+// matrix, for padded slots whose offset leaves it; their value is 0), not
+// loaded from `col`.
+template <typename VT, typename XT, typename YT, int DOT, bool PAT, bool UNIT>
+__device__ __forceinline__ double sell_row(const int row, const int n, const int32_t* __restrict__ slice_ptr,
+                                           const int32_t* __restrict__ col, const SellPat& pat,
+                                           const VT* __restrict__ val, const XT* __restrict__ u,
+                                           const XT* __restrict__ w, const XT* __restrict__ r, YT* __restrict__ y,
                                            const StepCoef<typename AccOf<XT>::type>& c,
                                            const double* __restrict__ rdot) {
     using AT = typename AccOf<XT>::type;
@@ -40,7 +45,20 @@ __device__ __forceinline__ double sell_row(const int row, const int32_t* __restr
     const int beg = slice_ptr[s];
     const int len = (slice_ptr[s + 1] - beg) >> 5;   // warp-uniform
     const VT* vp = val + beg + (row & 31);
-    const int32_t* cp = col + beg + (row & 31);
+    const int32_t* cp = nullptr;   // plain: the slot's column indices
+    const int32_t* op = nullptr;   // PAT: the slice's offsets
+    if constexpr (PAT) op = pat.poff + __ldg(pat.pstart + s);
+    else cp = col + beg + (row & 31);
+    // column of slot t of the current group
+    auto colt = [&](int t) -> int {
+        if constexpr (PAT) return min(max(row + __ldg(op + t), 0), n - 1);
+        else return ld_stream(cp + 32 * t);
+    };
+    auto advance = [&](int g) {
+        vp += 32 * g;
+        if constexpr (PAT) op += g;
+        else cp += 32 * g;
+    };
     AT acc = AT(0);
     if constexpr (sizeof(AT) == 8) {
         // float64: the fma chain itself is long-latency on GB300's narrow
@@ -48,8 +66,7 @@ __device__ __forceinline__ double sell_row(const int row, const int32_t* __restr
         // kernel at 32 registers and 8 CTAs (2048 threads) per SM.
         int j = 0;
         for (; j + 4 <= len; j += 4) {
-            const int c0 = ld_stream(cp), c1 = ld_stream(cp + 32), c2 = ld_stream(cp + 64),
-                      c3 = ld_stream(cp + 96);
+            const int c0 = colt(0), c1 = colt(1), c2 = colt(2), c3 = colt(3);
             const AT v0 = (AT)ld_stream(vp), v1 = (AT)ld_stream(vp + 32), v2 = (AT)ld_stream(vp + 64),
                      v3 = (AT)ld_stream(vp + 96);
             const AT x0 = (AT)__ldg(u + c0), x1 = (AT)__ldg(u + c1), x2 = (AT)__ldg(u + c2),
@@ -58,14 +75,12 @@ __device__ __forceinline__ double sell_row(const int row, const int32_t* __restr
             acc = fma(v1, x1, acc);
             acc = fma(v2, x2, acc);
             acc = fma(v3, x3, acc);
-            vp += 128;
-            cp += 128;
+            advance(4);
         }
         for (; j < len; ++j) {
-            const int c0 = ld_stream(cp);
+            const int c0 = colt(0);
             acc = fma((AT)ld_stream(vp), (AT)__ldg(u + c0), acc);
-            vp += 32;
-            cp += 32;
+            advance(1);
         }
     } else {
         // float: memory latency is the limit, so every column and value
@@ -79,7 +94,7 @@ __device__ __forceinline__ double sell_row(const int row, const int32_t* __restr
 #pragma unroll
             for (int t = 0; t < G; ++t)
                 if (j0 + t < len) {
-                    cc_[t] = ld_stream(cp + 32 * t);
+                    cc_[t] = colt(t);
                     vv[t] = (AT)ld_stream(vp + 32 * t);
                 }
 #pragma unroll
@@ -88,26 +103,25 @@ __device__ __forceinline__ double sell_row(const int row, const int32_t* __restr
 #pragma unroll
             for (int t = 0; t < G; ++t)
                 if (j0 + t < len) acc = fma(vv[t], xx[t], acc);
-            vp += 32 * G;
-            cp += 32 * G;
+            advance(G);
         }
     }
-    return step_row_out<XT, YT, DOT, AT>(row, acc, c, u, w, r, y, rdot);
+    return step_row_out<XT, YT, DOT, AT, UNIT>(row, acc, c, u, w, r, y, rdot);
 }
 
-template <typename VT, typename XT, typename YT, int DOT>
+template <typename VT, typename XT, typename YT, int DOT, bool PAT, bool UNIT>
 __global__ void __launch_bounds__(kBlock)
 sell_step_kernel(const int n, const int32_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
-                 const VT* __restrict__ val, const XT* __restrict__ u, const XT* __restrict__ w,
+                 const SellPat pat, const VT* __restrict__ val, const XT* __restrict__ u, const XT* __restrict__ w,
                  const XT* __restrict__ r, YT* __restrict__ y, const StepCoef<typename AccOf<XT>::type> c,
                  const double* __restrict__ rdot, const Reduce R, const int* __restrict__ done) {
     if (done != nullptr && *done) return;
     if constexpr (DOT == 0) {
         // one 256-row tile per CTA
         if constexpr (sizeof(typename AccOf<XT>::type) == 4)
-            if (threadIdx.x == 0) prefetch_sell_tile((int)blockIdx.x + kPrefetchAhead, n, slice_ptr, col, val);
+            if (threadIdx.x == 0) prefetch_sell_tile((int)blockIdx.x + kPrefetchAhead, n, slice_ptr, PAT ? nullptr : col, val);
         const int row = blockIdx.x * kBlock + threadIdx.x;
-        if (row < n) sell_row<VT, XT, YT, 0>(row, slice_ptr, col, val, u, w, r, y, c, rdot);
+        if (row < n) sell_row<VT, XT, YT, 0, PAT, UNIT>(row, n, slice_ptr, col, pat, val, u, w, r, y, c, rdot);
     } else {
         // with a dot product: a persistent grid loops over the tiles and
         // reduces once per CTA
@@ -115,9 +129,10 @@ sell_step_kernel(const int n, const int32_t* __restrict__ slice_ptr, const int32
         const int ntiles = (n + kBlock - 1) / kBlock;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             if constexpr (sizeof(typename AccOf<XT>::type) == 4)
-                if (threadIdx.x == 0) prefetch_sell_tile(tile + (int)gridDim.x, n, slice_ptr, col, val);
+                if (threadIdx.x == 0) prefetch_sell_tile(tile + (int)gridDim.x, n, slice_ptr, PAT ? nullptr : col, val);
             const int row = tile * kBlock + threadIdx.x;
-            if (row < n) dv += sell_row<VT, XT, YT, DOT>(row, slice_ptr, col, val, u, w, r, y, c, rdot);
+            if (row < n)
+                dv += sell_row<VT, XT, YT, DOT, PAT, UNIT>(row, n, slice_ptr, col, pat, val, u, w, r, y, c, rdot);
         }
         grid_reduce<kBlock>(dv, R);
     }
@@ -178,10 +193,101 @@ __global__ void sell_fill_kernel(int n, const int32_t* __restrict__ rowptr, cons
     if (row < n && !has_diag && shift != 0.0 && nodiag != nullptr) atomicOr(nodiag, 1);
 }
 
-template <typename VT, typename XT, typename YT>
-cudaError_t sell_dispatch(int n, const int32_t* sptr, const int32_t* col, const void* val, const void* u,
-                          const void* w, const void* r, void* y, double ca, double cb, double cc, double cd,
-                          int dot, const double* rdot, const Reduce& R, const int* done, cudaStream_t st) {
+// Offset patterns.  The columns of a row of a regularly numbered grid are
+// row + a few fixed offsets; a slice of 32 such rows shares one sorted set of
+// offsets (col - row), and all interior slices share the same set.  The
+// pattern layout stores each distinct set once and per slice only where its
+// set starts, so a step reads no column indices: 4 bytes less per stored
+// entry and no dependent column load before the gathers.  Rows that lack an
+// offset of their slice's set (faces of the grid) hold a 0 there.
+
+// Merge of one slice's 32 sorted rows of offsets into its set, one warp per
+// slice: each round takes the warp's smallest pending offset (an offset a row
+// repeats counts once per repetition), so a slice holding L entries ends
+// after at most L rounds.  Counting pass (off null): cnt[s].  Writing pass:
+// off[opos[s] + j].  *bad is set if a row's columns do not increase or a
+// slice needs more than kPatMaxSlots offsets.
+constexpr int kPatMaxSlots = 64;
+
+__global__ void psell_merge_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                   const int32_t* __restrict__ opos, int32_t* __restrict__ cnt,
+                                   int32_t* __restrict__ off, int* __restrict__ bad) {
+    const int s = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    const int nslices = (n + 31) >> 5;
+    if (s >= nslices) return;   // warp-uniform
+    const int row = s * 32 + lane;
+    int pos = 0, end = 0;
+    if (row < n) {
+        pos = rowptr[row];
+        end = rowptr[row + 1];
+    }
+    const int base = off != nullptr ? opos[s] : 0;
+    int last = INT_MIN, c = 0;
+    bool fail = false;
+    while (true) {
+        const int my = pos < end ? col[pos] - row : INT_MAX;
+        int m = my;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (m == INT_MAX) break;
+        if (c >= kPatMaxSlots) {
+            fail = true;
+            break;
+        }
+        if (off != nullptr && lane == 0) off[base + c] = m;
+        if (my == m) {
+            if (my < last) fail = true;
+            last = my;
+            ++pos;
+        }
+        ++c;
+    }
+    if (__any_sync(0xffffffffu, fail) && lane == 0) atomicOr(bad, 1);
+    if (off == nullptr && lane == 0) cnt[s] = c;
+}
+
+// Slot-major fill of the pattern layout: slot j of a row holds its entry at
+// column row + offset j, or 0; diagonal entries stored as a_ii - shift.
+template <typename VT>
+__global__ void psell_fill_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                  const double* __restrict__ val, const int32_t* __restrict__ slice_ptr,
+                                  const int32_t* __restrict__ pstart, const int32_t* __restrict__ poff, double shift,
+                                  VT* __restrict__ sval, int* __restrict__ nodiag) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nslices = (n + 31) >> 5;
+    if ((row >> 5) >= nslices) return;
+    const int s = row >> 5;
+    const int beg = slice_ptr[s] + (row & 31);
+    const int len = (slice_ptr[s + 1] - slice_ptr[s]) >> 5;
+    const int32_t* op = poff + pstart[s];
+    int pos = 0, end = 0;
+    if (row < n) {
+        pos = rowptr[row];
+        end = rowptr[row + 1];
+    }
+    bool has_diag = false;
+    for (int j = 0; j < len; ++j) {
+        const int o = op[j];
+        double v = 0.0;
+        if (pos < end && col[pos] - row == o) {
+            v = val[pos];
+            if (o == 0) {
+                v -= shift;
+                has_diag = true;
+            }
+            ++pos;
+        }
+        put_val(&sval[beg + 32 * j], v);
+    }
+    if (row < n && !has_diag && shift != 0.0 && nodiag != nullptr) atomicOr(nodiag, 1);
+}
+
+template <typename VT, typename XT, typename YT, bool PAT, bool UNIT>
+cudaError_t sell_dispatch_pu(int n, const int32_t* sptr, const int32_t* col, const SellPat& pat, const void* val,
+                             const void* u, const void* w, const void* r, void* y, double ca, double cb, double cc,
+                             double cd, int dot, const double* rdot, const Reduce& R, const int* done,
+                             cudaStream_t st) {
     using AT = typename AccOf<XT>::type;
     const int tiles = (n + kBlock - 1) / kBlock;
     const int grid = (dot == 0 || tiles < kRedGrid) ? tiles : kRedGrid;
@@ -191,46 +297,62 @@ cudaError_t sell_dispatch(int n, const int32_t* sptr, const int32_t* col, const 
     const XT* ww = static_cast<const XT*>(w);
     const XT* rr = static_cast<const XT*>(r);
     YT* yy = static_cast<YT*>(y);
+#define NC_SELL_KARGS n, sptr, col, pat, v, uu, ww, rr, yy, c, rdot, R, done
     switch (dot) {
-    case 0:
-        sell_step_kernel<VT, XT, YT, 0><<<grid, kBlock, 0, st>>>(n, sptr, col, v, uu, ww, rr, yy, c, rdot, R, done);
-        break;
-    case 1:
-        sell_step_kernel<VT, XT, YT, 1><<<grid, kBlock, 0, st>>>(n, sptr, col, v, uu, ww, rr, yy, c, rdot, R, done);
-        break;
-    default:
-        sell_step_kernel<VT, XT, YT, 2><<<grid, kBlock, 0, st>>>(n, sptr, col, v, uu, ww, rr, yy, c, rdot, R, done);
-        break;
+    case 0: sell_step_kernel<VT, XT, YT, 0, PAT, UNIT><<<grid, kBlock, 0, st>>>(NC_SELL_KARGS); break;
+    case 1: sell_step_kernel<VT, XT, YT, 1, PAT, UNIT><<<grid, kBlock, 0, st>>>(NC_SELL_KARGS); break;
+    default: sell_step_kernel<VT, XT, YT, 2, PAT, UNIT><<<grid, kBlock, 0, st>>>(NC_SELL_KARGS); break;
     }
+#undef NC_SELL_KARGS
     return cudaGetLastError();
+}
+
+// float64 steps whose product coefficient is exactly 1 (the scaled iterates,
+// q = A p) run a kernel without the multiply
+template <typename VT, typename XT, typename YT, bool PAT>
+cudaError_t sell_dispatch_p(int n, const int32_t* sptr, const int32_t* col, const SellPat& pat, const void* val,
+                            const void* u, const void* w, const void* r, void* y, double ca, double cb, double cc,
+                            double cd, int dot, const double* rdot, const Reduce& R, const int* done,
+                            cudaStream_t st) {
+    if constexpr (sizeof(typename AccOf<XT>::type) == 8) {
+        if (cd == 1.0)
+            return sell_dispatch_pu<VT, XT, YT, PAT, true>(n, sptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, dot,
+                                                           rdot, R, done, st);
+    }
+    return sell_dispatch_pu<VT, XT, YT, PAT, false>(n, sptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, dot, rdot, R,
+                                                    done, st);
+}
+
+template <typename VT, typename XT, typename YT>
+cudaError_t sell_dispatch(int n, const int32_t* sptr, const int32_t* col, const SellPat& pat, const void* val,
+                          const void* u, const void* w, const void* r, void* y, double ca, double cb, double cc,
+                          double cd, int dot, const double* rdot, const Reduce& R, const int* done, cudaStream_t st) {
+    if (pat.pstart != nullptr)
+        return sell_dispatch_p<VT, XT, YT, true>(n, sptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, dot, rdot, R,
+                                                 done, st);
+    return sell_dispatch_p<VT, XT, YT, false>(n, sptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done,
+                                              st);
 }
 
 }  // namespace
 
-cudaError_t launch_sell_step(int n, const int32_t* slice_ptr, const int32_t* col, const void* val, int vdt,
-                             bool x_f32, bool y_f64, const void* u, const void* w, const void* r, void* y,
-                             double ca, double cb, double cc, double cd, int dot, const double* rdot,
-                             const Reduce& R, const int* done, cudaStream_t st) {
+cudaError_t launch_sell_step(int n, const int32_t* slice_ptr, const int32_t* col, const SellPat& pat,
+                             const void* val, int vdt, bool x_f32, bool y_f64, const void* u, const void* w,
+                             const void* r, void* y, double ca, double cb, double cc, double cd, int dot,
+                             const double* rdot, const Reduce& R, const int* done, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
+#define NC_SELL_ARGS n, slice_ptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done, st
     if (!x_f32) {
         if (vdt != NC_F64) return cudaErrorInvalidValue;
-        return sell_dispatch<double, double, double>(n, slice_ptr, col, val, u, w, r, y, ca, cb, cc, cd, dot, rdot,
-                                                     R, done, st);
+        return sell_dispatch<double, double, double>(NC_SELL_ARGS);
     }
-    if (vdt == NC_F32) {
-        if (y_f64)
-            return sell_dispatch<float, float, double>(n, slice_ptr, col, val, u, w, r, y, ca, cb, cc, cd, dot,
-                                                       rdot, R, done, st);
-        return sell_dispatch<float, float, float>(n, slice_ptr, col, val, u, w, r, y, ca, cb, cc, cd, dot, rdot, R,
-                                                  done, st);
-    }
-    if (vdt == NC_BF16) {
-        if (y_f64)
-            return sell_dispatch<__nv_bfloat16, float, double>(n, slice_ptr, col, val, u, w, r, y, ca, cb, cc, cd,
-                                                               dot, rdot, R, done, st);
-        return sell_dispatch<__nv_bfloat16, float, float>(n, slice_ptr, col, val, u, w, r, y, ca, cb, cc, cd, dot,
-                                                          rdot, R, done, st);
-    }
+    if (vdt == NC_F32)
+        return y_f64 ? sell_dispatch<float, float, double>(NC_SELL_ARGS)
+                     : sell_dispatch<float, float, float>(NC_SELL_ARGS);
+    if (vdt == NC_BF16)
+        return y_f64 ? sell_dispatch<__nv_bfloat16, float, double>(NC_SELL_ARGS)
+                     : sell_dispatch<__nv_bfloat16, float, float>(NC_SELL_ARGS);
+#undef NC_SELL_ARGS
     return cudaErrorInvalidValue;
 }
 
@@ -257,6 +379,34 @@ cudaError_t launch_sell_fill(int n, const int32_t* rowptr, const int32_t* col, c
     else if (vdt == NC_BF16)
         sell_fill_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, shift, scol,
                                                               static_cast<__nv_bfloat16*>(sval), nodiag);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psell_merge(int n, const int32_t* rowptr, const int32_t* col, const int32_t* opos, int32_t* cnt,
+                               int32_t* off, int* bad, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const long long threads = (long long)((n + 31) / 32) * 32;
+    psell_merge_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, rowptr, col, opos, cnt, off, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psell_fill(int n, const int32_t* rowptr, const int32_t* col, const double* val,
+                              const int32_t* slice_ptr, const int32_t* pstart, const int32_t* poff, int vdt,
+                              double shift, void* sval, int* nodiag, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int threads = ((n + 31) / 32) * 32;
+    const int grid = (threads + 255) / 256;
+    if (vdt == NC_F64)
+        psell_fill_kernel<double><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, pstart, poff, shift,
+                                                        static_cast<double*>(sval), nodiag);
+    else if (vdt == NC_F32)
+        psell_fill_kernel<float><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, pstart, poff, shift,
+                                                       static_cast<float*>(sval), nodiag);
+    else if (vdt == NC_BF16)
+        psell_fill_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, pstart, poff, shift,
+                                                               static_cast<__nv_bfloat16*>(sval), nodiag);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -26,7 +26,7 @@ __device__ __forceinline__ float ld_stream(const __nv_bfloat16* p) {
 }
 __device__ __forceinline__ int ld_stream(const int32_t* p) { return __ldcs(p); }
 
-// L2 prefetch of the SELL-32 slices (columns and values) of 256-row tile t,
+// L2 prefetch of the SELL-32 slices (columns, unless null, and values) of 256-row tile t,
 // issued by one thread: cp.async.bulk.prefetch is a hint that holds no
 // registers and has nothing to wait for.  Slice offsets are multiples of 32
 // entries, so both ranges start and end on 16-byte boundaries.  The float
@@ -44,8 +44,9 @@ __device__ __forceinline__ void prefetch_sell_tile(int t, int n, const int32_t* 
     if (t < 0 || s0 >= nslices) return;
     const int b = slice_ptr[s0], e = slice_ptr[min(s0 + kBlock / 32, nslices)];
     if (e <= b) return;
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(col + b),
-                 "r"((uint32_t)(e - b) * (uint32_t)sizeof(int32_t)) : "memory");
+    if (col != nullptr)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(col + b),
+                     "r"((uint32_t)(e - b) * (uint32_t)sizeof(int32_t)) : "memory");
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(val + b),
                  "r"((uint32_t)(e - b) * (uint32_t)sizeof(VT)) : "memory");
 }
@@ -71,13 +72,18 @@ inline StepCoef<AT> make_coef(double ca, double cb, double cc, double cd) {
     return c;
 }
 
-// Row epilogue: returns the dot-product contribution of this row.
-template <typename XT, typename YT, int DOT, typename AT>
+// Row epilogue: returns the dot-product contribution of this row (DOT: 0
+// none, 1 (rdot, y), 2 (u, y)).  UNIT: cd == 1, the product taken as it is
+// -- a compile-time case, since a runtime test of kUnitD is if-converted and
+// the multiply issued anyway.
+template <typename XT, typename YT, int DOT, typename AT, bool UNIT = false>
 __device__ __forceinline__ double step_row_out(int row, AT acc, const StepCoef<AT>& c,
                                                const XT* __restrict__ u, const XT* __restrict__ w,
                                                const XT* __restrict__ r, YT* __restrict__ y,
                                                const double* __restrict__ rdot) {
-    AT o = (c.terms & kUnitD) ? acc : c.cd * acc;
+    AT o;
+    if constexpr (UNIT) o = acc;
+    else o = (c.terms & kUnitD) ? acc : c.cd * acc;
     if (c.terms & kTermR) o = fma(c.cc, (AT)r[row], o);
     if (c.terms & kTermW) o = fma(c.cb, (AT)w[row], o);
     if (c.terms & kTermU) o = fma(c.ca, (AT)u[row], o);

@@ -52,7 +52,7 @@ def test_matvec_and_jacobi_parity(env):
     assert g == gershgorin_np(As.rowptr, As.col, As.val, A.n) or abs(g - gershgorin_np(As.rowptr, As.col, As.val, A.n)) < 1e-14
 
 
-FORMATS = ["csr", "sell"]
+FORMATS = ["csr", "sell", "psell"]
 
 
 @pytest.mark.parametrize("fmt", FORMATS)
@@ -94,15 +94,20 @@ def test_apply_poly_diffusion_lanczos_bounds(env, N, k, fmt):
 
 
 def test_auto_layout_choice(env):
-    """AUTO picks SELL-32 for a grid operator (small padding) and CSR for a
-    matrix with one dense row (padding far above 1.5)."""
+    """AUTO picks the offset-pattern layout for a grid operator (small
+    padding, few distinct offset sets), SELL-32 when forced or in the cluster
+    solve, and CSR for a matrix with one dense row (padding far above 1.5)."""
     torch, nc = env
     A = W.diffusion_3d_7pt_lognormal(20, seed=1)
     S = nc.pcg_setup(csr_to_gpu(torch, nc, A), 0.1, 2.0, 4, 1.0)
     info = nc.pcg_get_info(S)
-    assert info["spmv_format"] == "sell" and 1.0 <= info["padding"] < 1.2
-    # SELL stores the shifted operator A - theta' I (every row has a diagonal)
+    assert info["spmv_format"] == "psell" and 1.0 <= info["padding"] < 1.2
+    # interior, and one set per combination of missing faces: at most 3^2 x 2
+    assert 1 <= info["patterns"] <= 18
+    # the sliced layouts store the shifted operator A - theta' I (every row has a diagonal)
     assert info["shift"] == info["theta"] == 1.0 * (0.1 + 2.0) / 2
+    info = nc.pcg_get_info(nc.pcg_setup(csr_to_gpu(torch, nc, A), 0.1, 2.0, 4, 1.0, spmv_format="sell"))
+    assert info["spmv_format"] == "sell" and info["patterns"] == 0 and 1.0 <= info["padding"] < 1.2
     n = 2000
     rows = [np.array([i]) for i in range(n)]
     rows[7] = np.arange(n)

@@ -20,7 +20,7 @@ def env():
 
 
 @pytest.mark.parametrize("bad", [float("nan"), float("inf")])
-@pytest.mark.parametrize("fmt", ["csr", "sell"])
+@pytest.mark.parametrize("fmt", ["csr", "sell", "psell"])
 def test_nonfinite_rhs_breaks_down_and_solver_recovers(env, bad, fmt):
     torch, nc = env
     A = W.laplacian_2d_5pt(64, 64)

@@ -42,7 +42,7 @@ def test_fullsize_lanczos_bounds(system):
 def test_fullsize_solve_iterations(system, k):
     torch, nc, g, A, M0, M = system
     S = nc.pcg_setup(M, g["lmin"], g["lmax"], k, g["theta_scale"], x0_is_zero=True)
-    assert nc.pcg_get_info(S)["spmv_format"] == "sell"
+    assert nc.pcg_get_info(S)["spmv_format"] == "psell"
     b = to_dev(torch, W.uniform_vector(A.n, seed=g["seed_rhs"]))
     x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
     res = nc.pcg_solve(S, b, x, g["tol"], 5000)
@@ -59,8 +59,9 @@ def test_fullsize_apply_parity(system):
     mv = O.csr_matvec(A.rowptr, A.col, val, A.n)
     v = W.uniform_vector(A.n, seed=21)
     ref = O.cheb_apply(mv, v, O.cheb_params(g["lmin"], g["lmax"], g["theta_scale"]), k)
-    for fmt in ("sell", "csr"):
+    for fmt in ("psell", "sell", "csr"):
         S = nc.pcg_setup(M, g["lmin"], g["lmax"], k, g["theta_scale"], spmv_format=fmt)
+        assert nc.pcg_get_info(S)["spmv_format"] == fmt
         z = torch.empty(A.n, dtype=torch.float64, device="cuda")
         nc.pcg_apply_poly(S, to_dev(torch, v), z)
         got = z.cpu().numpy()

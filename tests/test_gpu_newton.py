@@ -37,7 +37,7 @@ def newton_ref(A, lo, hi, s, nlev, v):
     return O.newton_apply(O.csr_matvec(A.rowptr, A.col, A.val, A.n), v, z, nlev)
 
 
-@pytest.mark.parametrize("fmt", ["csr", "sell"])
+@pytest.mark.parametrize("fmt", ["csr", "sell", "psell"])
 @pytest.mark.parametrize("nlev", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("s", [1.0, 1.001])
 def test_newton_apply_matches_oracle(env, nlev, s, fmt):
