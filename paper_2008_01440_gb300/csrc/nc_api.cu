@@ -86,6 +86,7 @@ struct nc_solver_s {
     double padding = 1.0;                 // SELL stored entries / nnz
     double tune_us[2] = {0.0, 0.0};       // measured step time, plain / sliced layout (TUNE)
     double shift = 0.0;                   // op values hold A - shift*I (theta' for SELL, else 0)
+    double pscale = 1.0;                  // opP holds A / pscale (a stencil: its x-weight), else 1
     void* lval = nullptr;                 // converted CSR values (F32/BF16), owned
     int32_t* sell_ptr = nullptr;          // SELL-32 arrays, owned
     int32_t* sell_col = nullptr;
@@ -327,12 +328,15 @@ std::vector<StepC> step_coefs(const nc_solver S) {
     const int k = S->k;
     std::vector<StepC> out(k + 1, StepC{0.0, 0.0, 0.0, 0.0});
     std::vector<double> g(k + 1, 1.0);
+    // a stencil inside P is stored divided by its x-weight kap (A = kap A^),
+    // so the coefficient of its product is cd kap
+    const double kap = S->pscale;
     for (int j = 1; j <= k; ++j) {
         double ca = S->ca[j];
         if (S->shift != 0.0) ca = (j == 1) ? S->ca1_shifted : 0.0;
         const double gu = (j == 1) ? 1.0 : g[j - 1];   // scale of u (r at step 1)
         const double gw = (j >= 3) ? g[j - 2] : 1.0;   // scale of w = y_{j-2}
-        const double t = S->cd[j] * gu;
+        const double t = S->cd[j] * kap * gu;
         const bool unit = !S->mixed && j < k && std::fabs(t) >= 0x1p-64 && std::fabs(t) <= 0x1p64;
         g[j] = unit ? t : 1.0;
         out[j].ca = ca * gu / g[j];
@@ -1037,6 +1041,17 @@ nc_status setup_operator(nc_solver S, cudaStream_t st) {
         S->opP.vdt = S->vdt;
         S->padding = 1.0;
         S->shift = 0.0;
+        // inside P the stencil is taken divided by its x-weight, which then
+        // is exactly 1: with the scaled float64 iterates the step's
+        // x-coefficient is exactly -1 and the kernel skips a multiply
+        const double kap = S->op64.c4[1];
+        if (kap != 0.0 && std::isfinite(kap) && std::isfinite(1.0 / kap)) {
+            S->pscale = kap;
+            S->opP.c4[0] = S->op64.c4[0] / kap;
+            S->opP.c4[1] = 1.0;
+            S->opP.c4[2] = S->op64.c4[2] / kap;
+            S->opP.c4[3] = S->op64.c4[3] / kap;
+        }
         return NC_OK;
     }
     const size_t eb = S->vdt == NC_F64 ? 8 : (S->vdt == NC_F32 ? 4 : 2);

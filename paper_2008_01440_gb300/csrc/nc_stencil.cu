@@ -23,7 +23,7 @@
 namespace nc {
 namespace {
 
-template <typename XT, typename YT, int DOT>
+template <typename XT, typename YT, int DOT, bool XU>
 __global__ void __launch_bounds__(kTX * kTY)
 stencil7_step_kernel(const int nx, const int ny, const int nz, const int zchunk, const XT* __restrict__ u,
                      const XT* __restrict__ w, const XT* __restrict__ r, YT* __restrict__ y,
@@ -32,7 +32,7 @@ stencil7_step_kernel(const int nx, const int ny, const int nz, const int zchunk,
     if (done != nullptr && *done) return;
     const int k0 = blockIdx.z * zchunk;
     const int k1 = min(k0 + zchunk, nz);
-    const double dv = stencil_tile<XT, YT, DOT>(nx, ny, nz, blockIdx.x, blockIdx.y, k0, k1, u, w, r, y, c, rdot,
+    const double dv = stencil_tile<XT, YT, DOT, XU>(nx, ny, nz, blockIdx.x, blockIdx.y, k0, k1, u, w, r, y, c, rdot,
                                                 threadIdx.x, threadIdx.y);
     if (DOT != 0) {
         const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
@@ -61,17 +61,25 @@ cudaError_t stencil_dispatch(const StencilGeom& g, const double* c4, const void*
     const XT* ww = static_cast<const XT*>(w);
     const XT* rr = static_cast<const XT*>(r);
     YT* yy = static_cast<YT*>(y);
-    switch (dot) {
-    case 0:
-        stencil7_step_kernel<XT, YT, 0><<<grid, block, 0, st>>>(g.nx, g.ny, g.nz, zc, uu, ww, rr, yy, c, rdot, R, done);
-        break;
-    case 1:
-        stencil7_step_kernel<XT, YT, 1><<<grid, block, 0, st>>>(g.nx, g.ny, g.nz, zc, uu, ww, rr, yy, c, rdot, R, done);
-        break;
-    default:
-        stencil7_step_kernel<XT, YT, 2><<<grid, block, 0, st>>>(g.nx, g.ny, g.nz, zc, uu, ww, rr, yy, c, rdot, R, done);
-        break;
+#define NC_ST_ARGS g.nx, g.ny, g.nz, zc, uu, ww, rr, yy, c, rdot, R, done
+    // float64 with ex == -1 exactly (a normalised operator with scaled
+    // iterates, or cx = 1 with cd = 1): the kernel without the centre multiply
+    if constexpr (sizeof(AT) == 8) {
+        if (c.ex == -1.0) {
+            switch (dot) {
+            case 0: stencil7_step_kernel<XT, YT, 0, true><<<grid, block, 0, st>>>(NC_ST_ARGS); break;
+            case 1: stencil7_step_kernel<XT, YT, 1, true><<<grid, block, 0, st>>>(NC_ST_ARGS); break;
+            default: stencil7_step_kernel<XT, YT, 2, true><<<grid, block, 0, st>>>(NC_ST_ARGS); break;
+            }
+            return cudaGetLastError();
+        }
     }
+    switch (dot) {
+    case 0: stencil7_step_kernel<XT, YT, 0, false><<<grid, block, 0, st>>>(NC_ST_ARGS); break;
+    case 1: stencil7_step_kernel<XT, YT, 1, false><<<grid, block, 0, st>>>(NC_ST_ARGS); break;
+    default: stencil7_step_kernel<XT, YT, 2, false><<<grid, block, 0, st>>>(NC_ST_ARGS); break;
+    }
+#undef NC_ST_ARGS
     return cudaGetLastError();
 }
 

@@ -25,7 +25,10 @@ struct StencilCoef {
 // before any of the batch's arithmetic, so a batch costs one memory latency
 // rather than one per plane.  u at the planes below and at the current plane
 // stay in registers across batches.
-template <typename XT, typename YT, int DOT>
+// XU: ex == -1 exactly (the stored operator normalised by its x-weight and
+// the iterates scaled so the product's coefficient is 1): the step starts
+// from -(x-neighbours) and needs no multiply for the centre.
+template <typename XT, typename YT, int DOT, bool XU = false>
 __device__ __forceinline__ double stencil_tile(const int nx, const int ny, const int nz, const int bx, const int by,
                                                const int k0, const int k1, const XT* __restrict__ u,
                                                const XT* __restrict__ w, const XT* __restrict__ r,
@@ -71,8 +74,13 @@ __device__ __forceinline__ double stencil_tile(const int nx, const int ny, const
             if (lane == kTX - 1) xp = xe[t];
             if (in) {
                 const long long q = idx + t * plane;
-                AT o = c.e0 * u_cur;
-                o = fma(c.ex, xm + xp, o);
+                AT o;
+                if constexpr (XU) {
+                    o = fma(c.e0, u_cur, -(xm + xp));
+                } else {
+                    o = c.e0 * u_cur;
+                    o = fma(c.ex, xm + xp, o);
+                }
                 o = fma(c.ey, ym[t] + yp[t], o);
                 o = fma(c.ez, u_prev + u_next, o);
                 if (has_r) o = fma(c.cc, rv[t], o);
