@@ -28,16 +28,19 @@ struct StencilCoef {
 // XU: ex == -1 exactly (the stored operator normalised by its x-weight and
 // the iterates scaled so the product's coefficient is 1): the step starts
 // from -(x-neighbours) and needs no multiply for the centre.
-template <typename XT, typename YT, int DOT, bool XU = false>
+//
+// PZ: planes per z-march batch.  Measured on the float32 step: 2 planes are
+// best for short z-chunks (511^3, 32-plane chunks: 388 us against 410 with 4),
+// 4 planes for long ones (1023^3, 205-plane chunks: 3316 us against 3481);
+// float64 takes 2.
+template <typename XT, typename YT, int DOT, bool XU = false, int PZ = 2>
 __device__ __forceinline__ double stencil_tile(const int nx, const int ny, const int nz, const int bx, const int by,
                                                const int k0, const int k1, const XT* __restrict__ u,
                                                const XT* __restrict__ w, const XT* __restrict__ r,
                                                YT* __restrict__ y, const StencilCoef<typename AccOf<XT>::type>& c,
                                                const double* __restrict__ rdot, const int lane, const int ty) {
     using AT = typename AccOf<XT>::type;
-    // planes per z-march batch (measured on the 511^3 step: 2 planes 411 us,
-    // 4 planes 443 us, 8 planes 554 us for float)
-    constexpr int P = 2;
+    constexpr int P = PZ;
     const int i = bx * kTX + lane;
     const int j = by * kTY + ty;
     const bool in = i < nx && j < ny;
