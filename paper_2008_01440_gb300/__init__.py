@@ -25,6 +25,11 @@ from .binding import (  # noqa: F401
     NC_ERR_UNSUPPORTED,
     NC_F32,
     NC_F64,
+    NC_FORMAT_AUTO,
+    NC_FORMAT_CSR,
+    NC_FORMAT_PSELL,
+    NC_FORMAT_SELL,
+    NC_FORMAT_TUNE,
     NC_OK,
     LIB_PATH,
     Matrix,
