@@ -91,3 +91,29 @@ def test_binding_structs_match_header(libpath):
         assert [f for f, _ in cls._fields_] == _header_struct_fields(name), name
     o = binding.make_options(poly="newton", persistent=True, apply_dtype="f32")
     assert (o.poly_form, o.use_graph, o.apply_dtype) == (1, 2, 1)
+
+
+def _header_constants():
+    """NAME = value pairs of the header's enums and integer #defines."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for body in re.findall(r"typedef enum\s*\{([^{}]*)\}", text):
+        for name, val in re.findall(r"\b(NC_\w+)\s*=\s*(-?\d+)", body):
+            out[name] = int(val)
+    for name, val in re.findall(r"^#define\s+(NC_\w+)\s+\(?(-?\d+)[uU]?\)?\s*$", text, re.M):
+        out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_header():
+    """Every enum value or integer constant of the header that the binding
+    defines has the header's value (status codes, dtypes, layouts, forms)."""
+    from paper_2008_01440_gb300 import binding
+    consts = _header_constants()
+    for required in ("NC_OK", "NC_F64", "NC_FORMAT_SELL", "NC_FORMAT_PSELL", "NC_POLY_NEWTON"):
+        assert required in consts, required
+    checked = [n for n in consts if hasattr(binding, n)]
+    assert len(checked) >= 15
+    mismatched = {n: (getattr(binding, n), consts[n]) for n in checked if getattr(binding, n) != consts[n]}
+    assert not mismatched, mismatched
+    assert binding._FORMATS["psell"] == consts["NC_FORMAT_PSELL"]
