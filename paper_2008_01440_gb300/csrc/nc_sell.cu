@@ -14,7 +14,9 @@
 //
 // The layout is built once at solver setup from the CSR arrays; it is chosen
 // when its padding is small (grid and finite-element matrices), otherwise
-// the CSR kernel runs.  The solver stores the shifted operator A - theta' I
+// the CSR kernel runs.  Its offset-pattern form (below, PAT) drops the column
+// indices where the slices' columns are row + a few repeated offsets.  The
+// solver stores the shifted operator A - theta' I
 // (only diagonal entries change): the p_k recursion of Sec. 3 applies
 // 2 sigma (1 - A/theta') = -(2/delta)(A - theta' I), so with the shift every
 // Chebyshev step after the first needs no separate x_{k-1} term, one FP64
