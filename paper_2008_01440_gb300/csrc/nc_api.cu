@@ -315,16 +315,19 @@ void setup_coefficients(nc_solver S) {
 // Coefficients of the fused steps as the kernels take them, for the stored
 // iterates y_j = x_j / g_j.  In float64 the scale g_j = cd_j g_{j-1} makes the
 // coefficient of the product exactly 1, so the step kernels drop one float64
-// multiply per row (their bound is the float64 pipe); the last step keeps
-// g_k = 1 so z itself is stored, and g falls back to 1 at any step where it
-// would leave [2^-64, 2^64].  The mixed-precision path stores x_j itself.
-// Entry j = step j (index 0 unused); the x_{k-1} term is dropped for the
-// shifted operator (see enqueue_poly).
+// multiply per row (their bound is the float64 pipe); g falls back to 1 at
+// any step where it would leave [2^-64, 2^64].  The last step keeps g_k = 1,
+// so z itself is stored, unless `in_solve`: PCG's iterates do not change when
+// P is multiplied by a positive constant (z, p and q scale alike, alpha and
+// beta compensate), so inside a solve the last step also stores z / g_k when
+// g_k > 0.  The mixed-precision path stores x_j itself.  Entry j = step j
+// (index 0 unused); the x_{k-1} term is dropped for the shifted operator
+// (see enqueue_poly).
 struct StepC {
     double ca, cb, cc, cd;
 };
 
-std::vector<StepC> step_coefs(const nc_solver S) {
+std::vector<StepC> step_coefs(const nc_solver S, bool in_solve) {
     const int k = S->k;
     std::vector<StepC> out(k + 1, StepC{0.0, 0.0, 0.0, 0.0});
     std::vector<double> g(k + 1, 1.0);
@@ -337,7 +340,8 @@ std::vector<StepC> step_coefs(const nc_solver S) {
         const double gu = (j == 1) ? 1.0 : g[j - 1];   // scale of u (r at step 1)
         const double gw = (j >= 3) ? g[j - 2] : 1.0;   // scale of w = y_{j-2}
         const double t = S->cd[j] * kap * gu;
-        const bool unit = !S->mixed && j < k && std::fabs(t) >= 0x1p-64 && std::fabs(t) <= 0x1p64;
+        const bool unit = !S->mixed && (j < k || (in_solve && t > 0.0)) && std::fabs(t) >= 0x1p-64 &&
+                          std::fabs(t) <= 0x1p64;
         g[j] = unit ? t : 1.0;
         out[j].ca = ca * gu / g[j];
         out[j].cb = S->cb[j] * gw / g[j];
@@ -403,7 +407,7 @@ cudaError_t enqueue_poly(nc_solver S, const double* r64, double* z, int fin, con
     // with the shifted operator A' = A - theta' I the x_{k-1} term of every
     // step k >= 2 vanishes (a_k + d_k theta' = 0 exactly) and step 1 keeps
     // (4 rho_1 - 2 rho_1)/delta = 2 rho_1/delta on r
-    const std::vector<StepC> cf = step_coefs(S);
+    const std::vector<StepC> cf = step_coefs(S, fin != FIN_NONE);
     for (int j = 1; j <= S->k; ++j) {
         const void* u = (j == 1) ? rx : S->buf[(j - 1) % 3];
         const void* w = (j >= 3) ? S->buf[(j - 2) % 3] : nullptr;
@@ -602,7 +606,7 @@ cudaError_t menqueue_poly(nc_solver S, int m, int fin, cudaStream_t st) {
         return cudaSuccess;
     }
     const void* rx = S->mixed ? static_cast<const void*>(S->mr32) : static_cast<const void*>(S->mr);
-    const std::vector<StepC> cf = step_coefs(S);
+    const std::vector<StepC> cf = step_coefs(S, fin != FIN_NONE);
     for (int j = 1; j <= S->k; ++j) {
         const void* u = (j == 1) ? rx : S->mbuf[(j - 1) % 3];
         const void* w = (j >= 3) ? S->mbuf[(j - 2) % 3] : nullptr;
@@ -1617,7 +1621,7 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
             // one-cluster solve: per-step coefficients of the shifted operator
             std::vector<double> cf(4 * (size_t)(S->k + 1), 0.0);
             if (S->k == 0) cf[0] = 1.0 / S->theta;
-            const std::vector<StepC> sc = step_coefs(S);
+            const std::vector<StepC> sc = step_coefs(S, true);
             for (int j = 1; j <= S->k; ++j) {
                 cf[4 * j] = sc[j].ca;
                 cf[4 * j + 1] = sc[j].cb;

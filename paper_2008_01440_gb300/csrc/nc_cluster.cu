@@ -18,6 +18,8 @@
 // There is no spin-wait: the cluster's CTAs are co-scheduled by the hardware
 // and every CTA takes the same branches (same scalars), so every barrier is
 // reached by all of them.
+#include <type_traits>
+
 #include "nc_common.cuh"
 
 namespace nc {
@@ -197,15 +199,21 @@ __global__ void __launch_bounds__(kCT) cluster_pcg_kernel(const ClusterArgs a) {
             const double* Wv = vec + (size_t)ws * R;
             double* Y = vec + (size_t)ys * R;
             const uint32_t uoff = (uint32_t)us * vstride;
-            for (int i = threadIdx.x; i < nloc; i += kCT) {
-                double o = row_product(i, lptr, mval, maddr, uoff, 0.0);
-                if (hd) o *= cd;
-                if (hc) o = fma(cc, Rv[i], o);
-                if (hb) o = fma(cb, Wv[i], o);
-                if (ha) o = fma(ca, U[i], o);
-                Y[i] = o;
-                if (j == k) pz = fma(Rv[i], o, pz);
-            }
+            // the test of the product's coefficient stays outside the row
+            // loop: inside it the compiler issues the multiply either way
+            auto rows = [&](auto scaled) {
+                for (int i = threadIdx.x; i < nloc; i += kCT) {
+                    double o = row_product(i, lptr, mval, maddr, uoff, 0.0);
+                    if constexpr (decltype(scaled)::value) o *= cd;
+                    if (hc) o = fma(cc, Rv[i], o);
+                    if (hb) o = fma(cb, Wv[i], o);
+                    if (ha) o = fma(ca, U[i], o);
+                    Y[i] = o;
+                    if (j == k) pz = fma(Rv[i], o, pz);
+                }
+            };
+            if (hd) rows(std::true_type{});
+            else rows(std::false_type{});
             if (j < k) cluster_sync();   // x_j visible before step j+1 gathers it
         }
         return cluster_sum(pz, num, div, sh, red, bc, slot);
