@@ -67,8 +67,9 @@ struct BState {
 
 struct BCoef {
     float e0, ex, ey, ez, cb, cc;
-    int terms, pad;
-    double e0d, exd, eyd, ezd, cbd, ccd;   // the same in float64 (float64 apply)
+    int terms;
+    int xu;                                // float64 fields: exd == -1 exactly (no centre multiply)
+    double e0d, exd, eyd, ezd, cbd, ccd;   // float64 apply: the step for the scaled iterates
 };
 
 struct BTile {
@@ -258,9 +259,15 @@ __global__ void __launch_bounds__(256) bk_cheb(const BDesc* __restrict__ D, BSta
             const double* u = (j == 1) ? d.r : tb[(j - 1) % 3];
             const double* w = (j >= 3) ? tb[(j - 2) % 3] : nullptr;
             if (j == d.k) {
-                const double dv = stencil_flat<double, double, 1>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r, d.z,
-                                                                  c, d.r, tid);
+                const double dv =
+                    bc.xu ? stencil_flat<double, double, 1, true>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r, d.z, c,
+                                                                  d.r, tid)
+                          : stencil_flat<double, double, 1>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r, d.z, c, d.r,
+                                                            tid);
                 reduce_slot(dv, partials, t, d.tile0, d.tile1 - d.tile0, st, ctl, BF_RZ);
+            } else if (bc.xu) {
+                stencil_flat<double, double, 0, true>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r, tb[j % 3], c,
+                                                      nullptr, tid);
             } else {
                 stencil_flat<double, double, 0>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r, tb[j % 3], c, nullptr,
                                                 tid);
@@ -669,6 +676,13 @@ nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx
     const double sigma = theta / delta;
     std::vector<BCoef> cf(degree_k);
     double rho_prev = 1.0 / sigma;
+    // float64 apply: iterates stored as y_j = x_j / g_j with g_j = d_j c_x g_{j-1},
+    // which makes the x-coefficient exactly -1 (a kernel variant without the
+    // centre multiply); g falls back to 1 outside [2^-64, 2^64], and the last
+    // step stores z itself unless g_k > 0 (PCG does not change when z, and
+    // with it p and q, are scaled by a positive constant: alpha and beta
+    // compensate).  The float apply keeps the plain coefficients.
+    std::vector<double> g(degree_k + 1, 1.0);
     for (int j = 1; j <= degree_k; ++j) {
         const double rho = 1.0 / (2.0 * sigma - rho_prev);
         double ca, cb, cc, cd;
@@ -686,12 +700,19 @@ nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx
         c.cb = (float)cb;
         c.cc = (float)cc;
         c.terms = (cb != 0.0 ? kTermW : 0) | (cc != 0.0 ? kTermR : 0);
-        c.e0d = ca + cd * d.c0;
-        c.exd = -cd * d.cx;
-        c.eyd = -cd * d.cy;
-        c.ezd = -cd * d.cz;
-        c.cbd = cb;
-        c.ccd = cc;
+        const double gu = (j == 1) ? 1.0 : g[j - 1];   // scale of u (r at step 1)
+        const double gw = (j >= 3) ? g[j - 2] : 1.0;   // scale of w = y_{j-2}
+        const double t = cd * d.cx * gu;
+        const bool unit = d.cx != 0.0 && (j < degree_k || t > 0.0) && std::fabs(t) >= 0x1p-64 &&
+                          std::fabs(t) <= 0x1p64;
+        g[j] = unit ? t : 1.0;
+        c.xu = unit ? 1 : 0;
+        c.e0d = (ca + cd * d.c0) * gu / g[j];
+        c.exd = unit ? -1.0 : -cd * d.cx * gu;
+        c.eyd = -cd * d.cy * gu / g[j];
+        c.ezd = -cd * d.cz * gu / g[j];
+        c.cbd = cb * gw / g[j];
+        c.ccd = cc / g[j];
         cf[j - 1] = c;
         rho_prev = rho;
     }

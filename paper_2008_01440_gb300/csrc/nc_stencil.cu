@@ -98,16 +98,28 @@ cudaError_t stencil_dispatch(const StencilGeom& g, const double* c4, const void*
 
 }  // namespace
 
-// z-chunk length: enough CTAs for about eight waves of 8 resident 256-thread
-// CTAs per SM, so a partial last wave of long z-marches costs little
-// (1023^3: 5 chunks of 205 planes, float step 4545 -> 3481 us against one
-// 1023-plane chunk), and at least 32 planes, so the two extra plane loads at
-// a chunk's start stay below 1 % of the traffic.
+// z-chunk length.  Large systems: about eight waves of the 8 resident
+// 256-thread CTAs per SM, so a partial last wave of long z-marches costs
+// little (1023^3: 3 chunks of 341 planes, float step 4545 -> 3481 us against
+// one 1023-plane chunk; 511^3: 10 chunks of 52, float 412 -> 389 us), with
+// chunks of at least 32 planes so the two extra plane loads at a chunk's
+// start stay a few percent of the traffic.  Where 32-plane chunks would not
+// give two waves (small and mid-size systems, up to about 255^3), about two
+// waves with chunks of at least 4 planes, so that the GPU is filled.
 int stencil_zchunk(const StencilGeom& g) {
     const long long tiles = (long long)((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY);
-    const long long want_chunks = (8LL * kSMs * 8 + tiles - 1) / tiles;
-    long long zc = (g.nz + want_chunks - 1) / (want_chunks > 0 ? want_chunks : 1);
-    if (zc < 32) zc = 32;
+    const long long wave = (long long)kSMs * 8;
+    const long long c8 = (8 * wave + tiles - 1) / tiles;
+    long long zc = (g.nz + c8 - 1) / c8;
+    if (zc < 32) {
+        if (tiles * ((g.nz + 31) / 32) >= 2 * wave) {
+            zc = 32;
+        } else {
+            const long long c2 = (2 * wave + tiles - 1) / tiles;
+            zc = (g.nz + c2 - 1) / c2;
+            if (zc < 4) zc = 4;
+        }
+    }
     if (zc > g.nz) zc = g.nz > 0 ? g.nz : 1;
     return (int)zc;
 }

@@ -30,8 +30,8 @@ struct StencilCoef {
 // from -(x-neighbours) and needs no multiply for the centre.
 //
 // PZ: planes per z-march batch.  Measured on the float32 step: 2 planes are
-// best for short z-chunks (511^3, 32-plane chunks: 388 us against 410 with 4),
-// 4 planes for long ones (1023^3, 205-plane chunks: 3316 us against 3481);
+// best for short z-chunks (511^3, 52-plane chunks: 388 us against 410 with 4),
+// 4 planes for long ones (1023^3, 341-plane chunks: 3316 us against 3481);
 // float64 takes 2.
 template <typename XT, typename YT, int DOT, bool XU = false, int PZ = 2>
 __device__ __forceinline__ double stencil_tile(const int nx, const int ny, const int nz, const int bx, const int by,
@@ -110,7 +110,7 @@ __device__ __forceinline__ double stencil_tile(const int nx, const int ny, const
 // called by all lanes of each warp together.
 constexpr int kFT = 256;
 
-template <typename XT, typename YT, int DOT>
+template <typename XT, typename YT, int DOT, bool XU = false>
 __device__ __forceinline__ double stencil_flat(const int nx, const int ny, const int nz, const int f0, const int k0,
                                                const int k1, const XT* __restrict__ u, const XT* __restrict__ w,
                                                const XT* __restrict__ r, YT* __restrict__ y,
@@ -164,8 +164,13 @@ __device__ __forceinline__ double stencil_flat(const int nx, const int ny, const
             if (!has_xp) xp = zero;
             if (in) {
                 const long long q = idx + t * plane;
-                AT o = c.e0 * u_cur;
-                o = fma(c.ex, xm + xp, o);
+                AT o;
+                if constexpr (XU) {   // ex == -1 exactly
+                    o = fma(c.e0, u_cur, -(xm + xp));
+                } else {
+                    o = c.e0 * u_cur;
+                    o = fma(c.ex, xm + xp, o);
+                }
                 o = fma(c.ey, ym[t] + yp[t], o);
                 o = fma(c.ez, u_prev + u_next, o);
                 if (has_r) o = fma(c.cc, rv[t], o);
