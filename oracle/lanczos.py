@@ -60,8 +60,10 @@ def lanczos_bounds(matvec, v0: np.ndarray, steps: int, gershgorin: float | None 
 def power_method(matvec, v0: np.ndarray, iters: int) -> float:
     """Rayleigh quotient after ``iters`` power iterations (Sec. 5.1's beta_0 estimate).
 
-    Parity unpinned against the paper's own runs (it prints no values); pinned
-    only by closed-form spectra in the tests.
+    The paper prints no values from its runs; pinned by closed forms in the
+    tests: for a diagonal matrix the estimate after m iterations equals
+    sum l^(2m-1) v0^2 / sum l^(2m-2) v0^2 exactly, and on the 64 x 64
+    Laplacian it rises towards 8 sin^2(64 pi / 130) from below.
     """
     v = v0 / np.linalg.norm(v0)
     lam = 0.0

@@ -185,6 +185,31 @@ def test_power_method_converges():
     assert abs(est - 2.0) < 1e-3
 
 
+@pytest.mark.parametrize("m", [1, 2, 5, 17])
+def test_power_method_exact_rayleigh_quotient(m):
+    """For a diagonal matrix the estimate after m iterations is the Rayleigh
+    quotient of A^(m-1) v0 in closed form: sum l^(2m-1) v^2 / sum l^(2m-2) v^2
+    (catches an off-by-one in the iteration count or a wrong normalisation)."""
+    lam = np.linspace(0.3, 1.7, 40)
+    v0 = W.uniform_vector(40, seed=3)
+    est = O.power_method(lambda u: lam * u, v0, m)
+    ref = np.sum(lam ** (2 * m - 1) * v0 ** 2) / np.sum(lam ** (2 * m - 2) * v0 ** 2)
+    assert abs(est - ref) <= 1e-13 * ref
+
+
+def test_power_method_laplacian_closed_form():
+    """2D 5-point Laplacian 64 x 64: lambda_max = 8 sin^2(64 pi / 130); the
+    estimate approaches it from below."""
+    A = W.laplacian_2d_5pt(64, 64)
+    _, lmax = W.laplacian_2d_bounds(64, 64)
+    assert abs(lmax - 8 * np.sin(64 * np.pi / 130) ** 2) < 1e-14
+    mv = O.csr_matvec(A.rowptr, A.col, A.val, A.n)
+    e1 = O.power_method(mv, W.uniform_vector(A.n, seed=2), 50)
+    e2 = O.power_method(mv, W.uniform_vector(A.n, seed=2), 400)
+    assert e1 <= e2 <= lmax * (1 + 1e-12)
+    assert lmax - e2 < 1e-2 * lmax
+
+
 # ---- operators ------------------------------------------------------------
 
 def test_stencil7_matvec_matches_csr_assembly():
