@@ -117,3 +117,35 @@ def test_binding_constants_match_header():
     mismatched = {n: (getattr(binding, n), consts[n]) for n in checked if getattr(binding, n) != consts[n]}
     assert not mismatched, mismatched
     assert binding._FORMATS["psell"] == consts["NC_FORMAT_PSELL"]
+
+
+def test_setup_rejects_bad_options_before_any_device_call(libpath):
+    """pcg_setup validates its options before it touches the device: an
+    empty matrix handle (no CUDA) is enough to see every rejection."""
+    from paper_2008_01440_gb300 import binding as b
+    h = ctypes.c_void_p()
+    assert b.lib.nc_matrix_csr(0, 0, None, None, None, ctypes.byref(h)) == b.NC_OK
+    S = ctypes.c_void_p()
+
+    try:
+        o = b.make_options()
+        o.spmv_format = b.NC_FORMAT_PSELL + 1
+        assert b.lib.pcg_setup(h, 0.1, 2.0, 3, 1.0, ctypes.byref(o), None, ctypes.byref(S)) == b.NC_ERR_ARG
+        o = b.make_options(spmv_format="psell")
+        o.apply_dtype = 7
+        assert b.lib.pcg_setup(h, 0.1, 2.0, 3, 1.0, ctypes.byref(o), None, ctypes.byref(S)) == b.NC_ERR_ARG
+        o = b.make_options()
+        o.rr_period = -1
+        assert b.lib.pcg_setup(h, 0.1, 2.0, 3, 1.0, ctypes.byref(o), None, ctypes.byref(S)) == b.NC_ERR_ARG
+        # the Newton form: k = 2^nlev - 1 only, float64 only
+        o = b.make_options(poly="newton")
+        assert b.lib.pcg_setup(h, 0.1, 2.0, 4, 1.0, ctypes.byref(o), None, ctypes.byref(S)) == b.NC_ERR_ARG
+        o = b.make_options(poly="newton", apply_dtype="f32")
+        assert b.lib.pcg_setup(h, 0.1, 2.0, 7, 1.0, ctypes.byref(o), None, ctypes.byref(S)) == b.NC_ERR_UNSUPPORTED
+        # the interval and the scale
+        o = b.make_options()
+        for lo, hi, s in ((0.0, 2.0, 1.0), (2.0, 1.0, 1.0), (0.1, float("inf"), 1.0), (0.1, 2.0, 0.0)):
+            assert b.lib.pcg_setup(h, lo, hi, 3, s, ctypes.byref(o), None, ctypes.byref(S)) == b.NC_ERR_ARG
+        assert not S.value
+    finally:
+        assert b.lib.nc_matrix_destroy(h) == b.NC_OK
