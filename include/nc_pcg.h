@@ -73,9 +73,9 @@ typedef enum { NC_F64 = 0, NC_F32 = 1, NC_BF16 = 2 } nc_dtype;
  * row + o for the sorted set of offsets o = col - row of its 32 rows (rows
  * lacking an offset store a 0 there), and each distinct set is kept once.
  * It applies when every row's columns increase, a slice has at most 64
- * offsets, the padding is at most 1.5x and the distinct sets hold at most
- * 16384 offsets in all (regularly numbered grid matrices); otherwise the
- * solver falls back to SELL.  AUTO tries PSELL first for CSR matrices,
+ * offsets, the padding is at most 1.5x, the distinct sets hold at most
+ * 16384 offsets in all (regularly numbered grid matrices) and n <= 2^30;
+ * otherwise the solver falls back to SELL.  AUTO tries PSELL first for CSR matrices,
  * except with use_graph = 2 (the cluster solve reads plain SELL).  Stencil
  * handles ignore the option. */
 typedef enum {

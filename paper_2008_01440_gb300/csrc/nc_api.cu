@@ -889,12 +889,14 @@ nc_status setup_operator_bsr3(nc_solver S, cudaStream_t st, size_t eb) {
 // Offset-pattern layout (NC_FORMAT_PSELL) from the CSR arrays.  Returns
 // NC_ERR_UNSUPPORTED, with nothing left allocated, when the matrix does not
 // qualify: a row whose columns do not increase, a slice with more than 64
-// offsets, padding above kSellMaxPadding, or distinct offset sets holding
-// more than kPatMaxTable offsets in all.
+// offsets, padding above kSellMaxPadding, distinct offset sets holding more
+// than kPatMaxTable offsets in all, or more than 2^30 rows (the kernels form
+// row + offset in 32 bits, which stays in range for |offset| < n <= 2^30).
 constexpr int64_t kPatMaxTable = 16384;
 
 nc_status setup_psell(nc_solver S, cudaStream_t st, size_t eb) {
     nc_matrix A = S->A;
+    if (S->n > ((int64_t)1 << 30)) return NC_ERR_UNSUPPORTED;
     const int n = (int)S->n;
     const int nslices = (n + 31) / 32;
     int32_t *dcnt = nullptr, *dopos = nullptr, *doff = nullptr;
