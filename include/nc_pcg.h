@@ -292,8 +292,8 @@ NC_API nc_status pcg_solve_host(nc_solver S, const double* b_host, double* x_hos
  * on.  B_dev, X_dev: n x m float64 on the device, column-major (column c at
  * offset c*n); X_dev holds the initial guesses unless opt.x0_is_zero.  res:
  * host array of m results (required).  Returns NC_OK when every column
- * converged, else the first column's non-OK status.  Needs the sliced
- * (SELL) layout and the Chebyshev form without residual replacement
+ * converged, else the first column's non-OK status.  Needs a sliced layout
+ * (SELL or PSELL) and the Chebyshev form without residual replacement
  * (NC_ERR_UNSUPPORTED otherwise); allocates 9 m n-vectors of workspace on
  * first use for a given m (kept until pcg_destroy).  Synchronises `stream`.
  * Not in the paper: a throughput form of its solver for many right-hand
@@ -301,9 +301,12 @@ NC_API nc_status pcg_solve_host(nc_solver S, const double* b_host, double* x_hos
 NC_API nc_status pcg_solve_multi(nc_solver S, int m, const double* B_dev, double* X_dev, double tol, int maxit,
                                  void* stream, nc_result* res);
 
-/* Layout and parameters the solver chose. */
+/* Layout and parameters the solver chose (info: caller-owned).  NC_ERR_ARG
+ * for a null argument. */
 NC_API nc_status pcg_get_info(nc_solver S, nc_solver_info* info);
 
+/* Frees the solver's workspaces and layouts (not the matrix handle); the
+ * frees wait for work still running on the device.  NC_ERR_ARG for NULL. */
 NC_API nc_status pcg_destroy(nc_solver S);
 
 /* ---- Batched and continuous-batching engine --------------------------------
