@@ -32,6 +32,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -509,6 +510,27 @@ def read_traffic(key, mode):
     return None
 
 
+def host_info():
+    """CPU model and logical core count of the host the oracle is timed on."""
+    model, impl, part = "", "", ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                key, val = key.strip(), val.strip()
+                if key == "model name" and val and not model:
+                    model = val
+                elif key == "CPU implementer" and not impl:
+                    impl = val
+                elif key == "CPU part" and not part:
+                    part = val
+    except OSError:
+        pass
+    if not model:
+        model = platform.machine() + (f" (implementer {impl}, part {part})" if impl or part else "")
+    return {"host_cpu": model or "unknown", "host_nproc": os.cpu_count()}
+
+
 def cpu_baseline_subprocess(args, gpu_iters):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
@@ -524,7 +546,7 @@ def cpu_baseline_subprocess(args, gpu_iters):
         ref = json.loads(line)
         cb = ref.get("cpu_baseline", {})
         return {"value": ref["value"], "unit": ref["unit"], "cores": cb.get("cores", 1), "kind": "oracle",
-                "sample": cb.get("sample")}
+                "sample": cb.get("sample"), **host_info()}
     except Exception as e:  # report, do not fail the GPU measurement
         return {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
 
@@ -604,7 +626,8 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generators, no dataset)",
             "config": {"workload": sp["workload"], "degree_k": k, "theta_scale": sp["s"], "tol": TOL},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             **host_info()},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -1042,7 +1065,8 @@ def run_fd3d(args, rank, world, local_rank):
         est = main_run["iters"] * (main_run["k"] + 1) * t_mv
         cpu = {"value": round(1.0 / est, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": f"one oracle 7-point product on the full {m}^3 grid ({t_mv:.2f} s), extrapolated to "
-                         f"{main_run['iters']} x {main_run['k'] + 1} products (vector updates not counted)"}
+                         f"{main_run['iters']} x {main_run['k'] + 1} products (vector updates not counted)",
+               **host_info()}
     line = {"metric": METRIC, "value": round(1.0 / main_run["seconds_per_solve"], 4), "unit": "solves/s",
             "n_gpus": world, "steps": steps, "warmup": warmup,
             "ms_per_step": round(1e3 * main_run["seconds_per_solve"], 2), "higher_is_better": True,

@@ -31,3 +31,9 @@ def test_float64_peak_from_unit_counts():
     # 2 float64 FMA per clock per SM x 2 flops x 152 SMs x 2.07 GHz
     assert bench.FP64_PEAK_TFLOPS == round(2 * 2 * 152 * 2.070e9 / 1e12, 4) == 1.2586
     assert "2 float64 FMA/clk/SM" in bench.FP64_PEAK_SOURCE
+
+
+def test_host_info_names_the_cpu_and_its_cores():
+    info = bench.host_info()
+    assert isinstance(info["host_cpu"], str) and info["host_cpu"]
+    assert isinstance(info["host_nproc"], int) and info["host_nproc"] >= 1
