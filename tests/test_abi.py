@@ -149,3 +149,62 @@ def test_setup_rejects_bad_options_before_any_device_call(libpath):
         assert not S.value
     finally:
         assert b.lib.nc_matrix_destroy(h) == b.NC_OK
+
+
+def test_host_side_matrix_entry_points(libpath):
+    """Stencil handles, their Jacobi scaling and their Gershgorin bound are
+    host-only: checked here against the assembled CSR's largest absolute row
+    sum (brute force), with the argument checks the header documents."""
+    import numpy as np
+    import workloads as W
+    from paper_2008_01440_gb300 import binding as b
+    h, hs = ctypes.c_void_p(), ctypes.c_void_p()
+    g = ctypes.c_double()
+    for bad in ((0, 4, 4, 6.0), (4, 4, 4, float("nan")), (2048, 1024, 1024, 6.0)):
+        assert b.lib.nc_matrix_stencil7(*bad[:3], bad[3], 1.0, 1.0, 1.0, ctypes.byref(h)) == b.NC_ERR_ARG
+    for dims, c in (((5, 4, 3), (6.0, 1.0, 0.5, 0.25)), ((1, 1, 5), (2.0, 1.0, 1.0, 1.0)),
+                    ((2, 7, 1), (3.0, 0.4, 0.9, 0.3))):
+        assert b.lib.nc_matrix_stencil7(*dims, *c, ctypes.byref(h)) == b.NC_OK
+        try:
+            A = W.stencil7_to_csr(W.Stencil7(*dims, *c))
+            rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+            ref = np.zeros(A.n)
+            np.add.at(ref, rows, np.abs(A.val))
+            assert b.lib.nc_gershgorin(h, None, ctypes.byref(g)) == b.NC_OK
+            assert abs(g.value - ref.max()) <= 1e-14 * ref.max()
+            # Jacobi scaling: constant diagonal c0, so the bound scales by 1/c0
+            assert b.lib.nc_matrix_jacobi(h, None, ctypes.byref(hs)) == b.NC_OK
+            assert b.lib.nc_gershgorin(hs, None, ctypes.byref(g)) == b.NC_OK
+            assert abs(g.value - ref.max() / c[0]) <= 1e-14 * ref.max() / c[0]
+            h2 = ctypes.c_void_p()
+            assert b.lib.nc_matrix_jacobi(hs, None, ctypes.byref(h2)) == b.NC_ERR_ARG   # already scaled
+            assert b.lib.nc_matrix_destroy(hs) == b.NC_OK
+        finally:
+            assert b.lib.nc_matrix_destroy(h) == b.NC_OK
+    assert b.lib.nc_matrix_stencil7(4, 4, 4, -1.0, 1.0, 1.0, 1.0, ctypes.byref(h)) == b.NC_OK
+    assert b.lib.nc_matrix_jacobi(h, None, ctypes.byref(hs)) == b.NC_ERR_ARG          # c0 <= 0
+    assert b.lib.nc_matrix_destroy(h) == b.NC_OK
+    assert b.lib.nc_matrix_destroy(None) == b.NC_ERR_ARG
+
+
+def test_status_strings_and_option_defaults(libpath):
+    from paper_2008_01440_gb300 import binding as b
+    consts = _header_constants()
+    codes = sorted({v for k, v in consts.items() if k == "NC_OK" or k.startswith("NC_ERR_")})
+    lib = ctypes.CDLL(libpath)
+    lib.nc_strerror.restype = ctypes.c_char_p
+    texts = [lib.nc_strerror(c) for c in codes]
+    assert len(set(texts)) == len(codes) and b"unknown status" not in texts
+    assert lib.nc_strerror(max(codes) + 1) == b"unknown status"
+    o = b.nc_options()
+    b.lib.nc_options_default(ctypes.byref(o))
+    assert (o.apply_dtype, o.rr_period, o.x0_is_zero, o.use_graph, o.spmv_format, o.poly_form) == \
+        (b.NC_F64, 0, 0, 1, b.NC_FORMAT_AUTO, consts["NC_POLY_CHEBYSHEV"])
+
+
+def test_batch_create_checks_arguments_first(libpath):
+    from paper_2008_01440_gb300 import binding as b
+    B = ctypes.c_void_p()
+    for args in ((0, 100, 8, 0), (4, 0, 8, 0), (4, 100, 0, 0), (4, 100, 5000, 0), (4, 100, 8, 1 << 12)):
+        assert b.lib.pcg_batch_create(*args, None, ctypes.byref(B)) == b.NC_ERR_ARG
+        assert not B.value
