@@ -15,7 +15,8 @@ from __future__ import annotations
 import numpy as np
 
 
-def lanczos_bounds(matvec, v0: np.ndarray, steps: int, gershgorin: float | None = None):
+def lanczos_bounds(matvec, v0: np.ndarray, steps: int, gershgorin: float | None = None,
+                   keep_basis: bool = False):
     """Lanczos estimate of [lambda_min, lambda_max] with a safe upper end.
 
     Recurrence (no reorthogonalisation), v_1 = v0/||v0||, beta_0 = 0:
@@ -28,13 +29,20 @@ def lanczos_bounds(matvec, v0: np.ndarray, steps: int, gershgorin: float | None 
     instead.  Lower end: ritz_min (an overestimate, which is safe: eigenvalues
     below alpha are mapped into (0, 1)).
 
-    Returns (lower, upper, info) with info = dict(alpha=a, beta=b, ritz=theta).
+    Returns (lower, upper, info) with info = dict(alpha=a, beta=b, ritz=theta,
+    ritz_vectors=S, resid=|b_m s_m|); with keep_basis the Lanczos vectors
+    v_1..v_m are kept as the columns of info["basis"] (n x m), so that a caller
+    can form the top Ritz vector y = V s and check the residual bound
+    ||A y - theta y|| = |b_m s_m| against the matrix itself.
     """
     v = v0 / np.linalg.norm(v0)
     v_prev = np.zeros_like(v)
     b_prev = 0.0
     a_list, b_list = [], []
+    basis = []
     for _ in range(steps):
+        if keep_basis:
+            basis.append(v.copy())
         w = matvec(v) - b_prev * v_prev
         a = float(np.dot(w, v))
         w = w - a * v
@@ -53,7 +61,9 @@ def lanczos_bounds(matvec, v0: np.ndarray, steps: int, gershgorin: float | None 
     upper = max(rmax + resid, 1.01 * rmax)
     if gershgorin is not None and rmax <= gershgorin < upper:
         upper = float(gershgorin)
-    info = dict(alpha=np.array(a_list), beta=np.array(b_list), ritz=theta)
+    info = dict(alpha=np.array(a_list), beta=np.array(b_list), ritz=theta, ritz_vectors=S, resid=resid)
+    if keep_basis:
+        info["basis"] = np.stack(basis, axis=1)
     return rmin, upper, info
 
 

@@ -179,6 +179,54 @@ def test_lanczos_bounds_contain_spectrum_laplacian():
     assert lmax <= hi2 <= max(hi, gersh)
 
 
+@pytest.mark.parametrize("seed,steps", [(0, 4), (1, 5), (2, 6), (3, 7)])
+def test_lanczos_top_ritz_residual_identity(seed, steps):
+    """The safe upper end's residual term is ||A y - theta y|| for the top Ritz
+    pair (theta, y = V s): for Lanczos A V = V T + b_m v_{m+1} e_m^T, so the
+    residual is |b_m| times the LAST component of s.  Checked against the
+    dense matrix itself (not the recurrence), with the residual branch
+    active; a wrong eigenvector component or a dropped term fails here.  The
+    residual bound also puts an eigenvalue of A within that distance of theta."""
+    A, lam = spd(40, 50.0, seed=seed)
+    lo, hi, info = O.lanczos_bounds(lambda u: A @ u, W.uniform_vector(40, seed=seed + 7), steps,
+                                    keep_basis=True)
+    V = info["basis"]
+    assert V.shape == (40, steps)
+    assert np.allclose(V.T @ V, np.eye(steps), atol=1e-10)          # orthonormal for few steps
+    T = V.T @ A @ V
+    assert np.allclose(np.diag(T), info["alpha"], atol=1e-10)
+    assert np.allclose(np.diag(T, 1), info["beta"][:steps - 1], atol=1e-10)
+    theta = info["ritz"].max()
+    y = V @ info["ritz_vectors"][:, -1]
+    assert abs(np.linalg.norm(y) - 1.0) < 1e-10
+    res = np.linalg.norm(A @ y - theta * y)
+    assert res > 0.01 * theta                                          # the residual branch decides
+    assert abs(hi - (theta + res)) <= 1e-10 * theta
+    assert np.min(np.abs(lam - theta)) <= res * (1 + 1e-10)
+
+
+@pytest.mark.parametrize("steps", [5, 6])
+@pytest.mark.parametrize("seed", [0, 5, 17])
+def test_lanczos_upper_end_covers_laplacian_1d(steps, seed):
+    """1D Laplacian of order 200, lambda_max = 4 sin^2(200 pi / 402) in closed
+    form.  After 5-6 steps the top Ritz value is still well below it and
+    1.01 ritz_max does not reach it; the upper end is ritz_max plus the
+    residual term, and that covers lambda_max."""
+    n = 200
+    A = W.laplacian_1d(n)
+    mv = O.csr_matvec(A.rowptr, A.col, A.val, A.n)
+    lmax = 4.0 * np.sin(n * np.pi / (2.0 * (n + 1))) ** 2
+    lo, hi, info = O.lanczos_bounds(mv, W.uniform_vector(n, seed=seed), steps, keep_basis=True)
+    rmax = info["ritz"].max()
+    assert 1.01 * rmax < lmax
+    Ad = A.to_scipy().toarray()
+    y = info["basis"] @ info["ritz_vectors"][:, -1]
+    res = np.linalg.norm(Ad @ y - rmax * y)
+    assert abs(hi - (rmax + res)) <= 1e-10 * rmax
+    assert hi >= lmax
+    assert lo >= 4.0 * np.sin(np.pi / (2.0 * (n + 1))) ** 2
+
+
 def test_power_method_converges():
     lam = np.linspace(0.1, 2.0, 50)
     est = O.power_method(lambda u: lam * u, W.uniform_vector(50, seed=1), 400)
