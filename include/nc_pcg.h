@@ -374,12 +374,16 @@ NC_API const char* nc_batch_last_cuda_error(void);
  * CSR matrix with float64 values (arguments as in nc_matrix_csr and
  * pcg_setup), but builds no handle and calls no allocator: the float64
  * recurrence keeps two of its three work vectors in one fixed device array
- * of 2 x nc_apply_poly_noalloc_max_n() doubles (16 MiB) that every device
- * loading the library holds until the process exits, and uses z_dev as the
- * third.  n above nc_apply_poly_noalloc_max_n() (2^20) is rejected with
- * NC_ERR_SCRATCH_LIMIT before any work.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
+ * of 2 x nc_apply_poly_noalloc_max_n() doubles (16 MiB), and uses z_dev as
+ * the third.  The array belongs to the library's module: under CUDA's
+ * default lazy module loading its 16 MiB are taken on a device when the
+ * module is first used there (possibly by the first call of this entry
+ * point) and held until the process exits.  Every call looks up the array's
+ * device address (cudaGetSymbolAddress) with the calling device current.
+ * Callers that need the no-allocation guarantee make one warm-up call per
+ * device at start-up, outside any stream capture; later calls then allocate
+ * nothing.  n above nc_apply_poly_noalloc_max_n() (2^20) is rejected with
+ * NC_ERR_SCRATCH_LIMIT before any work.  All calls share
  * the array: calls that overlap on the GPU (several streams or host threads
  * on one device) race and must be serialised by the caller.  Nothing in the
  * array needs to start at zero (every slot is written before it is read).

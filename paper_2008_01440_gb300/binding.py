@@ -132,10 +132,20 @@ def _stream(stream):
     return stream.cuda_stream
 
 
+def _check_device(index, current, what="tensor"):
+    """The library launches on the CURRENT device and looks up its per-device
+    state (the no-allocation array, solver workspaces) there, so a tensor on
+    another device would hand its kernels foreign pointers: refuse it."""
+    if index != current:
+        raise ValueError(f"{what}: on cuda:{index} but the current device is cuda:{current}; "
+                         f"call inside torch.cuda.device({index})")
+
+
 def _ptr(t, dtype=None, n=None, what="tensor"):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{what}: expected a CUDA tensor")
+    _check_device(t.device.index, torch.cuda.current_device(), what)
     if not t.is_contiguous():
         raise ValueError(f"{what}: must be contiguous")
     if dtype is not None and t.dtype != dtype:

@@ -17,39 +17,31 @@
 // written before it is read, so leftovers of an earlier call are harmless.
 // Calls that overlap on the GPU (two streams, or two host threads on one
 // device) share the array and race; serialise them.
-#include <mutex>
-
 #include "nc_common.cuh"
 
 namespace {
 
 constexpr int64_t kNoAllocMaxN = (int64_t)1 << 20;   // 1,048,576 unknowns
-constexpr int kMaxDevices = 64;
 
 // 2 vectors x 2^20 float64 = 16 MiB on every device that loads the library,
 // held until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxN];
 
-std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[kMaxDevices] = {nullptr};
-
 // Device address of the array for the current device.  The host-side name
 // g_noalloc_scratch is only a stand-in for the symbol; its device address
-// must come from cudaGetSymbolAddress with the device current.
+// must come from cudaGetSymbolAddress with the device current.  It is looked
+// up on every call (no cache), so a context torn down and re-created by the
+// caller (cudaDeviceReset) never leaves a stale address behind.  The first
+// lookup on a device may load the library's module there (lazy loading),
+// which is when the array's memory is taken.
 nc_status noalloc_scratch(double** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NC_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (g_noalloc_ptr[dev] == nullptr) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            cudaGetLastError();
-            return NC_ERR_CUDA;
-        }
-        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return NC_ERR_CUDA;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<double*>(p);
     return NC_OK;
 }
 

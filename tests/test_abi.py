@@ -208,3 +208,16 @@ def test_batch_create_checks_arguments_first(libpath):
     for args in ((0, 100, 8, 0), (4, 0, 8, 0), (4, 100, 0, 0), (4, 100, 5000, 0), (4, 100, 8, 1 << 12)):
         assert b.lib.pcg_batch_create(*args, None, ctypes.byref(B)) == b.NC_ERR_ARG
         assert not B.value
+
+
+def test_binding_refuses_tensor_on_another_device(libpath):
+    """Every entry point launches on the current device; a tensor that lives on
+    another one must be refused before any pointer reaches the library."""
+    from paper_2008_01440_gb300 import binding
+    binding._check_device(0, 0, "v")
+    binding._check_device(3, 3, "v")
+    with pytest.raises(ValueError, match="cuda:1 but the current device is cuda:0"):
+        binding._check_device(1, 0, "v")
+    import torch
+    with pytest.raises(TypeError):
+        binding._ptr(torch.zeros(4, dtype=torch.float64), torch.float64, 4, "v")   # host tensor
