@@ -62,6 +62,11 @@ def parse():
     ap.add_argument("--c4-systems", type=int, default=256, help="c4: number of systems")
     ap.add_argument("--no-modes", action="store_true", help="skip the other apply precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-north-star", action="store_true",
+                    help="c2: skip the compact batched (c4) and serving (c5) passes")
+    ap.add_argument("--ns-requests", type=int, default=60, help="c2: requests of the compact serving pass")
+    ap.add_argument("--err-inputs", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cores", type=int, default=None, help="reference: oracle processes (default: all cores)")
     ap.add_argument("--oracle-iters", type=int, default=6, help="PCG iterations per oracle sample")
     ap.add_argument("--gpu-iters", type=int, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--solve", default="auto", choices=["auto", "graph", "persistent"],
@@ -297,6 +302,8 @@ def run_system(args, spec, rank, world, local_rank):
 
     persistent = (args.solve == "persistent" or (args.solve == "auto" and spec.get("persistent", False))) \
         and not args.host_loop
+    want_err = rank == 0 and world == 1 and not args.no_cpu and args.workload == "c2"
+    err_inputs = {}
     modes = [args.apply] + ([] if args.no_modes else [m for m in ("f64", "f32", "bf16") if m != args.apply])
     out_modes = {}
     main = None
@@ -325,6 +332,14 @@ def run_system(args, spec, rank, world, local_rank):
         t_launch, nbytes = time_step_kernel(S, mode)
         rec["step_us"] = round(t_launch * 1e6, 2)
         rec["step_GBps"] = round(nbytes / t_launch / 1e9, 1)
+        info = nc.pcg_get_info(S)
+        rec["step_kernel"] = {"plain": info["step_kernel"], "dot": info["dot_step_kernel"],
+                              "stages": info["step_stages"], "ctas_per_sm": info["step_ctas_per_sm"],
+                              "tune_candidates": info["tune_candidates"]}
+        if want_err:
+            # the solution of the first right-hand side, for the error against the oracle (CPU leg)
+            nc.pcg_solve(S, bs[0], x, TOL, MAXIT)
+            err_inputs.setdefault("c2", {"lo": lo, "hi": hi, "k": k, "x": {}})["x"][mode] = x.cpu().numpy().copy()
         out_modes[mode] = rec
         if mode == args.apply:
             main = dict(rec=rec, S=S, clocks=clocks)
@@ -466,9 +481,36 @@ def run_system(args, spec, rank, world, local_rank):
     e2e = {"value": world * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": n * 8,
            "d2h_bytes_per_step": n * 8 + 48}
 
+    # the target of the configuration: mixed-precision batched and served
+    # solves against the plain FP64 solver one at a time (compact passes of
+    # the batched and serving workloads, same process and GPU)
+    north = None
+    if args.workload == "c2" and world == 1 and not args.no_north_star:
+        c4line, c4err = measure_c4(args, dev, world, plain_budget_s=20.0, steps=3, warmup=1,
+                                   n_err=4 if want_err else 0)
+        c5line, c5err = measure_c5(args, dev, world, args.ns_requests, n_err=4 if want_err else 0)
+        drop = ("metric", "unit", "n_gpus", "higher_is_better", "scaling", "vs_baseline")
+        north = {"c4_batched": {kk: vv for kk, vv in c4line.items() if kk not in drop},
+                 "c5_serving": {kk: vv for kk, vv in c5line.items() if kk not in drop}}
+        north["c4_batched"]["unit"] = north["c5_serving"]["unit"] = "solves/s"
+        north["c5_serving"]["note"] = (f"compact stream of {args.ns_requests} requests (the --workload c5 line "
+                                       f"runs {args.requests})")
+        if want_err:
+            err_inputs["c4"] = c4err
+            err_inputs["c5"] = c5err
+
     cpu = None
+    errs = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline_subprocess(args, rec["iters"])
+        cpu, errs = cpu_baseline_subprocess(args, rec["iters"], err_inputs if want_err else None)
+    if errs:
+        for mode, e in (errs.get("c2") or {}).items():
+            if mode in out_modes:
+                out_modes[mode]["err_vs_oracle"] = e
+        if north is not None:
+            for key, nk in (("c4", "c4_batched"), ("c5", "c5_serving")):
+                if errs.get(key) is not None:
+                    north[nk]["err_vs_oracle"] = errs[key]
 
     iters = rec["iters"]
     kk = max(k, 1)
@@ -489,7 +531,7 @@ def run_system(args, spec, rank, world, local_rank):
         "all_converged": rec["all_converged"], "max_relres": rec["max_relres"],
         "clocks": main["clocks"], "e2e": e2e, "gpu_launches": launches_per_solve * args.steps,
         "roofline": roofline, "cpu_baseline": cpu, "modes": out_modes, "multi_rhs": multi, "degrees": degrees,
-        "two_level_block_jacobi": two_level,
+        "two_level_block_jacobi": two_level, "north_star": north,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -531,7 +573,14 @@ def host_info():
     return {"host_cpu": model or "unknown", "host_nproc": os.cpu_count()}
 
 
-def cpu_baseline_subprocess(args, gpu_iters):
+def cpu_baseline_subprocess(args, gpu_iters, err_inputs=None):
+    """The CPU leg (rank 0, N = 1): `bench.py --impl reference` in a child
+    process without a GPU -- the oracle timed on one thread and on all host
+    cores; with err_inputs (GPU solutions, pickled to a temporary file) also
+    the oracle's own solves of the same problems and each GPU result's error
+    against them.  Returns (cpu_baseline record, errors or None)."""
+    import pickle
+    import tempfile
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "1", "--warmup", "0",
@@ -540,26 +589,118 @@ def cpu_baseline_subprocess(args, gpu_iters):
         cmd += ["--k", str(args.k)]
     if args.grid:
         cmd += ["--grid", str(args.grid)]
+    tmp = None
     try:
-        r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+        if err_inputs:
+            fd, tmp = tempfile.mkstemp(suffix=".pkl")
+            with os.fdopen(fd, "wb") as f:
+                pickle.dump(err_inputs, f)
+            cmd += ["--err-inputs", tmp]
+        r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1500)
         line = [ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1]
         ref = json.loads(line)
-        cb = ref.get("cpu_baseline", {})
-        return {"value": ref["value"], "unit": ref["unit"], "cores": cb.get("cores", 1), "kind": "oracle",
-                "sample": cb.get("sample"), **host_info()}
+        cb = dict(ref.get("cpu_baseline", {}))
+        cb.update({"value": ref["value"], "unit": ref["unit"], "kind": "oracle"})
+        return cb, ref.get("err_vs_oracle")
     except Exception as e:  # report, do not fail the GPU measurement
-        return {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+        return {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}, None
+    finally:
+        if tmp and os.path.exists(tmp):
+            os.remove(tmp)
 
 
 # ----------------------------------------------------------- reference ------
+# State of one oracle process of the all-cores leg (spawned: no CUDA, BLAS on
+# one thread): the scaled system, its own right-hand side and the polynomial.
+_REF_STATE = {}
+
+
+def _ref_worker_init(workload, grid, k, lo, hi, s, seed):
+    os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    import oracle as O
+    import workloads as W
+    if workload == "c1":
+        A = W.laplacian_2d_5pt(64, 64)
+        val, dis = A.val, None
+        b = W.rhs_from_solution(A, W.uniform_vector(A.n, seed=seed))
+    else:
+        A = W.diffusion_3d_7pt_lognormal(grid, seed=SEED_A)
+        val, dis = O.jacobi_scale_csr(A.rowptr, A.col, A.val, A.n)
+        b = dis * W.uniform_vector(A.n, seed=seed)
+    mv = O.csr_matvec(A.rowptr, A.col, val, A.n)
+    _REF_STATE.update(mv=mv, b=b, prm=O.cheb_params(lo, hi, s), k=k)
+
+
+def _ref_worker_run(m):
+    """m PCG iterations of this process's system; returns (seconds, iterations)."""
+    import oracle as O
+    st = _REF_STATE
+    t0 = time.perf_counter()
+    res = O.pcg(st["mv"], st["b"], lambda r: O.cheb_apply(st["mv"], r, st["prm"], st["k"]), m=st["k"], tol=TOL,
+                maxit=m)
+    return time.perf_counter() - t0, res.iters
+
+
+def oracle_errors(path, args):
+    """Error of each GPU solution against the FP64 oracle's solve of the same
+    problem (same bounds, degree, theta scale, tolerance and right-hand
+    side): ||x_gpu - x_oracle|| / ||x_oracle||, both in the original
+    (unscaled) variables."""
+    import pickle
+    import numpy as np
+    import oracle as O
+    import workloads as W
+    with open(path, "rb") as f:
+        E = pickle.load(f)
+    out = {}
+    if "c2" in E:
+        e = E["c2"]
+        A = W.diffusion_3d_7pt_lognormal(args.grid or GRID, seed=SEED_A)
+        val, dis = O.jacobi_scale_csr(A.rowptr, A.col, A.val, A.n)
+        mv = O.csr_matvec(A.rowptr, A.col, val, A.n)
+        prm = O.cheb_params(e["lo"], e["hi"], S_THETA)
+        b = dis * W.uniform_vector(A.n, seed=SEED_B)
+        t0 = time.perf_counter()
+        ro = O.pcg(mv, b, lambda r: O.cheb_apply(mv, r, prm, e["k"]), m=e["k"], tol=TOL, maxit=MAXIT)
+        xo = dis * ro.x
+        dt = time.perf_counter() - t0
+        nx = float(np.linalg.norm(xo))
+        out["c2"] = {mode: {"rel_err": float(np.linalg.norm(x - xo)) / nx, "oracle_iters": ro.iters,
+                            "oracle_true_relres": ro.true_relres, "oracle_seconds": round(dt, 1)}
+                     for mode, x in e["x"].items()}
+    for key in ("c4", "c5"):
+        if key not in E:
+            continue
+        lst = []
+        for smp in E[key]:
+            nx_, ny_, nz_ = smp["dims"]
+            c0, cx, cy, cz = smp["c"]
+            mv = O.stencil7_matvec(nx_, ny_, nz_, *O.jacobi_scale_stencil7(c0, cx, cy, cz))
+            dis = 1.0 / math.sqrt(c0)
+            prm = O.cheb_params(smp["lo"], smp["hi"], S_THETA)
+            k = smp["k"]
+            ro = O.pcg(mv, dis * smp["b"], lambda r: O.cheb_apply(mv, r, prm, k), m=k, tol=TOL, maxit=MAXIT)
+            xo = dis * ro.x
+            lst.append({"n": nx_ * ny_ * nz_, "k": k, "gpu_iters": smp["iters"], "oracle_iters": ro.iters,
+                        "rel_err": float(np.linalg.norm(smp["x"] - xo) / np.linalg.norm(xo))})
+        out[key] = {"max_rel_err": max(d["rel_err"] for d in lst) if lst else None, "samples": lst,
+                    "note": "the smallest systems of the run (first right-hand side each), FP32 apply"}
+    return out
+
+
 def run_reference(args, rank, world):
-    """The FP64 oracle as it stands, timed on the host cores: each step runs
-    `oracle_iters` PCG iterations of the full workload and the rate is
+    """The FP64 oracle as it stands, timed on the host cores.  One step runs
+    `oracle_iters` PCG iterations of the full workload; the solve rate is
     extrapolated with a full-solve iteration count (the oracle's own, from
     tests/golden/c2_oracle.json and c3_oracle.json, for the c2 and c3
-    workloads at their default sizes)."""
+    workloads at their default sizes).  Two legs: one process on one thread,
+    and (c1, c2) one process per host core, each with its own right-hand
+    side, all running the same sample at once; the line's value is the
+    all-cores aggregate.  `ms_per_step` is the measured wall time of one
+    all-cores step (the single-thread leg's in its own record)."""
     if rank != 0:
         return
+    import multiprocessing as mp
     import numpy as np
     import oracle as O
     import workloads as W
@@ -604,31 +745,75 @@ def run_reference(args, rank, world):
     prm = O.cheb_params(lo, hi, sp["s"])
     b = dis * sp["rhs"][0]
     m = args.oracle_iters
-    if full_iters is None and args.workload == "c1":
+    if full_iters is None and (args.workload == "c1" or A.n <= (1 << 18)):
         # small enough to run the whole oracle solve
         full_iters = O.pcg(mv, b, lambda r: O.cheb_apply(mv, r, prm, k), m=k, tol=TOL, maxit=MAXIT).iters
     if full_iters is None:
         full_iters = args.gpu_iters or 1
         iters_src = "GPU solver's (equal within +-1 in the parity tests)"
-    times = []
+    mm = min(m, full_iters)
+
+    # single thread, in this process
+    per_iter, step_s = [], []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        res = O.pcg(mv, b, lambda r: O.cheb_apply(mv, r, prm, k), m=k, tol=TOL, maxit=min(m, full_iters))
+        res = O.pcg(mv, b, lambda r: O.cheb_apply(mv, r, prm, k), m=k, tol=TOL, maxit=mm)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
-            times.append(dt / max(res.iters, 1))
-    t_iter = statistics.median(times)
-    value = 1.0 / (t_iter * max(full_iters, 1))
-    sample = (f"{min(m, full_iters)} PCG iterations (k={k}) of the full system per step, extrapolated to the "
-              f"{iters_src} {full_iters}-iteration solve; scipy sparse matvec + numpy, 1 thread")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * full_iters * 1e3,
+            per_iter.append(dt / max(res.iters, 1))
+            step_s.append(dt)
+    t_iter = statistics.median(per_iter)
+    single = {"value": 1.0 / (t_iter * full_iters), "unit": "solves/s", "cores": 1,
+              "ms_per_step": round(1e3 * statistics.median(step_s), 2),
+              "extrapolated_ms_per_solve": round(1e3 * t_iter * full_iters, 1)}
+
+    # all cores: one spawned process per core (c1, c2)
+    cores = args.cores or (os.cpu_count() or 1)
+    allc = None
+    if args.workload in ("c1", "c2") and cores > 1:
+        del A, val, mv
+        ctx = mp.get_context("spawn")
+        pools = [ctx.Pool(1, initializer=_ref_worker_init,
+                          initargs=(args.workload, args.grid or GRID, k, lo, hi, sp["s"], SEED_B + 100 + i))
+                 for i in range(cores)]
+        try:
+            for p_ in pools:   # wait until every process has built its system
+                p_.apply(_ref_worker_run, (1,))
+            walls, its = [], []
+            for i in range(args.warmup + args.steps):
+                t0 = time.perf_counter()
+                rs_ = [p_.apply_async(_ref_worker_run, (mm,)) for p_ in pools]
+                got = [r_.get() for r_ in rs_]
+                wall = time.perf_counter() - t0
+                if i >= args.warmup:
+                    walls.append(wall)
+                    its.append(sum(g[1] for g in got))
+        finally:
+            for p_ in pools:
+                p_.terminate()
+        wall = statistics.median(walls)
+        it_per_step = statistics.median(its)
+        allc = {"value": it_per_step / (wall * full_iters), "unit": "solves/s", "cores": cores,
+                "processes": cores, "ms_per_step": round(1e3 * wall, 2),
+                "extrapolated_ms_per_solve": round(1e3 * wall / mm * full_iters, 1)}
+    main_leg = allc or single
+    legs = (f"one process per core ({cores}), each its own right-hand side, all at once" if allc
+            else "one process, one thread")
+    sample = (f"{mm} PCG iterations (k={k}) of the full system per step and process, extrapolated to the "
+              f"{iters_src} {full_iters}-iteration solve; scipy sparse matvec + numpy, BLAS on 1 thread; {legs}")
+    line = {"impl": "reference", "metric": METRIC, "value": main_leg["value"], "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": main_leg["ms_per_step"],
+            "extrapolated_ms_per_solve": main_leg["extrapolated_ms_per_solve"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generators, no dataset)",
             "config": {"workload": sp["workload"], "degree_k": k, "theta_scale": sp["s"], "tol": TOL},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample,
+            "cpu_baseline": {"value": main_leg["value"], "unit": "solves/s", "cores": main_leg["cores"],
+                             "kind": "oracle", "sample": sample, "single_thread": single, "all_cores": allc,
                              **host_info()},
-            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": main_leg["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    if args.err_inputs:
+        line["err_vs_oracle"] = oracle_errors(args.err_inputs, args)
     print(json.dumps(line), flush=True)
 
 
@@ -657,8 +842,20 @@ def c4_systems(count=256, seed=41):
 def run_c4(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
+    line, _ = measure_c4(args, torch.device("cuda", local_rank), world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_c4(args, dev, world, plain_budget_s=90.0, steps=None, warmup=None, n_err=0):
+    """The batched workload; returns (its JSON record, error samples).  The
+    error samples are the n_err smallest systems' first right-hand side and
+    batched solution (host arrays) for the oracle comparison of the CPU leg."""
+    import numpy as np
+    import torch
     import paper_2008_01440_gb300 as nc
-    dev = torch.device("cuda", local_rank)
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     sy = c4_systems(args.c4_systems)
     pairs = []
     for s in sy:
@@ -687,13 +884,13 @@ def run_c4(args, rank, world, local_rank):
             nc.pcg_batch_release(eng, sl)
         return res
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         one_batch()
     torch.cuda.synchronize()
     clk = start_clocks(torch, dev)
     times = []
     _, l0 = nc.pcg_batch_stats(eng)
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
         res = one_batch()
         torch.cuda.synchronize()
@@ -726,6 +923,19 @@ def run_c4(args, rank, world, local_rank):
     del hb, hx, db
     t_step = statistics.median(times)
     iters = [r["iters"] for r in res]
+    # error samples: the smallest systems' first right-hand side
+    err_samples = []
+    if n_err > 0:
+        first = {}
+        for i, (s_, _) in enumerate(pairs):
+            first.setdefault(id(s_), i)
+        order = sorted(first.values(), key=lambda i: pairs[i][0]["st"].n)[:n_err]
+        for i in order:
+            s_, b_ = pairs[i]
+            st_ = s_["st"]
+            err_samples.append({"dims": [st_.nx, st_.ny, st_.nz], "c": [st_.c0, st_.cx, st_.cy, st_.cz],
+                                "lo": s_["lo"], "hi": s_["hi"], "k": s_["k"], "b": b_.cpu().numpy(),
+                                "x": xs[i].cpu().numpy(), "iters": res[i]["iters"]})
     ok = all(r["status"] == 0 and r["true_relres"] <= 2 * TOL for r in res)
     # algorithmic bytes of the whole batch: per slot and iteration, k float32
     # stencil steps (16 B per unknown), q = A p (16 B), x/r/p/q update with
@@ -756,7 +966,7 @@ def run_c4(args, rank, world, local_rank):
                  "all_converged": all(r["status"] == 0 for r in res64)}
 
     # plain FP64 one system at a time (same right-hand sides), bounded sample
-    t_budget = 90.0
+    t_budget = plain_budget_s
     t0 = time.perf_counter()
     done_pairs = 0
     for (s, b), x in zip(pairs, xs):
@@ -775,7 +985,7 @@ def run_c4(args, rank, world, local_rank):
     frac = sum(work[:done_pairs]) / sum(work)
     plain_batch_rate = len(pairs) / (t_plain / frac)
     line = {"metric": METRIC, "value": round(len(pairs) / t_step, 3), "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 3),
+            "steps": steps, "warmup": warmup, "ms_per_step": round(t_step * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-apply+f64-outer",
             "data": "synthetic (seeded generators; RHS from torch's CUDA generator, seeded)",
             "config": {"workload": "batched: 256 anisotropic 7-point Laplacians, sides U{16..96}, weights U[0.01,1], "
@@ -794,8 +1004,7 @@ def run_c4(args, rank, world, local_rank):
             "e2e": {"value": round(len(pairs) / t_e2e, 3), "unit": "solves/s", "h2d_bytes_per_step": e2e_bytes,
                     "d2h_bytes_per_step": e2e_bytes},
             "gpu_launches": launches, "f64_apply": f64_apply}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line, err_samples
 
 
 def run_c4_csr(args, rank, world, local_rank):
@@ -883,12 +1092,21 @@ def c5_requests(nreq, dev, torch, seed=51):
 
 
 def run_c5(args, rank, world, local_rank):
-    import numpy as np
     import torch
     torch.cuda.set_device(local_rank)
+    line, _ = measure_c5(args, torch.device("cuda", local_rank), world, args.requests)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_c5(args, dev, world, nreq, n_err=0):
+    """The serving workload with `nreq` requests; returns (its JSON record,
+    error samples: the n_err smallest requests' right-hand side and solution
+    from the continuous-batching run)."""
+    import numpy as np
+    import torch
     from paper_2008_01440_gb300 import serving
-    dev = torch.device("cuda", local_rank)
-    reqs = c5_requests(args.requests, dev, torch)
+    reqs = c5_requests(nreq, dev, torch)
 
     def clone(r):
         return serving.Request(rid=r.rid, arrival=r.arrival, nx=r.nx, ny=r.ny, nz=r.nz, c=r.c, lmin=r.lmin,
@@ -927,6 +1145,10 @@ def run_c5(args, rank, world, local_rank):
     ok_pl = all(r.result.get("status") == 0 for r in plain)
     err = max(float(torch.linalg.norm(a.x - b.x) / torch.linalg.norm(b.x)) for a, b in zip(reqs[:16], plain[:16]))
     sizes = [r.nx for r in reqs]
+    err_samples = []
+    for r in sorted(reqs, key=lambda r_: r_.n)[:n_err]:
+        err_samples.append({"dims": [r.nx, r.ny, r.nz], "c": list(r.c), "lo": r.lmin, "hi": r.lmax, "k": r.k,
+                            "b": r.b.cpu().numpy(), "x": r.x.cpu().numpy(), "iters": r.result["iters"]})
     line = {"metric": METRIC, "value": round(len(reqs) / span_cb, 3), "unit": "solves/s", "n_gpus": world,
             "steps": len(reqs), "warmup": 0, "ms_per_step": round(1e3 * span_cb / len(reqs), 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-apply+f64-outer",
@@ -955,8 +1177,7 @@ def run_c5(args, rank, world, local_rank):
                          "peak_source": peak_hbm()[1],
                          "kernel": "whole serving run (all engine kernels; algorithmic bytes / wall time, "
                                    "arrival-limited: the GPU waits for requests)"}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line, err_samples
 
 
 # ------------------------------------------------------ paper workload ----
@@ -1090,6 +1311,9 @@ def run_fd3d(args, rank, world, local_rank):
 
 def main():
     args = parse()
+    if args.impl == "reference":   # the oracle's BLAS on one thread per process
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(var, "1")
     rank, world, local_rank = dist_env()
     if world > 1:
         import torch.distributed as dist

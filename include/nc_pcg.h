@@ -56,7 +56,9 @@ typedef enum {
     NC_ERR_BREAKDOWN = 6,    /* NaN or Inf in a reduction                             */
     NC_ERR_UNSUPPORTED = 7,  /* option combination not implemented for this format    */
     NC_ERR_SCRATCH_LIMIT = 8, /* n above the fixed scratch of nc_apply_poly_csr_noalloc */
-    NC_ERR_ADMISSION = 9     /* batch engine: no free slot or not enough pooled memory */
+    NC_ERR_ADMISSION = 9,    /* batch engine: no free slot or not enough pooled memory */
+    NC_ERR_TIMEOUT = 10      /* a staged step kernel's bounded wait for its own copies
+                                ran out; the results of that call are not valid    */
 } nc_status;
 
 /* Value type of the matrix inside P_k(A) (the outer CG stays float64). */
@@ -98,6 +100,28 @@ typedef enum {
  * (use_graph = 2) runs the Chebyshev form only. */
 typedef enum { NC_POLY_CHEBYSHEV = 0, NC_POLY_NEWTON = 1 } nc_poly_form;
 
+/* Kernel variant of the fused product steps (Algorithm 2's loop body, and
+ * q = A p with (p, q)) on the SELL-32 layouts.  DIRECT: one row per thread,
+ * every operand loaded from global memory when it is needed.  STAGED
+ * (offset-pattern layout, PSELL): persistent CTAs; each 256-row tile's
+ * matrix slices and its rows of r and x_{k-2} are brought into shared memory
+ * by bulk asynchronous copies a few tiles ahead of their use, so the HBM
+ * stream does not wait on the gathers of x_{k-1}.  Both compute the same
+ * fma chain in the same order (identical results for the same grid).  TUNE:
+ * pcg_setup times a small set of candidates of both variants (stages in
+ * flight, CTAs per SM, L2 prefetch distance, CTAs of the dot-product steps)
+ * on the solver's own operator and keeps the fastest for the plain steps and
+ * for the steps with a dot product; pcg_tune_candidate lists what was
+ * measured.  AUTO (default): TUNE for PSELL operators of at least 2^16 rows,
+ * DIRECT otherwise.  Layouts other than PSELL, and the stencil and block
+ * kernels, always run their single variant. */
+typedef enum {
+    NC_STEP_AUTO = 0,
+    NC_STEP_DIRECT = 1,
+    NC_STEP_STAGED = 2,
+    NC_STEP_TUNE = 3
+} nc_step_kernel;
+
 typedef struct {
     int apply_dtype;   /* nc_dtype: F64 = plain method; F32: float32 matrix and
                           vectors inside P_k; BF16: bfloat16 matrix values,
@@ -120,6 +144,20 @@ typedef struct {
                           7-point operator); else the graph.                    */
     int spmv_format;   /* nc_format of the solver's product kernels (AUTO).    */
     int poly_form;     /* nc_poly_form: how z = P(A) r is evaluated.           */
+    int step_kernel;   /* nc_step_kernel (AUTO).  The six fields below fix a
+                          STAGED or DIRECT choice; 0 = the library default.   */
+    int step_stages;   /* STAGED: tiles in flight per CTA, 2..4 (default 2)    */
+    int step_ctas_per_sm; /* STAGED: resident CTAs per SM (default 6, capped by
+                          what the device holds)                               */
+    int step_rows_per_thread; /* STAGED: 1 or 2 rows per thread (default 1):
+                          tiles of 256 or 512 rows, the gathers of both rows
+                          in flight together                                    */
+    int step_tile_order; /* STAGED: 0 (default) CTA b takes tiles b, b + grid,
+                          ...; 1: a contiguous run of tiles per CTA            */
+    int prefetch_tiles;/* DIRECT float kernels: L2 prefetch distance in 256-row
+                          tiles (default 2 x the SM count; < 0: off)           */
+    int red_ctas_per_sm; /* DIRECT steps with a dot product: persistent CTAs
+                          per SM (default 8)                                    */
 } nc_options;
 
 typedef struct {
@@ -136,7 +174,33 @@ typedef struct {
     double tune_us_plain; /* TUNE: measured step time, plain layout (us)   */
     double tune_us_sliced;/* TUNE: measured step time, sliced layout (us)  */
     int64_t patterns;     /* PSELL: distinct offset sets stored; else 0     */
+    int32_t step_kernel;  /* NC_STEP_DIRECT or NC_STEP_STAGED: plain steps  */
+    int32_t dot_step_kernel; /* the same for the steps with a dot product   */
+    int32_t step_stages, step_ctas_per_sm;  /* STAGED shape, plain steps     */
+    int32_t step_rows_per_thread, step_tile_order;
+    int32_t dot_step_stages, dot_step_ctas_per_sm; /* and dot-product steps */
+    int32_t dot_step_rows_per_thread, dot_step_tile_order;
+    int32_t prefetch_tiles, red_ctas_per_sm; /* DIRECT configuration         */
+    int32_t tune_candidates; /* TUNE: candidates measured (pcg_tune_candidate) */
+    int32_t num_sms;      /* SM count of the device the solver was set up on */
+    int32_t faults;       /* 1: a staged kernel's bounded wait ran out (the
+                             results of that call are not valid)              */
+    int32_t reserved0;
 } nc_solver_info;
+
+/* One configuration measured by the tuner (pcg_setup with step_kernel =
+ * TUNE, or AUTO on a large PSELL operator). */
+typedef struct {
+    int32_t op;           /* 0: the operator inside P_k, plain step (DOT 0);
+                             1: inside P_k, last step with (r, z);
+                             2: the float64 operator, q = A p with (p, q)   */
+    int32_t step_kernel;  /* NC_STEP_DIRECT or NC_STEP_STAGED              */
+    int32_t stages, ctas_per_sm, rows_per_thread, tile_order; /* STAGED    */
+    int32_t prefetch_tiles, red_ctas_per_sm;                   /* DIRECT    */
+    double us;            /* mean duration of one launch (CUDA events)     */
+    int32_t chosen;       /* 1: kept for that operator and step kind       */
+    int32_t reserved0;
+} nc_tune_candidate;
 
 typedef struct {
     int32_t iters;        /* PCG iterations                                      */
@@ -302,8 +366,15 @@ NC_API nc_status pcg_solve_multi(nc_solver S, int m, const double* B_dev, double
                                  void* stream, nc_result* res);
 
 /* Layout and parameters the solver chose (info: caller-owned).  NC_ERR_ARG
- * for a null argument. */
+ * for a null argument.  Reads the solver's fault flag from the device
+ * (synchronises the device memory copy). */
 NC_API nc_status pcg_get_info(nc_solver S, nc_solver_info* info);
+
+/* Candidate i (0 <= i < info.tune_candidates) timed by the tuner during
+ * pcg_setup, in the order measured; NC_ERR_ARG when i is out of range or an
+ * argument is null.  Host only.  Not in the paper: launch parameters of the
+ * product kernels chosen by measurement on the solver's own matrix. */
+NC_API nc_status pcg_tune_candidate(nc_solver S, int i, nc_tune_candidate* out);
 
 /* Frees the solver's workspaces and layouts (not the matrix handle); the
  * frees wait for work still running on the device.  NC_ERR_ARG for NULL. */

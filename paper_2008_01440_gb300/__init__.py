@@ -22,6 +22,7 @@ from .binding import (  # noqa: F401
     NC_ERR_MAXIT,
     NC_ERR_OOM,
     NC_ERR_SCRATCH_LIMIT,
+    NC_ERR_TIMEOUT,
     NC_ERR_UNSUPPORTED,
     NC_F32,
     NC_F64,
@@ -31,6 +32,10 @@ from .binding import (  # noqa: F401
     NC_FORMAT_SELL,
     NC_FORMAT_TUNE,
     NC_OK,
+    NC_STEP_AUTO,
+    NC_STEP_DIRECT,
+    NC_STEP_STAGED,
+    NC_STEP_TUNE,
     LIB_PATH,
     Matrix,
     NcError,
@@ -68,4 +73,5 @@ from .binding import (  # noqa: F401
     pcg_solve,
     pcg_solve_host,
     pcg_solve_multi,
+    pcg_tune_candidates,
 )

@@ -22,7 +22,7 @@ if not os.path.exists(LIB_PATH):
 lib = ctypes.CDLL(LIB_PATH)
 
 NC_OK, NC_ERR_ARG, NC_ERR_CUDA, NC_ERR_OOM, NC_ERR_INDEFINITE, NC_ERR_MAXIT, NC_ERR_BREAKDOWN, \
-    NC_ERR_UNSUPPORTED, NC_ERR_SCRATCH_LIMIT, NC_ERR_ADMISSION = range(10)
+    NC_ERR_UNSUPPORTED, NC_ERR_SCRATCH_LIMIT, NC_ERR_ADMISSION, NC_ERR_TIMEOUT = range(11)
 NC_F64, NC_F32, NC_BF16 = 0, 1, 2
 _DTYPES = {"f64": NC_F64, "f32": NC_F32, "bf16": NC_BF16}
 # statuses a solve may end with while still returning a meaningful iterate
@@ -34,10 +34,18 @@ _FORMATS = {"auto": NC_FORMAT_AUTO, "csr": NC_FORMAT_CSR, "sell": NC_FORMAT_SELL
             "psell": NC_FORMAT_PSELL}
 
 
+NC_STEP_AUTO, NC_STEP_DIRECT, NC_STEP_STAGED, NC_STEP_TUNE = 0, 1, 2, 3
+_STEPS = {"auto": NC_STEP_AUTO, "direct": NC_STEP_DIRECT, "staged": NC_STEP_STAGED, "tune": NC_STEP_TUNE}
+_STEP_NAMES = {NC_STEP_DIRECT: "direct", NC_STEP_STAGED: "staged"}
+
+
 class nc_options(ctypes.Structure):
     _fields_ = [("apply_dtype", ctypes.c_int), ("rr_period", ctypes.c_int),
                 ("x0_is_zero", ctypes.c_int), ("use_graph", ctypes.c_int), ("spmv_format", ctypes.c_int),
-                ("poly_form", ctypes.c_int)]
+                ("poly_form", ctypes.c_int), ("step_kernel", ctypes.c_int), ("step_stages", ctypes.c_int),
+                ("step_ctas_per_sm", ctypes.c_int), ("step_rows_per_thread", ctypes.c_int),
+                ("step_tile_order", ctypes.c_int), ("prefetch_tiles", ctypes.c_int),
+                ("red_ctas_per_sm", ctypes.c_int)]
 
 
 class nc_solver_info(ctypes.Structure):
@@ -45,7 +53,22 @@ class nc_solver_info(ctypes.Structure):
                 ("apply_dtype", ctypes.c_int32), ("persistent", ctypes.c_int32), ("padding", ctypes.c_double),
                 ("theta", ctypes.c_double), ("delta", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("shift", ctypes.c_double), ("tune_us_plain", ctypes.c_double), ("tune_us_sliced", ctypes.c_double),
-                ("patterns", ctypes.c_int64)]
+                ("patterns", ctypes.c_int64), ("step_kernel", ctypes.c_int32), ("dot_step_kernel", ctypes.c_int32),
+                ("step_stages", ctypes.c_int32), ("step_ctas_per_sm", ctypes.c_int32),
+                ("step_rows_per_thread", ctypes.c_int32), ("step_tile_order", ctypes.c_int32),
+                ("dot_step_stages", ctypes.c_int32), ("dot_step_ctas_per_sm", ctypes.c_int32),
+                ("dot_step_rows_per_thread", ctypes.c_int32), ("dot_step_tile_order", ctypes.c_int32),
+                ("prefetch_tiles", ctypes.c_int32), ("red_ctas_per_sm", ctypes.c_int32),
+                ("tune_candidates", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("faults", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
+
+
+class nc_tune_candidate(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("step_kernel", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("rows_per_thread", ctypes.c_int32), ("tile_order", ctypes.c_int32),
+                ("prefetch_tiles", ctypes.c_int32),
+                ("red_ctas_per_sm", ctypes.c_int32), ("us", ctypes.c_double), ("chosen", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
 
 
 class nc_result(ctypes.Structure):
@@ -87,6 +110,7 @@ _SIGS = {
                                        ctypes.POINTER(nc_result)]),
     "pcg_destroy": (ctypes.c_int, [_vp]),
     "pcg_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(nc_solver_info)]),
+    "pcg_tune_candidate": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(nc_tune_candidate)]),
     "nc_apply_poly_csr_noalloc": (ctypes.c_int, [_i64, _vp, _vp, _vp, _dbl, _dbl, ctypes.c_int, _dbl, _vp, _vp,
                                                  _vp]),
     "nc_apply_poly_noalloc_max_n": (_i64, []),
@@ -276,7 +300,8 @@ _POLY = {"chebyshev": 0, "newton": 1}
 
 
 def make_options(apply_dtype="f64", rr_period=0, x0_is_zero=False, use_graph=True, spmv_format="auto",
-                 persistent=False, poly="chebyshev") -> nc_options:
+                 persistent=False, poly="chebyshev", step_kernel="auto", step_stages=0, step_ctas_per_sm=0,
+                 step_rows_per_thread=0, step_tile_order=0, prefetch_tiles=0, red_ctas_per_sm=0) -> nc_options:
     o = nc_options()
     lib.nc_options_default(ctypes.byref(o))
     o.spmv_format = _FORMATS[spmv_format] if isinstance(spmv_format, str) else int(spmv_format)
@@ -285,6 +310,13 @@ def make_options(apply_dtype="f64", rr_period=0, x0_is_zero=False, use_graph=Tru
     o.x0_is_zero = int(bool(x0_is_zero))
     o.use_graph = 2 if persistent else int(bool(use_graph))
     o.poly_form = _POLY[poly] if isinstance(poly, str) else int(poly)
+    o.step_kernel = _STEPS[step_kernel] if isinstance(step_kernel, str) else int(step_kernel)
+    o.step_stages = int(step_stages)
+    o.step_ctas_per_sm = int(step_ctas_per_sm)
+    o.step_rows_per_thread = int(step_rows_per_thread)
+    o.step_tile_order = int(step_tile_order)
+    o.prefetch_tiles = int(prefetch_tiles)
+    o.red_ctas_per_sm = int(red_ctas_per_sm)
     return o
 
 
@@ -304,7 +336,27 @@ def pcg_get_info(S: Solver) -> dict:
     d["persistent"] = bool(d["persistent"])
     d["spmv_format"] = {NC_FORMAT_CSR: "csr", NC_FORMAT_SELL: "sell", NC_FORMAT_PSELL: "psell"}.get(
         d["spmv_format"], d["spmv_format"])
+    d["step_kernel"] = _STEP_NAMES.get(d["step_kernel"], d["step_kernel"])
+    d["dot_step_kernel"] = _STEP_NAMES.get(d["dot_step_kernel"], d["dot_step_kernel"])
     return d
+
+
+_TUNE_OPS = {0: "step", 1: "last_step_dot", 2: "q_dot"}
+
+
+def pcg_tune_candidates(S: Solver) -> list:
+    """Every launch configuration the tuner timed during pcg_setup, in order
+    (empty when the solver was not tuned)."""
+    out = []
+    for i in range(pcg_get_info(S)["tune_candidates"]):
+        c = nc_tune_candidate()
+        _check(lib.pcg_tune_candidate(S.handle, i, ctypes.byref(c)), "pcg_tune_candidate")
+        d = {f: getattr(c, f) for f, _ in c._fields_ if f != "reserved0"}
+        d["op"] = _TUNE_OPS.get(d["op"], d["op"])
+        d["step_kernel"] = _STEP_NAMES.get(d["step_kernel"], d["step_kernel"])
+        d["chosen"] = bool(d["chosen"])
+        out.append(d)
+    return out
 
 
 def pcg_apply_poly(S: Solver, v, z, stream=None):

@@ -115,7 +115,8 @@ cudaError_t bsr_dispatch(bool sliced, int nb, const int32_t* ptr, const int32_t*
                          cudaStream_t st) {
     using AT = typename AccOf<XT>::type;
     const int tiles = (nb + kBlock - 1) / kBlock;
-    const int grid = (dot == 0 || tiles < kRedGrid) ? tiles : kRedGrid;
+    const int red = vec_grid_max();
+    const int grid = (dot == 0 || tiles < red) ? tiles : red;
     const StepCoef<AT> c = make_coef<AT>(ca, cb, cc, cd);
     const VT* v = static_cast<const VT*>(val);
     const XT* uu = static_cast<const XT*>(u);

@@ -17,9 +17,46 @@ namespace nc {
 
 constexpr int kBlock = 256;           // threads per CTA of the row kernels
 constexpr int kChunk = 2048;          // nonzeros staged in shared memory per pass
-constexpr int kSMs = 152;             // GB300 streaming multiprocessors
-constexpr int kVecGrid = kSMs * 8;    // CTAs of the grid-stride vector kernels (2048 threads/SM)
-constexpr int kRedGrid = kSMs * 8;    // CTAs of the persistent reduction variants of the step kernels
+constexpr int kCtasPerSm = 8;         // 2048 threads per SM at kBlock threads per CTA
+
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// read once per device; 152 on GB300).  Grid sizes of the persistent and
+// grid-stride kernels are multiples of it.
+int num_sms();
+// CTAs of the grid-stride vector kernels (kCtasPerSm per SM)
+inline int vec_grid_max() { return num_sms() * kCtasPerSm; }
+// Upper bound of vec_grid_max() over any device (partial-sum buffers are
+// sized with it so that a solver never depends on the device it was set up on)
+constexpr int kMaxGrid = 1024 * kCtasPerSm;
+
+// Launch choices of the SELL-32 step kernels (sliced and offset-pattern
+// layouts), fixed per solver at setup -- by default, or by the tuner, which
+// times candidates on the solver's own operator.
+enum StepVariant : int {
+    STEP_DIRECT = 0,   // one row per thread, loads straight from global memory
+    STEP_STAGED = 1    // persistent CTAs; each 256-row tile's slices (and its r and
+                       // x_{k-2} rows) brought into shared memory by bulk
+                       // asynchronous copies, `stages` tiles ahead
+};
+struct StepTune {
+    int variant = STEP_DIRECT;       // plain steps (no dot product)
+    int dot_variant = STEP_DIRECT;   // steps with a dot product
+    int stages = 3;         // staged: tiles in flight per CTA (2..4)
+    int ctas_per_sm = 2;    // staged: resident CTAs per SM
+    int rpt = 1;            // staged: rows per thread (1 or 2; tiles of 256 rpt rows)
+    int contig = 0;         // staged: 1 = each CTA takes a contiguous run of tiles
+    int dot_stages = 3;     // the same four for the staged steps with a dot product
+    int dot_ctas_per_sm = 2;
+    int dot_rpt = 1;
+    int dot_contig = 0;
+    int lookahead = -1;     // direct float kernels: L2 prefetch distance in tiles
+                            // (-1: two waves, 2 x num_sms(); 0: off)
+    int red_ctas_per_sm = kCtasPerSm;   // direct kernels with a dot product:
+                                        // persistent CTAs per SM
+    int vcap = 0;           // staged: matrix entries of the largest 256-row tile
+    int vcap2 = 0;          // and of the largest 512-row tile (rpt = 2)
+    int npoff = 0;          // staged: entries of the offset-pattern table
+};
 
 // What the last CTA of a reduction does with the finished sum.
 enum Fin : int {
@@ -39,7 +76,9 @@ struct PcgScalars {
     int iter, maxit, done, status;
     int n_dot, n_prec, rr_period, rr_skip;   // residual replacement: period, and
                                              // "skip it this iteration" flag
-    int n_replace, pad0, pad1, pad2;
+    int n_replace;
+    int fault;       // set by a kernel whose bounded wait on its own copies ran out
+    int pad1, pad2;
 };
 
 struct Reduce {
@@ -187,7 +226,24 @@ struct SellPat {
 cudaError_t launch_sell_step(int n, const int32_t* slice_ptr, const int32_t* col, const SellPat& pat,
                              const void* val, int vdt, bool x_f32, bool y_f64, const void* u, const void* w,
                              const void* r, void* y, double ca, double cb, double cc, double cd, int dot,
-                             const double* rdot, const Reduce& R, const int* done, cudaStream_t st);
+                             const double* rdot, const Reduce& R, const int* done, cudaStream_t st,
+                             const StepTune& tune = StepTune());
+// The staged variant (nc_sell_staged.cu).  Returns cudaErrorNotSupported when
+// it does not apply (no scalar block to report a fault in, unaligned vectors
+// or values, a stage larger than shared memory); the caller then runs the
+// direct kernel.  *R.S->fault is set if a wait for a tile's copies ran out.
+cudaError_t launch_sell_staged(int n, const int32_t* slice_ptr, const int32_t* col, const SellPat& pat,
+                               const void* val, int vdt, bool x_f32, bool y_f64, const void* u, const void* w,
+                               const void* r, void* y, double ca, double cb, double cc, double cd, int dot,
+                               const double* rdot, const Reduce& R, const int* done, cudaStream_t st,
+                               const StepTune& tune);
+// Resident CTAs per SM the staged variant would run with for this value /
+// vector type, dot kind and tune (at most tune.ctas_per_sm); 0 when it cannot
+// run on the current device.
+int sell_staged_ctas(int vdt, bool x_f32, bool y_f64, int dot, bool unit, const StepTune& tune);
+// Largest number of matrix entries of any tile of `per_tile` slices of a
+// SELL-32 layout with host slice offsets hsptr[0..nslices].
+int sell_max_tile_entries(const int32_t* hsptr, int nslices, int per_tile);
 // Pattern layout construction from CSR: per-slice offset sets (a counting
 // pass with off null, then a writing pass at opos), then the slot-major fill.
 cudaError_t launch_psell_merge(int n, const int32_t* rowptr, const int32_t* col, const int32_t* opos, int32_t* cnt,

@@ -69,7 +69,8 @@ cudaError_t step_dispatch(int n, const int32_t* rowptr, const int32_t* col, cons
                           double cb, double cc, double cd, int dot, const double* rdot,
                           const Reduce& R, const int* done, cudaStream_t st) {
     const int tiles = (n + kBlock - 1) / kBlock;
-    const int grid = (dot == 0 || tiles < kRedGrid) ? tiles : kRedGrid;
+    const int red = vec_grid_max();
+    const int grid = (dot == 0 || tiles < red) ? tiles : red;
     const VT* v = static_cast<const VT*>(val);
     const XT* uu = static_cast<const XT*>(u);
     const XT* ww = static_cast<const XT*>(w);

@@ -34,13 +34,13 @@ __global__ void __launch_bounds__(kBlock)
 sell_mstep_kernel(const int n, const int ld, const int32_t* __restrict__ slice_ptr,
                   const int32_t* __restrict__ col, const SellPat pat, const VT* __restrict__ val,
                   const XT* __restrict__ u, const XT* __restrict__ w, const XT* __restrict__ r, YT* __restrict__ y,
-                  const StepCoef<typename AccOf<XT>::type> cf, const PcgScalars* __restrict__ Sm) {
+                  const StepCoef<typename AccOf<XT>::type> cf, const PcgScalars* __restrict__ Sm, const int ahead) {
     using AT = typename AccOf<XT>::type;
     constexpr int G = M >= 8 ? 2 : (M >= 4 ? 4 : 8);
     if (Sm != nullptr && all_done(Sm, M)) return;
     if constexpr (sizeof(AT) == 4)
-        if (threadIdx.x == 0)
-            prefetch_sell_tile((int)blockIdx.x + kPrefetchAhead, n, slice_ptr, PAT ? nullptr : col, val);
+        if (threadIdx.x == 0 && ahead > 0)
+            prefetch_sell_tile((int)blockIdx.x + ahead, n, slice_ptr, PAT ? nullptr : col, val);
     const int row = blockIdx.x * kBlock + threadIdx.x;
     if (row >= n) return;
     const int s = row >> 5;
@@ -109,6 +109,7 @@ cudaError_t mstep_launch_m(int n, int ld, const int32_t* sptr, const int32_t* co
     using AT = typename AccOf<XT>::type;
     const StepCoef<AT> c = make_coef<AT>(ca, cb, cc, cd);
     const unsigned grid = (unsigned)((n + kBlock - 1) / kBlock);
+    const int ahead = default_lookahead();
     const VT* v = static_cast<const VT*>(val);
     const XT* uu = static_cast<const XT*>(u);
     const XT* ww = static_cast<const XT*>(w);
@@ -118,19 +119,19 @@ cudaError_t mstep_launch_m(int n, int ld, const int32_t* sptr, const int32_t* co
         if (cd == 1.0) {
             if (pat.pstart != nullptr)
                 sell_mstep_kernel<VT, XT, YT, M, true, true><<<grid, kBlock, 0, st>>>(n, ld, sptr, col, pat, v, uu,
-                                                                                      ww, rr, yy, c, Sm);
+                                                                                      ww, rr, yy, c, Sm, ahead);
             else
                 sell_mstep_kernel<VT, XT, YT, M, false, true><<<grid, kBlock, 0, st>>>(n, ld, sptr, col, pat, v, uu,
-                                                                                       ww, rr, yy, c, Sm);
+                                                                                       ww, rr, yy, c, Sm, ahead);
             return cudaGetLastError();
         }
     }
     if (pat.pstart != nullptr)
         sell_mstep_kernel<VT, XT, YT, M, true, false><<<grid, kBlock, 0, st>>>(n, ld, sptr, col, pat, v, uu, ww, rr,
-                                                                               yy, c, Sm);
+                                                                               yy, c, Sm, ahead);
     else
         sell_mstep_kernel<VT, XT, YT, M, false, false><<<grid, kBlock, 0, st>>>(n, ld, sptr, col, pat, v, uu, ww, rr,
-                                                                                yy, c, Sm);
+                                                                                yy, c, Sm, ahead);
     return cudaGetLastError();
 }
 

@@ -116,12 +116,13 @@ __global__ void __launch_bounds__(kBlock)
 sell_step_kernel(const int n, const int32_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
                  const SellPat pat, const VT* __restrict__ val, const XT* __restrict__ u, const XT* __restrict__ w,
                  const XT* __restrict__ r, YT* __restrict__ y, const StepCoef<typename AccOf<XT>::type> c,
-                 const double* __restrict__ rdot, const Reduce R, const int* __restrict__ done) {
+                 const double* __restrict__ rdot, const Reduce R, const int* __restrict__ done, const int ahead) {
     if (done != nullptr && *done) return;
     if constexpr (DOT == 0) {
         // one 256-row tile per CTA
         if constexpr (sizeof(typename AccOf<XT>::type) == 4)
-            if (threadIdx.x == 0) prefetch_sell_tile((int)blockIdx.x + kPrefetchAhead, n, slice_ptr, PAT ? nullptr : col, val);
+            if (threadIdx.x == 0 && ahead > 0)
+                prefetch_sell_tile((int)blockIdx.x + ahead, n, slice_ptr, PAT ? nullptr : col, val);
         const int row = blockIdx.x * kBlock + threadIdx.x;
         if (row < n) sell_row<VT, XT, YT, 0, PAT, UNIT>(row, n, slice_ptr, col, pat, val, u, w, r, y, c, rdot);
     } else {
@@ -131,7 +132,8 @@ sell_step_kernel(const int n, const int32_t* __restrict__ slice_ptr, const int32
         const int ntiles = (n + kBlock - 1) / kBlock;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             if constexpr (sizeof(typename AccOf<XT>::type) == 4)
-                if (threadIdx.x == 0) prefetch_sell_tile(tile + (int)gridDim.x, n, slice_ptr, PAT ? nullptr : col, val);
+                if (threadIdx.x == 0 && ahead > 0)
+                    prefetch_sell_tile(tile + (int)gridDim.x, n, slice_ptr, PAT ? nullptr : col, val);
             const int row = tile * kBlock + threadIdx.x;
             if (row < n)
                 dv += sell_row<VT, XT, YT, DOT, PAT, UNIT>(row, n, slice_ptr, col, pat, val, u, w, r, y, c, rdot);
@@ -289,17 +291,19 @@ template <typename VT, typename XT, typename YT, bool PAT, bool UNIT>
 cudaError_t sell_dispatch_pu(int n, const int32_t* sptr, const int32_t* col, const SellPat& pat, const void* val,
                              const void* u, const void* w, const void* r, void* y, double ca, double cb, double cc,
                              double cd, int dot, const double* rdot, const Reduce& R, const int* done,
-                             cudaStream_t st) {
+                             cudaStream_t st, const StepTune& tune) {
     using AT = typename AccOf<XT>::type;
     const int tiles = (n + kBlock - 1) / kBlock;
-    const int grid = (dot == 0 || tiles < kRedGrid) ? tiles : kRedGrid;
+    const int red = num_sms() * (tune.red_ctas_per_sm > 0 ? tune.red_ctas_per_sm : kCtasPerSm);
+    const int grid = (dot == 0 || tiles < red) ? tiles : red;
+    const int ahead = tune.lookahead < 0 ? default_lookahead() : tune.lookahead;
     const StepCoef<AT> c = make_coef<AT>(ca, cb, cc, cd);
     const VT* v = static_cast<const VT*>(val);
     const XT* uu = static_cast<const XT*>(u);
     const XT* ww = static_cast<const XT*>(w);
     const XT* rr = static_cast<const XT*>(r);
     YT* yy = static_cast<YT*>(y);
-#define NC_SELL_KARGS n, sptr, col, pat, v, uu, ww, rr, yy, c, rdot, R, done
+#define NC_SELL_KARGS n, sptr, col, pat, v, uu, ww, rr, yy, c, rdot, R, done, ahead
     switch (dot) {
     case 0: sell_step_kernel<VT, XT, YT, 0, PAT, UNIT><<<grid, kBlock, 0, st>>>(NC_SELL_KARGS); break;
     case 1: sell_step_kernel<VT, XT, YT, 1, PAT, UNIT><<<grid, kBlock, 0, st>>>(NC_SELL_KARGS); break;
@@ -315,25 +319,26 @@ template <typename VT, typename XT, typename YT, bool PAT>
 cudaError_t sell_dispatch_p(int n, const int32_t* sptr, const int32_t* col, const SellPat& pat, const void* val,
                             const void* u, const void* w, const void* r, void* y, double ca, double cb, double cc,
                             double cd, int dot, const double* rdot, const Reduce& R, const int* done,
-                            cudaStream_t st) {
+                            cudaStream_t st, const StepTune& tune) {
     if constexpr (sizeof(typename AccOf<XT>::type) == 8) {
         if (cd == 1.0)
             return sell_dispatch_pu<VT, XT, YT, PAT, true>(n, sptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, dot,
-                                                           rdot, R, done, st);
+                                                           rdot, R, done, st, tune);
     }
     return sell_dispatch_pu<VT, XT, YT, PAT, false>(n, sptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, dot, rdot, R,
-                                                    done, st);
+                                                    done, st, tune);
 }
 
 template <typename VT, typename XT, typename YT>
 cudaError_t sell_dispatch(int n, const int32_t* sptr, const int32_t* col, const SellPat& pat, const void* val,
                           const void* u, const void* w, const void* r, void* y, double ca, double cb, double cc,
-                          double cd, int dot, const double* rdot, const Reduce& R, const int* done, cudaStream_t st) {
+                          double cd, int dot, const double* rdot, const Reduce& R, const int* done, cudaStream_t st,
+                          const StepTune& tune) {
     if (pat.pstart != nullptr)
         return sell_dispatch_p<VT, XT, YT, true>(n, sptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, dot, rdot, R,
-                                                 done, st);
+                                                 done, st, tune);
     return sell_dispatch_p<VT, XT, YT, false>(n, sptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done,
-                                              st);
+                                              st, tune);
 }
 
 }  // namespace
@@ -341,9 +346,15 @@ cudaError_t sell_dispatch(int n, const int32_t* sptr, const int32_t* col, const 
 cudaError_t launch_sell_step(int n, const int32_t* slice_ptr, const int32_t* col, const SellPat& pat,
                              const void* val, int vdt, bool x_f32, bool y_f64, const void* u, const void* w,
                              const void* r, void* y, double ca, double cb, double cc, double cd, int dot,
-                             const double* rdot, const Reduce& R, const int* done, cudaStream_t st) {
+                             const double* rdot, const Reduce& R, const int* done, cudaStream_t st,
+                             const StepTune& tune) {
     if (n <= 0) return cudaSuccess;
-#define NC_SELL_ARGS n, slice_ptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done, st
+    if ((dot == 0 ? tune.variant : tune.dot_variant) == STEP_STAGED) {
+        const cudaError_t e = launch_sell_staged(n, slice_ptr, col, pat, val, vdt, x_f32, y_f64, u, w, r, y, ca, cb,
+                                                 cc, cd, dot, rdot, R, done, st, tune);
+        if (e != cudaErrorNotSupported) return e;
+    }
+#define NC_SELL_ARGS n, slice_ptr, col, pat, val, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done, st, tune
     if (!x_f32) {
         if (vdt != NC_F64) return cudaErrorInvalidValue;
         return sell_dispatch<double, double, double>(NC_SELL_ARGS);

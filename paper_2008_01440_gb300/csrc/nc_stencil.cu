@@ -108,7 +108,7 @@ cudaError_t stencil_dispatch(const StencilGeom& g, const double* c4, const void*
 // waves with chunks of at least 4 planes, so that the GPU is filled.
 int stencil_zchunk(const StencilGeom& g) {
     const long long tiles = (long long)((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY);
-    const long long wave = (long long)kSMs * 8;
+    const long long wave = (long long)vec_grid_max();
     const long long c8 = (8 * wave + tiles - 1) / tiles;
     long long zc = (g.nz + c8 - 1) / c8;
     if (zc < 32) {

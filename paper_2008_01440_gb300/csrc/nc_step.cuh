@@ -30,11 +30,12 @@ __device__ __forceinline__ int ld_stream(const int32_t* p) { return __ldcs(p); }
 // issued by one thread: cp.async.bulk.prefetch is a hint that holds no
 // registers and has nothing to wait for.  Slice offsets are multiples of 32
 // entries, so both ranges start and end on 16-byte boundaries.  The float
-// step kernels take the tile kPrefetchAhead tiles ahead of their own (about
-// two CTAs per SM later): its loads then hit L2, which brought the float
-// step of the 128^3 system from 26.5 to 25.0 us (0.95 of the copy bandwidth).
-// The float64 kernels, latency-bound at full occupancy, ran slower with it.
-constexpr int kPrefetchAhead = 2 * kSMs;
+// step kernels take the tile `ahead` tiles ahead of their own (by default
+// two CTAs per SM later, default_lookahead()): its loads then hit L2, which
+// brought the float step of the 128^3 system from 26.5 to 25.0 us (0.95 of
+// the copy bandwidth).  The float64 kernels, latency-bound at full
+// occupancy, ran slower with it.
+inline int default_lookahead() { return 2 * num_sms(); }
 
 template <typename VT>
 __device__ __forceinline__ void prefetch_sell_tile(int t, int n, const int32_t* __restrict__ slice_ptr,

@@ -125,9 +125,30 @@ __global__ void div_kernel(int n, const double* __restrict__ x, double d, double
 
 }  // namespace
 
+int num_sms() {
+    // one entry per device ordinal; 0 = not read yet (a benign race: every
+    // thread that reads it stores the same value)
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 1;
+    }
+    int v = __atomic_load_n(&cache[dev], __ATOMIC_RELAXED);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (v > kMaxGrid / kCtasPerSm) v = kMaxGrid / kCtasPerSm;
+    __atomic_store_n(&cache[dev], v, __ATOMIC_RELAXED);
+    return v;
+}
+
 int vec_grid(int64_t n) {
     const int64_t want = (n + kBlock - 1) / kBlock;
-    return (int)(want < kVecGrid ? (want > 0 ? want : 1) : kVecGrid);
+    const int cap = vec_grid_max();
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
 cudaError_t launch_axpy2_rr(int n, double* x, double* r, const double* p, const double* q,

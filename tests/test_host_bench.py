@@ -37,3 +37,37 @@ def test_host_info_names_the_cpu_and_its_cores():
     info = bench.host_info()
     assert isinstance(info["host_cpu"], str) and info["host_cpu"]
     assert isinstance(info["host_nproc"], int) and info["host_nproc"] >= 1
+
+
+def test_oracle_errors_of_the_cpu_leg(tmp_path):
+    """The CPU leg's error of a GPU solution against the oracle: 0 for the
+    oracle's own solution, and the relative size of a planted perturbation
+    otherwise (checked on two small stencil systems, in the scaled-back
+    original variables)."""
+    import math
+    import pickle
+    import types
+    import numpy as np
+    import oracle as O
+    import workloads as W
+    samples = []
+    for (nx, ny, nz, w) in ((6, 5, 4, (1.0, 0.3, 0.1)), (9, 7, 3, (0.2, 1.0, 0.5))):
+        st = W.stencil7_aniso(nx, ny, nz, *w)
+        sc = W.Stencil7(nx, ny, nz, 1.0, st.cx / st.c0, st.cy / st.c0, st.cz / st.c0)
+        lo, hi = W.stencil7_bounds(sc)
+        b = W.uniform_vector(st.n, seed=nx)
+        mv = O.stencil7_matvec(nx, ny, nz, 1.0, sc.cx, sc.cy, sc.cz)
+        prm = O.cheb_params(lo, hi, bench.S_THETA)
+        dis = 1.0 / math.sqrt(st.c0)
+        ro = O.pcg(mv, dis * b, lambda r: O.cheb_apply(mv, r, prm, 8), m=8, tol=bench.TOL, maxit=1000)
+        samples.append({"dims": [nx, ny, nz], "c": [st.c0, st.cx, st.cy, st.cz], "lo": lo, "hi": hi, "k": 8,
+                        "b": b, "x": dis * ro.x, "iters": ro.iters})
+    bumped = dict(samples[1])
+    bumped["x"] = samples[1]["x"] * (1.0 + 1e-3)
+    path = tmp_path / "e.pkl"
+    with open(path, "wb") as f:
+        pickle.dump({"c4": samples, "c5": [bumped]}, f)
+    out = bench.oracle_errors(str(path), types.SimpleNamespace(grid=None))
+    assert [d["rel_err"] for d in out["c4"]["samples"]] == [0.0, 0.0]
+    assert out["c4"]["samples"][0]["oracle_iters"] == samples[0]["iters"]
+    assert abs(out["c5"]["max_rel_err"] - 1e-3) < 1e-12
