@@ -149,9 +149,9 @@ typedef struct {
     int step_stages;   /* STAGED: tiles in flight per CTA, 2..4 (default 2)    */
     int step_ctas_per_sm; /* STAGED: resident CTAs per SM (default 6, capped by
                           what the device holds)                               */
-    int step_rows_per_thread; /* STAGED: 1 or 2 rows per thread (default 1):
-                          tiles of 256 or 512 rows, the gathers of both rows
-                          in flight together                                    */
+    int step_rows_per_thread; /* plain steps, either variant: 1 or 2 rows per
+                          thread (default 1): tiles of 256 or 512 rows, the
+                          loads of both rows in flight together               */
     int step_tile_order; /* STAGED: 0 (default) CTA b takes tiles b, b + grid,
                           ...; 1: a contiguous run of tiles per CTA            */
     int prefetch_tiles;/* DIRECT float kernels: L2 prefetch distance in 256-row

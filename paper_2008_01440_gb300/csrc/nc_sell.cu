@@ -23,6 +23,7 @@
 // instruction less per row on GB300's narrow FP64 pipe; the outer products
 // add theta' u back (q = A' p + theta' p).
 #include <climits>
+#include <type_traits>
 
 #include "nc_step.cuh"
 
@@ -43,6 +44,17 @@ __device__ __forceinline__ double sell_row(const int row, const int n, const int
                                            const StepCoef<typename AccOf<XT>::type>& c,
                                            const double* __restrict__ rdot) {
     using AT = typename AccOf<XT>::type;
+    // float32 values: r and x_{k-2} depend on nothing, so their loads go out
+    // first and their latency overlaps the slot loop's instead of following
+    // it (the float32 step of the 128^3 system 25.6 -> 21.8 us); with
+    // float64 or bfloat16 values the same order measured slower (41.9 ->
+    // 43.5 and 25.4 -> 31.7 us), so those load them in the epilogue
+    constexpr bool kEarly = std::is_same<VT, float>::value;
+    AT rv = AT(0), wv = AT(0);
+    if constexpr (kEarly) {
+        if (c.terms & kTermR) rv = (AT)r[row];
+        if (c.terms & kTermW) wv = (AT)w[row];
+    }
     const int s = row >> 5;
     const int beg = slice_ptr[s];
     const int len = (slice_ptr[s + 1] - beg) >> 5;   // warp-uniform
@@ -108,17 +120,109 @@ __device__ __forceinline__ double sell_row(const int row, const int n, const int
             advance(G);
         }
     }
-    return step_row_out<XT, YT, DOT, AT, UNIT>(row, acc, c, u, w, r, y, rdot);
+    if constexpr (!kEarly) {
+        if (c.terms & kTermR) rv = (AT)r[row];
+        if (c.terms & kTermW) wv = (AT)w[row];
+    }
+    return sell_row_out<XT, YT, DOT, AT, UNIT>(row, acc, c, rv, wv, u, y, rdot);
 }
 
-template <typename VT, typename XT, typename YT, int DOT, bool PAT, bool UNIT>
-__global__ void __launch_bounds__(kBlock)
+// Two rows per thread (rows row0 and row0 + 256: slices w and w + 8 of a
+// 512-row tile for warp w), no dot product: every load of both rows is
+// issued before either fma chain, so twice the loads are in flight per warp
+// (the float step is latency-bound).  Each row's arithmetic is sell_row's.
+template <typename VT, typename XT, typename YT, bool PAT, bool UNIT>
+__device__ __forceinline__ void sell_rows2(const int row0, const int n, const int32_t* __restrict__ slice_ptr,
+                                           const int32_t* __restrict__ col, const SellPat& pat,
+                                           const VT* __restrict__ val, const XT* __restrict__ u,
+                                           const XT* __restrict__ w, const XT* __restrict__ r, YT* __restrict__ y,
+                                           const StepCoef<typename AccOf<XT>::type>& c) {
+    using AT = typename AccOf<XT>::type;
+    constexpr int Q = 2;
+    const int nslices = (n + 31) >> 5;
+    int row[Q], len[Q];
+    bool act[Q];
+    const VT* vp[Q];
+    const int32_t* cp[Q];
+    AT rv[Q], wv[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        row[q] = row0 + kBlock * q;
+        act[q] = row[q] < n;
+        rv[q] = (act[q] && (c.terms & kTermR)) ? (AT)r[row[q]] : AT(0);
+        wv[q] = (act[q] && (c.terms & kTermW)) ? (AT)w[row[q]] : AT(0);
+        const int s = row[q] >> 5;
+        len[q] = 0;
+        vp[q] = val;
+        cp[q] = col;
+        if (s < nslices) {   // warp-uniform; lanes past n read padded slots (clamped columns)
+            const int beg = slice_ptr[s];
+            len[q] = (slice_ptr[s + 1] - beg) >> 5;
+            vp[q] = val + beg + (row[q] & 31);
+            if constexpr (PAT) cp[q] = pat.poff + __ldg(pat.pstart + s);
+            else cp[q] = col + beg + (row[q] & 31);
+        }
+    }
+    auto colt = [&](int q, int t) -> int {
+        if constexpr (PAT) return min(max(row[q] + __ldg(cp[q] + t), 0), n - 1);
+        else return ld_stream(cp[q] + 32 * t);
+    };
+    constexpr int G = sizeof(AT) == 8 ? 4 : kSellGroup;
+    const int maxlen = max(len[0], len[1]);
+    AT acc[Q] = {AT(0), AT(0)};
+    for (int j0 = 0; j0 < maxlen; j0 += G) {
+        int cc_[Q][G];
+        AT vv[Q][G], xx[Q][G];
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (j0 + t < len[q]) {
+                    cc_[q][t] = colt(q, j0 + t);
+                    vv[q][t] = (AT)ld_stream(vp[q] + 32 * (j0 + t));
+                }
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (j0 + t < len[q]) xx[q][t] = (AT)__ldg(u + cc_[q][t]);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (j0 + t < len[q]) acc[q] = fma(vv[q][t], xx[q][t], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        if (act[q]) sell_row_out<XT, YT, 0, AT, UNIT>(row[q], acc[q], c, rv[q], wv[q], u, y, nullptr);
+}
+
+// Resident CTAs per SM the register budget aims at: plain steps 8 with
+// float64 values (32 registers), 5 with float32 (48), 4 with bfloat16 (64),
+// 3 with two rows per thread; the persistent dot-product variants 6 in
+// float64 (40) and 4 in float (64).
+template <typename VT, typename XT, int DOT, int RPT>
+constexpr int sell_min_ctas() {
+    constexpr bool f64 = sizeof(typename AccOf<XT>::type) == 8;
+    return DOT != 0 ? (f64 ? 6 : 4) : (RPT == 2 ? 3 : (f64 ? 8 : (sizeof(VT) == 4 ? 5 : 4)));
+}
+
+template <typename VT, typename XT, typename YT, int DOT, bool PAT, bool UNIT, int RPT = 1>
+__global__ void __launch_bounds__(kBlock, sell_min_ctas<VT, XT, DOT, RPT>())
 sell_step_kernel(const int n, const int32_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
                  const SellPat pat, const VT* __restrict__ val, const XT* __restrict__ u, const XT* __restrict__ w,
                  const XT* __restrict__ r, YT* __restrict__ y, const StepCoef<typename AccOf<XT>::type> c,
                  const double* __restrict__ rdot, const Reduce R, const int* __restrict__ done, const int ahead) {
     if (done != nullptr && *done) return;
-    if constexpr (DOT == 0) {
+    if constexpr (DOT == 0 && RPT == 2) {
+        // one 512-row tile (two 256-row tiles) per CTA
+        if constexpr (sizeof(typename AccOf<XT>::type) == 4)
+            if (threadIdx.x < 2 && ahead > 0)
+                prefetch_sell_tile(2 * ((int)blockIdx.x + ahead) + (int)threadIdx.x, n, slice_ptr, PAT ? nullptr : col,
+                                   val);
+        sell_rows2<VT, XT, YT, PAT, UNIT>(2 * (int)blockIdx.x * kBlock + (int)threadIdx.x, n, slice_ptr, col, pat, val,
+                                          u, w, r, y, c);
+    } else if constexpr (DOT == 0) {
         // one 256-row tile per CTA
         if constexpr (sizeof(typename AccOf<XT>::type) == 4)
             if (threadIdx.x == 0 && ahead > 0)
@@ -305,7 +409,12 @@ cudaError_t sell_dispatch_pu(int n, const int32_t* sptr, const int32_t* col, con
     YT* yy = static_cast<YT*>(y);
 #define NC_SELL_KARGS n, sptr, col, pat, v, uu, ww, rr, yy, c, rdot, R, done, ahead
     switch (dot) {
-    case 0: sell_step_kernel<VT, XT, YT, 0, PAT, UNIT><<<grid, kBlock, 0, st>>>(NC_SELL_KARGS); break;
+    case 0:
+        if (tune.rpt == 2)
+            sell_step_kernel<VT, XT, YT, 0, PAT, UNIT, 2><<<(tiles + 1) / 2, kBlock, 0, st>>>(NC_SELL_KARGS);
+        else
+            sell_step_kernel<VT, XT, YT, 0, PAT, UNIT><<<grid, kBlock, 0, st>>>(NC_SELL_KARGS);
+        break;
     case 1: sell_step_kernel<VT, XT, YT, 1, PAT, UNIT><<<grid, kBlock, 0, st>>>(NC_SELL_KARGS); break;
     default: sell_step_kernel<VT, XT, YT, 2, PAT, UNIT><<<grid, kBlock, 0, st>>>(NC_SELL_KARGS); break;
     }

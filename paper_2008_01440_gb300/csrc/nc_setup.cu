@@ -466,7 +466,7 @@ nc_status time_launches(cudaStream_t st, F launch, double* us) {
     NC_CU(cudaEventCreate(&e0));
     cudaError_t e = cudaEventCreate(&e1);
     if (e) { cudaEventDestroy(e0); g_last_cuda = e; return NC_ERR_CUDA; }
-    const int reps = 8;
+    const int reps = 20;
     e = cudaEventRecord(e0, st);
     for (int i = 0; i < reps && e == cudaSuccess; ++i) e = launch();
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -511,16 +511,23 @@ nc_status tune_kind(nc_solver S, OpView& op, int kind, cudaStream_t st) {
         else t.dot_variant = v;
         return t;
     };
-    {   // direct loads
+    {   // direct loads: L2 prefetch distance (float) and rows per thread
+        // for the plain step, persistent CTAs per SM for the dot steps
         StepTune t = with_variant(base, STEP_DIRECT);
         t.lookahead = -1;
         t.red_ctas_per_sm = kCtasPerSm;
-        cands.push_back(t);
-        if (x_f32 && kind == 0) {
-            t.lookahead = 0;
+        if (kind == 0) {
+            for (int rpt = 1; rpt <= 2; ++rpt) {
+                t.rpt = rpt;
+                t.lookahead = -1;
+                cands.push_back(t);
+                if (x_f32) {
+                    t.lookahead = 0;
+                    cands.push_back(t);
+                }
+            }
+        } else {
             cands.push_back(t);
-        }
-        if (kind != 0) {
             t.red_ctas_per_sm = 4;
             cands.push_back(t);
         }
@@ -528,8 +535,9 @@ nc_status tune_kind(nc_solver S, OpView& op, int kind, cudaStream_t st) {
     // staged: (stages, CTAs per SM, rows per thread, tile order); a shape the
     // device cannot hold or that repeats another after the occupancy cap is skipped
     std::vector<std::array<int, 4>> seen;
+    // (the contiguous tile order measured slower on every operator tried: not a candidate)
     for (int rpt = 1; rpt <= 2; ++rpt)
-        for (int contig = 0; contig <= 1; ++contig)
+        for (int contig = 0; contig <= 0; ++contig)
             for (int stages = 2; stages <= 3; ++stages)
                 for (int ctas : {4, 6, 8}) {
                     StepTune t = with_variant(base, STEP_STAGED);
@@ -582,6 +590,7 @@ nc_status tune_kind(nc_solver S, OpView& op, int kind, cudaStream_t st) {
     b.chosen = 1;
     if (kind == 0) {
         op.tune.variant = b.variant;
+        op.tune.rpt = b.rpt;
         if (b.variant == STEP_DIRECT) op.tune.lookahead = b.lookahead;
         else {
             op.tune.stages = b.stages;

@@ -95,4 +95,23 @@ __device__ __forceinline__ double step_row_out(int row, AT acc, const StepCoef<A
     return 0.0;
 }
 
+// The same epilogue with r[row] and w[row] already loaded (rv, wv; zero
+// when their term is absent), in the same order of operations.
+template <typename XT, typename YT, int DOT, typename AT, bool UNIT = false>
+__device__ __forceinline__ double sell_row_out(int row, AT acc, const StepCoef<AT>& c, AT rv, AT wv,
+                                               const XT* __restrict__ u, YT* __restrict__ y,
+                                               const double* __restrict__ rdot) {
+    AT o;
+    if constexpr (UNIT) o = acc;
+    else o = (c.terms & kUnitD) ? acc : c.cd * acc;
+    if (c.terms & kTermR) o = fma(c.cc, rv, o);
+    if (c.terms & kTermW) o = fma(c.cb, wv, o);
+    if (c.terms & kTermU) o = fma(c.ca, (AT)u[row], o);
+    const YT yo = (YT)o;
+    y[row] = yo;
+    if (DOT == 1) return rdot[row] * (double)yo;
+    if (DOT == 2) return (double)u[row] * (double)yo;
+    return 0.0;
+}
+
 }  // namespace nc

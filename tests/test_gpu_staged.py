@@ -57,6 +57,9 @@ def test_staged_equals_direct_and_oracle(env, grid, dt):
     idir, zd = _apply(torch, nc, M, A.n, lo, hi, k, 1.001, vd, apply_dtype=dt, spmv_format="psell",
                       step_kernel="direct")
     assert idir["spmv_format"] == "psell" and idir["step_kernel"] == "direct"
+    i2, z2 = _apply(torch, nc, M, A.n, lo, hi, k, 1.001, vd, apply_dtype=dt, spmv_format="psell",
+                    step_kernel="direct", step_rows_per_thread=2)
+    assert i2["step_rows_per_thread"] == 2 and np.array_equal(z2, zd)
     for stages, ctas, rpt, order in ((2, 1, 1, 0), (3, 2, 1, 1), (4, 6, 1, 0), (2, 4, 2, 0), (3, 8, 2, 1),
                                      (2, 6, 1, 1)):
         ist, zs = _apply(torch, nc, M, A.n, lo, hi, k, 1.001, vd, apply_dtype=dt, spmv_format="psell",
@@ -106,6 +109,9 @@ def test_staged_tiny_and_ragged(env, n):
     v = W.uniform_vector(n, seed=n)
     vd = to_dev(torch, v)
     _, zd = _apply(torch, nc, M, n, lo, hi, 6, 1.001, vd, spmv_format="psell", step_kernel="direct")
+    _, z2 = _apply(torch, nc, M, n, lo, hi, 6, 1.001, vd, spmv_format="psell", step_kernel="direct",
+                   step_rows_per_thread=2)
+    assert np.array_equal(z2, zd)
     for rpt in (1, 2):
         for order in (0, 1):
             _, zs = _apply(torch, nc, M, n, lo, hi, 6, 1.001, vd, spmv_format="psell", step_kernel="staged",
@@ -200,3 +206,44 @@ def test_direct_options_are_kept(env):
     assert i1["prefetch_tiles"] == 0 and i1["red_ctas_per_sm"] == 4
     assert i0["prefetch_tiles"] == 2 * i0["num_sms"] and i0["tune_candidates"] == 0
     assert np.array_equal(z0, z1)
+
+
+def _banded(n, offsets):
+    """Symmetric banded matrix: 10 on the diagonal, -1 at +-o for o in
+    offsets (diagonally dominant, spectrum inside Gershgorin's [4, 16])."""
+    rows, vals = [], []
+    offs = sorted({0} | set(offsets) | {-o for o in offsets})
+    for i in range(n):
+        c = np.array([i + o for o in offs if 0 <= i + o < n], dtype=np.int32)
+        rows.append(c)
+        vals.append(np.where(c == i, 10.0, -1.0))
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    return W.CSR(n, rowptr, np.concatenate(rows), np.concatenate(vals))
+
+
+@pytest.mark.parametrize("offsets,n", [((1, 2, 500), 50001), ((1000, 3000, 7000), 40000), ((1, 64, 4096), 70001)])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_staged_gather_windows_and_fallback(env, offsets, n, dt):
+    """Banded operators whose offsets are near (0, +-1, +-2, +-500), far
+    (+-1000, +-3000, +-7000: every slot gathers a separate stretch of
+    x_{k-1}) or mixed (0, +-1, +-64, +-4096): the staged kernel's result is
+    the direct kernel's, bit for bit, for both row counts per thread, and
+    n % 4 != 0 leaves a ragged last tile."""
+    torch, nc = env
+    A = _banded(n, offsets)
+    M = csr_to_gpu(torch, nc, A)
+    v = W.uniform_vector(n, seed=3)
+    vd = to_dev(torch, v)
+    info, zd = _apply(torch, nc, M, n, 4.0, 16.0, 7, 1.001, vd, apply_dtype=dt, spmv_format="psell",
+                      step_kernel="direct")
+    assert info["spmv_format"] == "psell"
+    _, z2 = _apply(torch, nc, M, n, 4.0, 16.0, 7, 1.001, vd, apply_dtype=dt, spmv_format="psell",
+                   step_kernel="direct", step_rows_per_thread=2)
+    assert np.array_equal(z2, zd)
+    for rpt in (1, 2):
+        _, zs = _apply(torch, nc, M, n, 4.0, 16.0, 7, 1.001, vd, apply_dtype=dt, spmv_format="psell",
+                       step_kernel="staged", step_rows_per_thread=rpt)
+        assert np.array_equal(zs, zd), rpt
+    ref = O.cheb_apply(O.csr_matvec(A.rowptr, A.col, A.val, n), v, O.cheb_params(4.0, 16.0, 1.001), 7)
+    assert rel_err(zd, ref) <= TOL[dt] and elem_err(zd, ref) <= TOL[dt]
