@@ -157,7 +157,8 @@ typedef struct {
     int prefetch_tiles;/* DIRECT float kernels: L2 prefetch distance in 256-row
                           tiles (default 2 x the SM count; < 0: off)           */
     int red_ctas_per_sm; /* DIRECT steps with a dot product: persistent CTAs
-                          per SM (default 8)                                    */
+                          per SM, 1..64 (default 8; 64 = one 256-row tile per
+                          CTA on any device)                                   */
 } nc_options;
 
 typedef struct {

@@ -64,7 +64,7 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
     if (o.spmv_format < NC_FORMAT_AUTO || o.spmv_format > NC_FORMAT_PSELL) return NC_ERR_ARG;
     if (o.step_kernel < NC_STEP_AUTO || o.step_kernel > NC_STEP_TUNE || o.step_stages < 0 || o.step_stages > 4 ||
         o.step_stages == 1 || o.step_ctas_per_sm < 0 || o.step_ctas_per_sm > 8 || o.red_ctas_per_sm < 0 ||
-        o.red_ctas_per_sm > 32 || o.step_rows_per_thread < 0 || o.step_rows_per_thread > 2 ||
+        o.red_ctas_per_sm > 64 || o.step_rows_per_thread < 0 || o.step_rows_per_thread > 2 ||
         o.step_tile_order < 0 || o.step_tile_order > 1)
         return NC_ERR_ARG;
     int nlev = -1;

@@ -29,6 +29,8 @@ inline int vec_grid_max() { return num_sms() * kCtasPerSm; }
 // sized with it so that a solver never depends on the device it was set up on)
 constexpr int kMaxGrid = 1024 * kCtasPerSm;
 
+constexpr int kRedOneTile = 64;   // CTAs per SM large enough for one tile per CTA
+
 // Launch choices of the SELL-32 step kernels (sliced and offset-pattern
 // layouts), fixed per solver at setup -- by default, or by the tuner, which
 // times candidates on the solver's own operator.
@@ -52,7 +54,8 @@ struct StepTune {
     int lookahead = -1;     // direct float kernels: L2 prefetch distance in tiles
                             // (-1: two waves, 2 x num_sms(); 0: off)
     int red_ctas_per_sm = kCtasPerSm;   // direct kernels with a dot product:
-                                        // persistent CTAs per SM
+                                        // persistent CTAs per SM (kRedOneTile:
+                                        // one 256-row tile per CTA)
     int vcap = 0;           // staged: matrix entries of the largest 256-row tile
     int vcap2 = 0;          // and of the largest 512-row tile (rpt = 2)
     int npoff = 0;          // staged: entries of the offset-pattern table

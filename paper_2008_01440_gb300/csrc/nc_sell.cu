@@ -120,11 +120,8 @@ __device__ __forceinline__ double sell_row(const int row, const int n, const int
             advance(G);
         }
     }
-    if constexpr (!kEarly) {
-        if (c.terms & kTermR) rv = (AT)r[row];
-        if (c.terms & kTermW) wv = (AT)w[row];
-    }
-    return sell_row_out<XT, YT, DOT, AT, UNIT>(row, acc, c, rv, wv, u, y, rdot);
+    if constexpr (kEarly) return sell_row_out<XT, YT, DOT, AT, UNIT>(row, acc, c, rv, wv, u, y, rdot);
+    else return step_row_out<XT, YT, DOT, AT, UNIT>(row, acc, c, u, w, r, y, rdot);
 }
 
 // Two rows per thread (rows row0 and row0 + 256: slices w and w + 8 of a
@@ -199,8 +196,8 @@ __device__ __forceinline__ void sell_rows2(const int row0, const int n, const in
 
 // Resident CTAs per SM the register budget aims at: plain steps 8 with
 // float64 values (32 registers), 5 with float32 (48), 4 with bfloat16 (64),
-// 3 with two rows per thread; the persistent dot-product variants 6 in
-// float64 (40) and 4 in float (64).
+// 3 with two rows per thread; dot-product variants 6 in float64 (40) and 4
+// in float (64).
 template <typename VT, typename XT, int DOT, int RPT>
 constexpr int sell_min_ctas() {
     constexpr bool f64 = sizeof(typename AccOf<XT>::type) == 8;

@@ -527,9 +527,13 @@ nc_status tune_kind(nc_solver S, OpView& op, int kind, cudaStream_t st) {
                 }
             }
         } else {
-            cands.push_back(t);
-            t.red_ctas_per_sm = 4;
-            cands.push_back(t);
+            // persistent grids of 4 to 8 CTAs per SM (the float64 dot
+            // kernels hold 6 per SM: 8 leaves a second, partial wave), or
+            // one 256-row tile per CTA (a grid as large as the tile count)
+            for (int red : {4, 5, 6, 8, kRedOneTile}) {
+                t.red_ctas_per_sm = red;
+                cands.push_back(t);
+            }
         }
     }
     // staged: (stages, CTAs per SM, rows per thread, tile order); a shape the
