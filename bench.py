@@ -68,6 +68,10 @@ def parse():
                     help="c2: skip the compact batched (c4) and serving (c5) passes")
     ap.add_argument("--ns-requests", type=int, default=60, help="c2: requests of the compact serving pass")
     ap.add_argument("--err-inputs", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "direct", "staged", "tune"],
+                    help="variant of the fused step kernels (auto: tuned on large offset-pattern operators)")
+    ap.add_argument("--step-rpt", type=int, default=0, help="rows per thread of the plain steps (0: default)")
+    ap.add_argument("--red-ctas", type=int, default=0, help="CTAs per SM of the direct dot-product steps (0: default)")
     ap.add_argument("--cores", type=int, default=None, help="reference: oracle processes (default: all cores)")
     ap.add_argument("--oracle-iters", type=int, default=6, help="PCG iterations per oracle sample")
     ap.add_argument("--gpu-iters", type=int, default=None, help=argparse.SUPPRESS)
@@ -312,7 +316,8 @@ def run_system(args, spec, rank, world, local_rank):
     for mode in modes:
         rr = spec["rr_mixed"] if mode != "f64" else 0
         S = nc.pcg_setup(M, lo, hi, k, spec["s"], apply_dtype=mode, x0_is_zero=True, rr_period=rr,
-                         use_graph=not args.host_loop, persistent=persistent)
+                         use_graph=not args.host_loop, persistent=persistent, step_kernel=args.step_kernel,
+                         step_rows_per_thread=args.step_rpt, red_ctas_per_sm=args.red_ctas)
         barrier()
         clk = start_clocks(torch, dev) if mode == args.apply else None
         torch.cuda.synchronize()
@@ -337,7 +342,10 @@ def run_system(args, spec, rank, world, local_rank):
         info = nc.pcg_get_info(S)
         rec["step_kernel"] = {"plain": info["step_kernel"], "dot": info["dot_step_kernel"],
                               "stages": info["step_stages"], "ctas_per_sm": info["step_ctas_per_sm"],
-                              "tune_candidates": info["tune_candidates"]}
+                              "rows_per_thread": info["step_rows_per_thread"],
+                              "dot_red_ctas_per_sm": info["red_ctas_per_sm"],
+                              "tune_candidates": info["tune_candidates"],
+                              "tune_from_cache": bool(info["tune_from_cache"])}
         if want_err:
             # the solution of the first right-hand side, for the error against the oracle (CPU leg)
             nc.pcg_solve(S, bs[0], x, TOL, MAXIT)
@@ -402,9 +410,9 @@ def run_system(args, spec, rank, world, local_rank):
 
     # the configuration's other degrees (same system, FP64 unless --apply)
     degrees = None
-    if not args.no_modes and args.workload == "c2" and world == 1:
+    if not args.no_modes and args.workload in ("c2", "c3") and world == 1:
         degrees = {}
-        for kk in (10, 20, 40):
+        for kk in ((10, 20, 40) if args.workload == "c2" else (20, 60)):
             Sk = nc.pcg_setup(M, lo, hi, kk, spec["s"], apply_dtype=args.apply, x0_is_zero=True)
             nc.pcg_solve(Sk, bs[0], x, TOL, MAXIT)
             torch.cuda.synchronize()
@@ -1011,11 +1019,13 @@ def measure_c4(args, dev, world, plain_budget_s=90.0, steps=None, warmup=None, n
 
 def run_c4_csr(args, rank, world, local_rank):
     """The batched workload with explicit matrices: each of the systems of
-    c4_systems assembled as CSR (the same constant 7-point operators) and
-    solved with all its right-hand sides in one pcg_solve_multi block (the
-    matrix read once per step for the whole block), float32 apply, float64
-    outer CG, systems one after another.  Setup (SELL layout, graph) is timed
-    apart from the solves."""
+    c4_systems assembled as CSR (the same constant 7-point operators),
+    Jacobi scaled, with its own solver (float32 apply, float64 outer CG,
+    offset-pattern layout).  Headline: every (system, right-hand side) pair a
+    slot of one batch engine (pcg_batch_add_solver), all of them advancing
+    together in one graph launch per batch.  Compared with the same systems
+    one after another, each with all its right-hand sides in one
+    pcg_solve_multi block.  Setup (layouts, tuning, graphs) is timed apart."""
     import numpy as np
     import torch
     torch.cuda.set_device(local_rank)
@@ -1024,15 +1034,12 @@ def run_c4_csr(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     sy = c4_systems(args.c4_systems)
-    t_solve = t_setup = 0.0
-    rhs_total = 0
-    iters, ok = [], True
-    clk = start_clocks(torch, dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    keep, solvers, Bs = [], [], []
     for s_ in sy:
         st = s_["st"]
         A = W.stencil7_to_csr(st)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
         M0 = nc.nc_matrix_csr(torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.col).to(dev),
                               torch.from_numpy(A.val).to(dev))
         M = nc.nc_matrix_jacobi(M0)
@@ -1041,33 +1048,70 @@ def run_c4_csr(args, rank, world, local_rank):
         g.manual_seed(s_["seed"])
         B = torch.stack([torch.rand(st.n, generator=g, dtype=torch.float64, device=dev) * 2.0 - 1.0
                          for _ in range(s_["nrhs"])])
-        X = torch.zeros_like(B)
-        nc.pcg_solve_multi(S, B, X, TOL, MAXIT)      # builds the block graph
+        keep.append((M0, M))
+        solvers.append(S)
+        Bs.append(B)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    pairs = [(i, c) for i, B in enumerate(Bs) for c in range(B.shape[0])]
+    units = sum(Bs[i].shape[1] for i, _ in pairs)
+    eng = nc.pcg_batch_create(len(pairs), units, 32)
+    X = [torch.empty_like(B) for B in Bs]
+
+    def one_batch():
+        slots = [nc.pcg_batch_add_solver(eng, solvers[i], Bs[i][c]) for i, c in pairs]
+        nc.pcg_batch_run(eng, TOL, MAXIT, 0)
+        res = []
+        for sl, (i, c) in zip(slots, pairs):
+            res.append(nc.pcg_batch_status(eng, sl)[1])
+            nc.pcg_batch_collect(eng, sl, X[i][c])
+        for sl in slots:
+            nc.pcg_batch_release(eng, sl)
+        return res
+
+    for _ in range(max(args.warmup, 1)):
+        one_batch()
+    torch.cuda.synchronize()
+    clk = start_clocks(torch, dev)
+    times = []
+    _, l0 = nc.pcg_batch_stats(eng)
+    for _ in range(args.steps):
+        a = time.perf_counter()
+        res = one_batch()
         torch.cuda.synchronize()
-        t_setup += time.perf_counter() - t0
+        times.append(time.perf_counter() - a)
+    clocks = clk.stop()
+    _, l1 = nc.pcg_batch_stats(eng)
+    t_batch = replica_max(statistics.median(times), world)
+    iters = [r["iters"] for r in res]
+    ok = all(r["status"] == 0 and r["true_relres"] <= 2 * TOL for r in res)
+    eng.close()
+    # the same systems one after another, each a multi-RHS block
+    t_seq, n_seq = 0.0, 0
+    for S, B in zip(solvers, Bs):
+        Xs = torch.zeros_like(B)
+        nc.pcg_solve_multi(S, B, Xs, TOL, MAXIT)   # builds the block graph
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res = nc.pcg_solve_multi(S, B, X, TOL, MAXIT)
+        rm = nc.pcg_solve_multi(S, B, Xs, TOL, MAXIT)
         e1.record(stream)
         torch.cuda.synchronize()
-        t_solve += e0.elapsed_time(e1) / 1e3
-        rhs_total += len(res)
-        iters += [r["iters"] for r in res]
-        ok = ok and all(r["status"] == 0 and r["true_relres"] <= 2 * TOL for r in res)
-        S.close()
-        del M, M0, B, X
-    clocks = clk.stop()
-    t_solve = replica_max(t_solve, world)
-    line = {"metric": METRIC, "value": round(world * rhs_total / t_solve, 3), "unit": "solves/s", "n_gpus": world,
-            "steps": 1, "warmup": 1, "ms_per_step": round(t_solve * 1e3, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32-apply+f64-outer",
+        t_seq += e0.elapsed_time(e1) / 1e3
+        n_seq += len(rm)
+    line = {"metric": METRIC, "value": round(world * len(pairs) / t_batch, 3), "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": round(t_batch * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-apply+f64-outer",
             "data": "synthetic (seeded generators; RHS from torch's CUDA generator, seeded)",
             "config": {"workload": f"batched, explicit-matrix variant: {len(sy)} anisotropic 7-point Laplacians "
-                                   "as CSR, each with its 1-8 RHS in one multi-RHS block (SpMM steps), "
-                                   "systems in sequence", "solves": rhs_total, "tol": TOL,
-                       "theta_scale": S_THETA, "parallelism": f"replicas x{world}"},
+                                   "as CSR (offset-pattern layout), every (system, RHS) pair a slot of one "
+                                   "engine, one graph launch per batch", "solves_per_step": len(pairs),
+                       "unknowns": units, "tol": TOL, "theta_scale": S_THETA,
+                       "parallelism": f"replicas x{world}"},
             "iters_range": [min(iters), max(iters)], "all_converged": ok, "clocks": clocks,
-            "setup_s_total": round(t_setup, 3)}
+            "gpu_launches": l1 - l0, "setup_s_total": round(t_setup, 3),
+            "one_after_another_multi_rhs": {"solves_per_s": round(n_seq / t_seq, 3),
+                                            "ms_all_systems": round(t_seq * 1e3, 2)},
+            "speedup_vs_one_after_another": round((len(pairs) / t_batch) / (n_seq / t_seq), 2)}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -113,7 +113,10 @@ typedef enum { NC_POLY_CHEBYSHEV = 0, NC_POLY_NEWTON = 1 } nc_poly_form;
  * on the solver's own operator and keeps the fastest for the plain steps and
  * for the steps with a dot product; pcg_tune_candidate lists what was
  * measured.  AUTO (default): TUNE for PSELL operators of at least 2^16 rows,
- * DIRECT otherwise.  Layouts other than PSELL, and the stencil and block
+ * DIRECT otherwise.  When the environment variable NC_TUNE_CACHE names a
+ * file, the choices are looked up there by the operator's signature (rows,
+ * stored entries, offset sets, apply precision, SM count, compute
+ * capability) and measured and appended only when absent.  Layouts other than PSELL, and the stencil and block
  * kernels, always run their single variant. */
 typedef enum {
     NC_STEP_AUTO = 0,
@@ -186,7 +189,8 @@ typedef struct {
     int32_t num_sms;      /* SM count of the device the solver was set up on */
     int32_t faults;       /* 1: a staged kernel's bounded wait ran out (the
                              results of that call are not valid)              */
-    int32_t reserved0;
+    int32_t tune_from_cache; /* 1: the tuner's choices came from the file named
+                             by NC_TUNE_CACHE (nothing measured)              */
 } nc_solver_info;
 
 /* One configuration measured by the tuner (pcg_setup with step_kernel =
@@ -383,7 +387,8 @@ NC_API nc_status pcg_destroy(nc_solver S);
 
 /* ---- Batched and continuous-batching engine --------------------------------
  * Many independent systems (matrix-free constant 7-point stencils of any
- * size, each with its own bounds, degree k and theta scale; one slot per
+ * size, each with its own bounds, degree k and theta scale, and explicit
+ * matrices through their solvers, pcg_batch_add_solver; one slot per
  * right-hand side) solved together: every PCG iteration of every slot is one
  * pass of a fixed sequence of persistent kernels over device-side work lists
  * (stencil tiles and vector chunks of all slots), captured once as a CUDA
@@ -425,6 +430,31 @@ NC_API nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax,
 NC_API nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx, double cy, double cz,
                                double lambda_min, double lambda_max, int degree_k, double theta_scale,
                                const double* b_dev, void* stream, int* slot);
+/* Admit one system given by a solver on an explicit matrix (pcg_setup of a
+ * CSR handle, optionally Jacobi scaled, whose layout is SELL-32 or the
+ * offset-pattern form; the Chebyshev form; no residual replacement) and one
+ * right-hand side b_dev (n float64 on the device, the original system's).
+ * The slot runs that solver's polynomial -- its degree (1..kmax), bounds,
+ * theta scale, stored operator and step coefficients -- inside the engine's
+ * persistent work lists: its 256-row tiles join the other slots' tiles in
+ * every step kernel, its vectors come from the pools, x0 = 0.  The solver's
+ * apply precision must be the engine's (float32 or bfloat16 values with a
+ * float32 engine, float64 with NC_BATCH_F64_APPLY): NC_ERR_UNSUPPORTED
+ * otherwise.  The solver (and its matrix) must stay alive until the slot is
+ * released.  Not in the paper: many explicit systems in one launch. */
+NC_API nc_status pcg_batch_add_solver(nc_batch B, nc_solver S, const double* b_dev, void* stream, int* slot);
+
+/* Solve nsys systems at once, system i (solver S[i], as in
+ * pcg_batch_add_solver) with nrhs[i] right-hand sides B_dev[i] (n_i x nrhs[i]
+ * float64 on the device, column-major) into X_dev[i] (same shape; x0 = 0):
+ * every (system, right-hand side) pair is a slot of one engine and all of
+ * them advance together in one graph launch.  res: host array of
+ * sum(nrhs) results, system by system.  All solvers share one apply
+ * precision (NC_ERR_UNSUPPORTED otherwise).  Returns NC_OK when every slot
+ * converged, else the first non-OK status.  Allocates the engine's pools for
+ * the call and frees them before returning; synchronises `stream`. */
+NC_API nc_status pcg_solve_batched(int nsys, const nc_solver* S, const int* nrhs, const double* const* B_dev,
+                                   double* const* X_dev, double tol, int maxit, void* stream, nc_result* res);
 NC_API nc_status pcg_batch_run(nc_batch B, double tol, int maxit, int iter_limit, void* stream, int* active_left);
 NC_API nc_status pcg_batch_status(nc_batch B, int slot, int* done, nc_result* res);
 NC_API nc_status pcg_batch_collect(nc_batch B, int slot, double* x_dev, void* stream);

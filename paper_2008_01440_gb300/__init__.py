@@ -59,6 +59,7 @@ from .binding import (  # noqa: F401
     NC_ERR_ADMISSION,
     pcg_apply_poly,
     pcg_batch_add,
+    pcg_batch_add_solver,
     pcg_batch_collect,
     pcg_batch_create,
     pcg_batch_destroy,
@@ -72,6 +73,7 @@ from .binding import (  # noqa: F401
     pcg_setup,
     pcg_solve,
     pcg_solve_host,
+    pcg_solve_batched,
     pcg_solve_multi,
     pcg_tune_candidates,
 )

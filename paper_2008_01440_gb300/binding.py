@@ -60,7 +60,7 @@ class nc_solver_info(ctypes.Structure):
                 ("dot_step_rows_per_thread", ctypes.c_int32), ("dot_step_tile_order", ctypes.c_int32),
                 ("prefetch_tiles", ctypes.c_int32), ("red_ctas_per_sm", ctypes.c_int32),
                 ("tune_candidates", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("faults", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32)]
+                ("tune_from_cache", ctypes.c_int32)]
 
 
 class nc_tune_candidate(ctypes.Structure):
@@ -117,6 +117,10 @@ _SIGS = {
     "pcg_batch_create": (ctypes.c_int, [ctypes.c_int, _i64, ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
     "pcg_batch_add": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dbl, _dbl, _dbl, _dbl, _dbl,
                                      _dbl, ctypes.c_int, _dbl, _vp, _vp, ctypes.POINTER(ctypes.c_int)]),
+    "pcg_batch_add_solver": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int)]),
+    "pcg_solve_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(_vp), ctypes.POINTER(_vp), _dbl, ctypes.c_int, _vp,
+                                         ctypes.POINTER(nc_result)]),
     "pcg_batch_run": (ctypes.c_int, [_vp, _dbl, ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int)]),
     "pcg_batch_status": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(nc_result)]),
     "pcg_batch_collect": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
@@ -486,6 +490,47 @@ def pcg_batch_add(B: Batch, nx: int, ny: int, nz: int, c0: float, cx: float, cy:
         return None
     _check(st, "pcg_batch_add")
     return slot.value
+
+
+def pcg_batch_add_solver(B: Batch, S: Solver, b, stream=None):
+    """Admit one right-hand side of an explicit-matrix solver (pcg_setup of a
+    CSR handle in a sliced layout) as a slot; returns the slot id, or None when
+    the engine is full (NC_ERR_ADMISSION)."""
+    import torch
+    slot = ctypes.c_int(-1)
+    st = lib.pcg_batch_add_solver(B.handle, S.handle, _ptr(b, torch.float64, S.n, "b"), _stream(stream),
+                                  ctypes.byref(slot))
+    if st == NC_ERR_ADMISSION:
+        return None
+    _check(st, "pcg_batch_add_solver")
+    return slot.value
+
+
+def pcg_solve_batched(solvers, Bs, Xs, tol: float, maxit: int, stream=None) -> list:
+    """Solve every system i (solvers[i]) for the right-hand sides Bs[i] (CUDA
+    float64, shape (m_i, n_i) or (n_i,)) into Xs[i] (same shape) in one engine
+    launch; returns one result dict per (system, right-hand side)."""
+    import torch
+    ns = len(solvers)
+    if not (len(Bs) == len(Xs) == ns) or ns < 1:
+        raise ValueError("solvers, Bs, Xs: equal, non-zero lengths")
+    hs = (_vp * ns)(*[S.handle for S in solvers])
+    nrhs = (ctypes.c_int * ns)()
+    bp = (_vp * ns)()
+    xp = (_vp * ns)()
+    for i, (S, b, x) in enumerate(zip(solvers, Bs, Xs)):
+        if b.shape != x.shape or b.shape[-1] != S.n or b.dim() not in (1, 2):
+            raise ValueError(f"Bs[{i}], Xs[{i}]: expected equal shapes (m, {S.n}) or ({S.n},)")
+        m = 1 if b.dim() == 1 else int(b.shape[0])
+        nrhs[i] = m
+        bp[i] = _ptr(b, torch.float64, m * S.n, f"Bs[{i}]")
+        xp[i] = _ptr(x, torch.float64, m * S.n, f"Xs[{i}]")
+    total = sum(nrhs)
+    res = (nc_result * total)()
+    st = lib.pcg_solve_batched(ns, hs, nrhs, bp, xp, float(tol), int(maxit), _stream(stream), res)
+    if st not in SOLVE_STATUSES:
+        _check(st, "pcg_solve_batched")
+    return [r.as_dict() for r in res]
 
 
 def pcg_batch_run(B: Batch, tol: float, maxit: int, iter_limit: int = 0, stream=None) -> int:

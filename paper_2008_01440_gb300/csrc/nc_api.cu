@@ -304,7 +304,7 @@ nc_status pcg_get_info(nc_solver S, nc_solver_info* info) {
     info->tune_candidates = (int32_t)S->tune.size();
     info->num_sms = S->num_sms;
     info->faults = 0;
-    info->reserved0 = 0;
+    info->tune_from_cache = S->tune_cached ? 1 : 0;
     if (S->S) {
         int f = 0;
         if (cudaMemcpy(&f, &S->S->fault, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {

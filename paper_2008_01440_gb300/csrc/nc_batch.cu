@@ -34,8 +34,11 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <type_traits>
 #include <vector>
 
+#include "nc_internal.h"
+#include "nc_sell.cuh"
 #include "nc_stencil.cuh"
 
 namespace nc {
@@ -43,10 +46,16 @@ namespace {
 
 constexpr int kVch = 8192;    // vector-chunk length
 constexpr int kZC = 32;       // planes per stencil tile (32 measured 4.5% faster than 16 or 64 on the 256-system batch)
+// rows per tile of an explicit-matrix slot: as many as a stencil tile's
+// points, so the per-tile reduction (fence + atomic) stays as rare; a CTA
+// walks them in blocks of 256 rows, one row per thread
+constexpr int kSellTileRows = kFT * kZC;
 
 enum Phase : int { PH_FREE = 0, PH_INIT = 1, PH_RUN = 2, PH_FINISH = 3, PH_DONE = 4 };
 
 enum BFin : int { BF_ALPHA = 1, BF_RR = 2, BF_INIT = 3, BF_RZ = 4, BF_START = 5, BF_TRUE = 6 };
+
+enum SlotKind : int { SLOT_STENCIL = 0, SLOT_SELL = 1 };
 
 struct BDesc {
     int nx, ny, nz, n;
@@ -56,6 +65,16 @@ struct BDesc {
     double *b, *x, *r, *z, *p, *q;
     float *t0, *t1, *t2, *r32;      // float32 apply (NC_BATCH_F64_APPLY unset)
     double *dt0, *dt1, *dt2;        // float64 apply: the Chebyshev vectors, r read directly
+    // SLOT_SELL: an explicit matrix in a solver's SELL-32 layout (borrowed):
+    // slice offsets, columns (plain) or offset patterns, the float64 values of
+    // A - shift I and the values inside P (apply precision vdtP)
+    int kind, vdtP;
+    double shift;
+    const int32_t *sptr, *scol;
+    SellPat pat;
+    const double* val64;
+    const void* valP;
+    const double* disv;             // d^{-1/2} per unknown (null: the slot's scalar)
 };
 
 struct BState {
@@ -69,6 +88,8 @@ struct BCoef {
     int terms;
     int xu;                                // float64 fields: exd == -1 exactly (no centre multiply)
     double e0d, exd, eyd, ezd, cbd, ccd;   // float64 apply: the step for the scaled iterates
+    // SLOT_SELL: y = ca u + cb w + cc r + cd A' u (nc_step.cuh's StepCoef),
+    // float for the float32 apply, double for the float64 one; xu: cd == 1
 };
 
 struct BTile {
@@ -82,7 +103,7 @@ struct BVch {
 struct BCtl {
     double tol2;
     int maxit, ntiles, nvch, active;
-    int iters_this_call, iter_limit, pad0, pad1;
+    int iters_this_call, iter_limit, nstiles, pad1;   // nstiles: tiles of explicit-matrix slots
 };
 
 __device__ void bfinalize(BState* st, BCtl* ctl, int kind, double s) {
@@ -339,6 +360,162 @@ __global__ void __launch_bounds__(256) bk_true(const BDesc* __restrict__ D, BSta
     }
 }
 
+// ---- explicit-matrix slots: their own kernels over their own tile list
+// (kSellTileRows rows per tile, walked by the CTA in 256-row blocks), so
+// that the stencil kernels keep their register budgets; launched only while
+// the engine holds such slots
+
+// Chebyshev step j of the explicit slots whose values inside P are VT
+// (double: the float64 apply; float or bfloat16: the float32 apply)
+template <typename VT, typename XT, typename YT, int DOT, bool UNIT>
+__device__ __forceinline__ double sell_block(int row, int n, const int32_t* sptr, const int32_t* scol,
+                                             const SellPat& pat, const VT* val, const XT* u, const XT* w,
+                                             const XT* r, YT* y, const StepCoef<typename AccOf<XT>::type>& c,
+                                             const double* rdot) {
+    if (row >= n) return 0.0;
+    if (pat.pstart != nullptr)
+        return sell_row<VT, XT, YT, DOT, true, UNIT>(row, n, sptr, nullptr, pat, val, u, w, r, y, c, rdot);
+    return sell_row<VT, XT, YT, DOT, false, UNIT>(row, n, sptr, scol, pat, val, u, w, r, y, c, rdot);
+}
+
+__global__ void __launch_bounds__(256, 6) bk_sell_opq(const BDesc* __restrict__ D, BState* S,
+                                                   const BTile* __restrict__ T, BCtl* ctl, double* partials) {
+    const int tid = threadIdx.x;
+    const int nt = ctl->nstiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const BTile tl = T[t];
+        BState* st = S + tl.pair;
+        if (st->phase != PH_RUN) continue;
+        const BDesc* dp = D + tl.pair;
+        const int n = dp->n;
+        const SellPat pat = dp->pat;
+        const int32_t *sptr = dp->sptr, *scol = dp->scol;
+        const double* val = dp->val64;
+        const double* p = dp->p;
+        double* q = dp->q;
+        StepCoef<double> c;   // q = A' p + shift p, (p, q)
+        c.ca = dp->shift; c.cb = 0.0; c.cc = 0.0; c.cd = 1.0;
+        c.terms = (c.ca != 0.0 ? kTermU : 0) | kUnitD;
+        const int tile0 = dp->tile0, ntl = dp->tile1 - dp->tile0;
+        double dv = 0.0;
+        const int f1 = min(tl.f0 + kSellTileRows, n);
+#pragma unroll 1
+        for (int f = tl.f0; f < f1; f += kFT)
+            dv += sell_block<double, double, double, 2, true>(f + tid, n, sptr, scol, pat, val, p, nullptr, nullptr, q,
+                                                               c, nullptr);
+        reduce_slot(dv, partials, t, tile0, ntl, st, ctl, BF_ALPHA);
+    }
+}
+
+// PART: 0 every slot (float64 apply), 1 only the slots whose last step is
+// j (with (r, z)), 2 only the others -- the float kernels are split so that
+// each inlines one row path and keeps its register budget
+template <typename VT, int PART>
+__global__ void __launch_bounds__(256, std::is_same<VT, double>::value ? 6 : 4) bk_sell_cheb(const BDesc* __restrict__ D, BState* S,
+                                                    const BTile* __restrict__ T, const BCoef* __restrict__ C,
+                                                    BCtl* ctl, double* partials, int j,
+                                                    const int* __restrict__ ntile_step) {
+    constexpr bool F64 = std::is_same<VT, double>::value;
+    using XT = typename std::conditional<F64, double, float>::type;
+    using AT = XT;
+    const int tid = threadIdx.x;
+    const int nt = ntile_step[j];   // tiles of slots with k >= j (ordered by degree)
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const BTile tl = T[t];
+        BState* st = S + tl.pair;
+        const int ph = st->phase;
+        if (ph != PH_RUN && ph != PH_INIT) continue;
+        const BDesc* dp = D + tl.pair;
+        const int k = dp->k;
+        if (j > k) continue;
+        if ((PART == 1 && j != k) || (PART == 2 && j == k)) continue;
+        const int vdt = dp->vdtP;
+        if (!F64 && (vdt == NC_BF16) != std::is_same<VT, __nv_bfloat16>::value) continue;   // the other kernel's
+        // the fields this step needs, read once per tile
+        const int n = dp->n;
+        const int32_t* sptr = dp->sptr;
+        const int32_t* scol = dp->scol;
+        const SellPat pat = dp->pat;
+        const VT* val = F64 ? reinterpret_cast<const VT*>(dp->val64) : static_cast<const VT*>(dp->valP);
+        const double* r64 = dp->r;
+        double* z = dp->z;
+        XT *t0, *t1, *t2;
+        const XT* r;
+        if constexpr (F64) {
+            t0 = dp->dt0; t1 = dp->dt1; t2 = dp->dt2;
+            r = dp->r;
+        } else {
+            t0 = dp->t0; t1 = dp->t1; t2 = dp->t2;
+            r = dp->r32;
+        }
+        // the rotating vectors by index, selected (not an indexed array: no local memory)
+        auto tb = [&](int i) -> XT* { return i == 0 ? t0 : (i == 1 ? t1 : t2); };
+        const int tile0 = dp->tile0, ntl = dp->tile1 - dp->tile0;
+        const BCoef bc = C[dp->coef0 + j - 1];
+        StepCoef<AT> c;
+        if constexpr (F64) {
+            c.ca = bc.e0d; c.cb = bc.cbd; c.cc = bc.ccd; c.cd = bc.exd;
+        } else {
+            c.ca = bc.e0; c.cb = bc.cb; c.cc = bc.cc; c.cd = bc.ex;
+        }
+        c.terms = bc.terms;
+        const XT* u = (j == 1) ? r : tb((j - 1) % 3);
+        const XT* w = (j >= 3) ? tb((j - 2) % 3) : nullptr;
+        const int f1 = min(tl.f0 + kSellTileRows, n);
+        const bool unit = F64 && bc.xu;
+        if constexpr (PART != 2) {
+            if (j == k) {
+                double dv = 0.0;
+#pragma unroll 1
+                for (int f = tl.f0; f < f1; f += kFT)
+                    dv += unit ? sell_block<VT, XT, double, 1, F64>(f + tid, n, sptr, scol, pat, val, u, w, r, z, c,
+                                                                     r64)
+                               : sell_block<VT, XT, double, 1, false>(f + tid, n, sptr, scol, pat, val, u, w, r, z, c,
+                                                                       r64);
+                reduce_slot(dv, partials, t, tile0, ntl, st, ctl, BF_RZ);
+                continue;
+            }
+        }
+        if constexpr (PART != 1) {
+            XT* y = tb(j % 3);
+#pragma unroll 1
+            for (int f = tl.f0; f < f1; f += kFT) {
+                if (unit) sell_block<VT, XT, XT, 0, F64>(f + tid, n, sptr, scol, pat, val, u, w, r, y, c, nullptr);
+                else sell_block<VT, XT, XT, 0, false>(f + tid, n, sptr, scol, pat, val, u, w, r, y, c, nullptr);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) bk_sell_true(const BDesc* __restrict__ D, BState* S,
+                                                    const BTile* __restrict__ T, BCtl* ctl, double* partials) {
+    const int tid = threadIdx.x;
+    const int nt = ctl->nstiles;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const BTile tl = T[t];
+        BState* st = S + tl.pair;
+        if (st->phase != PH_FINISH) continue;
+        const BDesc* dp = D + tl.pair;
+        const int n = dp->n;
+        const SellPat pat = dp->pat;
+        const int32_t *sptr = dp->sptr, *scol = dp->scol;
+        const double* val = dp->val64;
+        StepCoef<double> c;   // q = b - (A' x + shift x), ||q||^2
+        c.ca = -dp->shift; c.cb = 0.0; c.cc = 1.0; c.cd = -1.0;
+        c.terms = (c.ca != 0.0 ? kTermU : 0) | kTermR;
+        const double *x = dp->x, *b = dp->b;
+        double* q = dp->q;
+        const int tile0 = dp->tile0, ntl = dp->tile1 - dp->tile0;
+        double dv = 0.0;
+        const int f1 = min(tl.f0 + kSellTileRows, n);
+#pragma unroll 1
+        for (int f = tl.f0; f < f1; f += kFT)
+            dv += sell_block<double, double, double, 3, false>(f + tid, n, sptr, scol, pat, val, x, nullptr, b, q, c,
+                                                                nullptr);
+        reduce_slot(dv, partials, t, tile0, ntl, st, ctl, BF_TRUE);
+    }
+}
+
 __global__ void bk_cond(BCtl* ctl, cudaGraphConditionalHandle h, int use_cond) {
     ctl->iters_this_call += 1;
     const int go = ctl->active > 0 && ctl->iters_this_call < ctl->iter_limit;
@@ -347,6 +524,12 @@ __global__ void bk_cond(BCtl* ctl, cudaGraphConditionalHandle h, int use_cond) {
 
 __global__ void bk_scale(int n, const double* __restrict__ in, double s, double* __restrict__ out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = in[i] * s;
+}
+
+// out = s * d .* in (a Jacobi-scaled explicit matrix: d = d^{-1/2}; s = 0 for b = 0)
+__global__ void bk_scale_vec(int n, const double* __restrict__ in, const double* __restrict__ d, double s,
+                             double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = s * d[i] * in[i];
 }
 
 }  // namespace
@@ -369,6 +552,11 @@ struct nc_batch_s {
     BVch* d_vch = nullptr;
     BCoef* d_coef = nullptr;
     int* d_ntile_step = nullptr;  // tiles of slots with k >= j, j = 0..kmax
+    BTile* d_stiles = nullptr;    // tiles of explicit-matrix slots
+    int* d_sntile_step = nullptr; // and their counts with k >= j
+    int cap_stiles = 0;
+    int graph_sell = 0;           // explicit-slot kernels the captured iteration launches:
+                                  // bit 0 float32 / float64 values, bit 1 bfloat16 values
     double* d_partials = nullptr;
     double* pool64 = nullptr;
     float* pool32 = nullptr;
@@ -462,10 +650,27 @@ nc_status grow(void** p, int* cap, int need, size_t elem) {
 }
 
 // One PCG iteration of every slot (the graph body).
+// Persistent grid of a kernel: as many CTAs as the device holds at once (a
+// second, partial wave would start its statically assigned tiles late),
+// capped at kCtasPerSm per SM.
+template <typename K>
+int resident_grid(K kernel, int threads) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm <= 0) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    if (per_sm > kCtasPerSm) per_sm = kCtasPerSm;
+    return per_sm * num_sms();
+}
+
 void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, cudaStream_t st) {
     const dim3 tb(kTX, kTY);
-    const int grid = vec_grid_max();   // persistent CTAs over the work lists
+    const int grid = vec_grid_max();   // persistent CTAs over the work lists (stencil and vector kernels)
     bk_opq<<<grid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
+    if (B->graph_sell)
+        bk_sell_opq<<<resident_grid(bk_sell_opq, 256), 256, 0, st>>>(B->d_desc, B->d_state, B->d_stiles, B->d_ctl,
+                                                                     B->d_partials);
     bk_axpy<<<grid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
     for (int j = 1; j <= B->kmax; ++j) {
         if (B->flags & NC_BATCH_F64_APPLY)
@@ -474,9 +679,30 @@ void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, c
         else
             bk_cheb<false><<<grid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_coef, B->d_ctl,
                                                       B->d_partials, j, B->d_ntile_step);
+        if (B->graph_sell) {
+#define NB_SELL_ARGS B->d_desc, B->d_state, B->d_stiles, B->d_coef, B->d_ctl, B->d_partials, j, B->d_sntile_step
+#define NB_SELL_CHEB(VT, P) bk_sell_cheb<VT, P><<<resident_grid(bk_sell_cheb<VT, P>, 256), 256, 0, st>>>(NB_SELL_ARGS)
+            if (B->flags & NC_BATCH_F64_APPLY) {
+                NB_SELL_CHEB(double, 0);
+            } else {
+                if (B->graph_sell & 1) {
+                    NB_SELL_CHEB(float, 1);
+                    NB_SELL_CHEB(float, 2);
+                }
+                if (B->graph_sell & 2) {
+                    NB_SELL_CHEB(__nv_bfloat16, 1);
+                    NB_SELL_CHEB(__nv_bfloat16, 2);
+                }
+            }
+#undef NB_SELL_CHEB
+#undef NB_SELL_ARGS
+        }
     }
     bk_pupd<<<grid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
     bk_true<<<grid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
+    if (B->graph_sell)
+        bk_sell_true<<<resident_grid(bk_sell_true, 256), 256, 0, st>>>(B->d_desc, B->d_state, B->d_stiles,
+                                                                       B->d_ctl, B->d_partials);
     bk_cond<<<1, 1, 0, st>>>(B->d_ctl, h, use_cond);
 }
 
@@ -520,39 +746,52 @@ nc_status build_batch_graph(nc_batch B) {
 
 // Rebuild the work lists and descriptors of all slots in use and upload them.
 nc_status sync_tables(nc_batch B, cudaStream_t st) {
-    std::vector<BTile> tiles;
+    std::vector<BTile> tiles, stiles;
     std::vector<BVch> vch;
     std::vector<BCoef> coef;
     std::vector<int> order;
     for (int s = 0; s < B->cap_slots; ++s)
         if (B->used[s]) order.push_back(s);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->kdeg[a] > B->kdeg[b]; });
-    std::vector<int> nstep(B->kmax + 1, 0);
+    std::vector<int> nstep(B->kmax + 1, 0), snstep(B->kmax + 1, 0);
     for (int s : order) {
         BDesc& d = B->desc[s];
-        d.tile0 = (int)tiles.size();
-        const int nxy = d.nx * d.ny, tz = (d.nz + kZC - 1) / kZC;
-        for (int bz = 0; bz < tz; ++bz)
-            for (int f0 = 0; f0 < nxy; f0 += kFT) tiles.push_back(BTile{s, f0, 0, bz});
-        d.tile1 = (int)tiles.size();
-        for (int j = 0; j <= std::min(d.k, B->kmax); ++j) nstep[j] = d.tile1;   // prefix ends after this slot
+        if (d.kind == SLOT_SELL) {   // kSellTileRows-row tiles of the layout, in their own list
+            d.tile0 = (int)stiles.size();
+            for (int f0 = 0; f0 < d.n; f0 += kSellTileRows) stiles.push_back(BTile{s, f0, 0, 0});
+            d.tile1 = (int)stiles.size();
+            for (int j = 0; j <= std::min(d.k, B->kmax); ++j) snstep[j] = d.tile1;
+        } else {
+            d.tile0 = (int)tiles.size();
+            const int nxy = d.nx * d.ny, tz = (d.nz + kZC - 1) / kZC;
+            for (int bz = 0; bz < tz; ++bz)
+                for (int f0 = 0; f0 < nxy; f0 += kFT) tiles.push_back(BTile{s, f0, 0, bz});
+            d.tile1 = (int)tiles.size();
+            for (int j = 0; j <= std::min(d.k, B->kmax); ++j) nstep[j] = d.tile1;   // prefix ends after this slot
+        }
         d.vch0 = (int)vch.size();
         for (int i = 0; i < d.n; i += kVch) vch.push_back(BVch{s, i});
         d.vch1 = (int)vch.size();
         d.coef0 = (int)coef.size();
         coef.insert(coef.end(), B->coefs[s].begin(), B->coefs[s].end());
     }
-    const int cap_t = B->cap_tiles, cap_v = B->cap_vch;
+    const int cap_t = B->cap_tiles, cap_v = B->cap_vch, cap_s = B->cap_stiles;
     nc_status s;
     if ((s = grow(reinterpret_cast<void**>(&B->d_tiles), &B->cap_tiles, (int)tiles.size(), sizeof(BTile)))) return s;
+    if ((s = grow(reinterpret_cast<void**>(&B->d_stiles), &B->cap_stiles, (int)stiles.size(), sizeof(BTile))))
+        return s;
     if ((s = grow(reinterpret_cast<void**>(&B->d_vch), &B->cap_vch, (int)vch.size(), sizeof(BVch)))) return s;
     int cap_c = B->cap_coef;
     if ((s = grow(reinterpret_cast<void**>(&B->d_coef), &B->cap_coef, (int)coef.size(), sizeof(BCoef)))) return s;
-    const bool realloc_ = cap_t != B->cap_tiles || cap_v != B->cap_vch || cap_c != B->cap_coef;
+    int want_sell = 0;
+    for (const BTile& tl : stiles) want_sell |= B->desc[tl.pair].vdtP == NC_BF16 ? 2 : 1;
+    const bool realloc_ = cap_t != B->cap_tiles || cap_v != B->cap_vch || cap_c != B->cap_coef ||
+                          cap_s != B->cap_stiles || want_sell != B->graph_sell;
     if (realloc_) {
         if (B->d_partials) cudaFree(B->d_partials);
         B->d_partials = nullptr;
-        const int np = std::max(B->cap_tiles, B->cap_vch);
+        B->graph_sell = want_sell;
+        const int np = std::max(std::max(B->cap_tiles, B->cap_vch), B->cap_stiles);
         if ((s = balloc(reinterpret_cast<void**>(&B->d_partials), sizeof(double) * (size_t)np))) return s;
         if ((s = build_batch_graph(B))) return s;
     }
@@ -563,12 +802,16 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
     if (!coef.empty())
         NB_CU(cudaMemcpyAsync(B->d_coef, coef.data(), sizeof(BCoef) * coef.size(), cudaMemcpyHostToDevice, st));
     NB_CU(cudaMemcpyAsync(B->d_ntile_step, nstep.data(), sizeof(int) * nstep.size(), cudaMemcpyHostToDevice, st));
+    if (!stiles.empty())
+        NB_CU(cudaMemcpyAsync(B->d_stiles, stiles.data(), sizeof(BTile) * stiles.size(), cudaMemcpyHostToDevice, st));
+    NB_CU(cudaMemcpyAsync(B->d_sntile_step, snstep.data(), sizeof(int) * snstep.size(), cudaMemcpyHostToDevice, st));
     // states of slots admitted or released since the last run (pinned source)
     for (int slot : B->state_upload)
         NB_CU(cudaMemcpyAsync(B->d_state + slot, &B->h_state[slot], sizeof(BState), cudaMemcpyHostToDevice, st));
     B->state_upload.clear();
     NB_CU(cudaMemcpyAsync(B->d_desc, B->desc.data(), sizeof(BDesc) * B->cap_slots, cudaMemcpyHostToDevice, st));
     B->h_ctl->ntiles = (int)tiles.size();
+    B->h_ctl->nstiles = (int)stiles.size();
     B->h_ctl->nvch = (int)vch.size();
     // the host vectors must outlive the copies
     NB_CU(cudaStreamSynchronize(st));
@@ -608,6 +851,7 @@ nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, int fl
         if ((s = balloc(reinterpret_cast<void**>(&B->d_state), sizeof(BState) * max_slots))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->d_ctl), sizeof(BCtl)))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->d_ntile_step), sizeof(int) * (kmax + 1)))) break;
+        if ((s = balloc(reinterpret_cast<void**>(&B->d_sntile_step), sizeof(int) * (kmax + 1)))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->pool64), sizeof(double) * 6 * (size_t)max_unknowns))) break;
         // apply vectors: 4 float32 per unknown (t0..t2, r32), or 3 float64 (+ slack
         // for the 16-byte rounding of the split below)
@@ -737,6 +981,136 @@ nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx
     return NC_OK;
 }
 
+nc_status pcg_batch_add_solver(nc_batch B, nc_solver S, const double* b_dev, void* stream, int* slot) {
+    if (!B || !S || !slot || !b_dev) return NC_ERR_ARG;
+    *slot = -1;
+    const bool f64 = (B->flags & NC_BATCH_F64_APPLY) != 0;
+    // an explicit matrix in a sliced layout, the Chebyshev form, no residual
+    // replacement, scalar (Jacobi) scaling only; the apply precision must be
+    // the engine's
+    if (S->op64.kind != OP_SELL || S->opP.kind != OP_SELL || S->nlev >= 0 || S->opt.rr_period > 0 ||
+        S->A->wblk != nullptr || f64 == S->mixed)
+        return NC_ERR_UNSUPPORTED;
+    if (S->k < 1 || S->k > B->kmax || S->n < 1) return NC_ERR_ARG;
+    const int64_t n = S->n;
+    int s = -1;
+    for (int i = 0; i < B->cap_slots; ++i)
+        if (!B->used[i]) { s = i; break; }
+    if (s < 0) return NC_ERR_ADMISSION;
+    const int64_t o = pool_alloc(B, n);
+    if (o < 0) return NC_ERR_ADMISSION;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BDesc d{};
+    d.kind = SLOT_SELL;
+    d.nx = (int)n; d.ny = 1; d.nz = 1; d.n = (int)n; d.k = S->k;
+    d.sptr = S->op64.ptr;
+    d.scol = S->op64.col;
+    d.pat = S->op64.pat;
+    d.val64 = static_cast<const double*>(S->op64.val);
+    d.valP = S->opP.val;
+    d.vdtP = S->opP.vdt;
+    d.shift = S->shift;
+    d.disv = S->A->scaled ? S->A->dis : nullptr;
+    double* base64 = B->pool64 + 6 * o;
+    d.b = base64; d.x = base64 + n; d.r = base64 + 2 * n; d.z = base64 + 3 * n; d.p = base64 + 4 * n;
+    d.q = base64 + 5 * n;
+    if (f64) {
+        double* baseP = reinterpret_cast<double*>(B->pool32) + 3 * o;
+        d.dt0 = baseP; d.dt1 = baseP + n; d.dt2 = baseP + 2 * n;
+    } else {
+        float* base32 = B->pool32 + 4 * o;
+        d.t0 = base32; d.t1 = base32 + n; d.t2 = base32 + 2 * n; d.r32 = base32 + 3 * n;
+    }
+    // the solver's own step coefficients, as its solves take them (the
+    // float64 iterates scaled so that the product's coefficient is 1)
+    const std::vector<StepC> sc = step_coefs(S, true);
+    std::vector<BCoef> cf(S->k);
+    for (int j = 1; j <= S->k; ++j) {
+        BCoef c{};
+        c.e0 = (float)sc[j].ca;
+        c.ex = (float)sc[j].cd;
+        c.cb = (float)sc[j].cb;
+        c.cc = (float)sc[j].cc;
+        c.e0d = sc[j].ca;
+        c.exd = sc[j].cd;
+        c.cbd = sc[j].cb;
+        c.ccd = sc[j].cc;
+        c.terms = (sc[j].ca != 0.0 ? kTermU : 0) | (sc[j].cb != 0.0 ? kTermW : 0) | (sc[j].cc != 0.0 ? kTermR : 0) |
+                  (sc[j].cd == 1.0 ? kUnitD : 0);
+        c.xu = sc[j].cd == 1.0 ? 1 : 0;
+        cf[j - 1] = c;
+    }
+    B->desc[s] = d;
+    B->used[s] = 1;
+    B->kdeg[s] = S->k;
+    B->dis[s] = 1.0;   // the scaling is the vector d.disv
+    B->coefs[s] = cf;
+    B->off[s] = o;
+    B->dirty = true;
+    const int grid = (int)std::min<int64_t>(4096, (n + 255) / 256);
+    if (d.disv != nullptr)
+        bk_scale_vec<<<grid, 256, 0, st>>>((int)n, b_dev, d.disv, 1.0, d.b);
+    else
+        bk_scale<<<grid, 256, 0, st>>>((int)n, b_dev, 1.0, d.b);
+    NB_CU(cudaGetLastError());
+    BState init{};
+    init.phase = PH_INIT;
+    init.status = NC_ERR_MAXIT;
+    B->h_state[s] = init;
+    B->state_upload.push_back(s);
+    B->h_ctl->active += 1;
+    B->stat_launches += 1;
+    *slot = s;
+    return NC_OK;
+}
+
+nc_status pcg_solve_batched(int nsys, const nc_solver* S, const int* nrhs, const double* const* B_dev,
+                            double* const* X_dev, double tol, int maxit, void* stream, nc_result* res) {
+    if (nsys < 1 || !S || !nrhs || !B_dev || !X_dev || !res || !(tol >= 0.0) || maxit < 0) return NC_ERR_ARG;
+    int slots = 0, kmax = 1;
+    int64_t units = 0;
+    bool mixed = false;
+    for (int i = 0; i < nsys; ++i) {
+        if (!S[i] || nrhs[i] < 1 || !B_dev[i] || !X_dev[i]) return NC_ERR_ARG;
+        if (i == 0) mixed = S[i]->mixed;
+        else if (S[i]->mixed != mixed) return NC_ERR_UNSUPPORTED;   // one apply precision per batch
+        slots += nrhs[i];
+        units += S[i]->n * nrhs[i];
+        kmax = std::max(kmax, S[i]->k);
+    }
+    nc_batch B = nullptr;
+    nc_status st = pcg_batch_create(slots, units, kmax, mixed ? 0 : NC_BATCH_F64_APPLY, stream, &B);
+    if (st != NC_OK) return st;
+    std::vector<int> ids;
+    ids.reserve(slots);
+    for (int i = 0; i < nsys && st == NC_OK; ++i)
+        for (int c = 0; c < nrhs[i] && st == NC_OK; ++c) {
+            int sl = -1;
+            st = pcg_batch_add_solver(B, S[i], B_dev[i] + (size_t)c * S[i]->n, stream, &sl);
+            ids.push_back(sl);
+        }
+    int left = 0;
+    if (st == NC_OK) st = pcg_batch_run(B, tol, maxit, 0, stream, &left);
+    nc_status first = NC_OK;
+    int q = 0;
+    for (int i = 0; i < nsys && st == NC_OK; ++i)
+        for (int c = 0; c < nrhs[i] && st == NC_OK; ++c, ++q) {
+            int done = 0;
+            st = pcg_batch_status(B, ids[q], &done, &res[q]);
+            if (st == NC_OK) st = pcg_batch_collect(B, ids[q], X_dev[i] + (size_t)c * S[i]->n, stream);
+            if (st == NC_OK && first == NC_OK && res[q].status != NC_OK) first = (nc_status)res[q].status;
+        }
+    if (st == NC_OK) {
+        const cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) {
+            g_batch_err = e;
+            st = NC_ERR_CUDA;
+        }
+    }
+    pcg_batch_destroy(B);
+    return st != NC_OK ? st : first;
+}
+
 nc_status pcg_batch_run(nc_batch B, double tol, int maxit, int iter_limit, void* stream, int* active_left) {
     if (!B || !(tol >= 0.0) || maxit < 0) return NC_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -768,7 +1142,10 @@ nc_status pcg_batch_run(nc_batch B, double tol, int maxit, int iter_limit, void*
         NB_CU(cudaStreamSynchronize(st));
         // one iteration: opq, axpy, kmax Chebyshev steps, pupd, true, cond
         B->stat_iters += c->iters_this_call;
-        B->stat_launches += (int64_t)c->iters_this_call * (B->kmax + 5);
+        // explicit-slot Chebyshev kernels per step: 1 (float64), 2 per float value type
+        const int nsell = (B->flags & NC_BATCH_F64_APPLY) ? (B->graph_sell ? 1 : 0)
+                                                          : 2 * ((B->graph_sell & 1) + ((B->graph_sell >> 1) & 1));
+        B->stat_launches += (int64_t)c->iters_this_call * (B->kmax + 5 + (nsell ? nsell * B->kmax + 2 : 0));
     }
     if (active_left) *active_left = B->h_ctl->active;
     return NC_OK;
@@ -797,7 +1174,11 @@ nc_status pcg_batch_collect(nc_batch B, int slot, double* x_dev, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const BDesc& d = B->desc[slot];
     const double scale = B->h_state[slot].bb == 0.0 ? 0.0 : B->dis[slot];
-    bk_scale<<<std::min<int64_t>(4096, ((int64_t)d.n + 255) / 256), 256, 0, st>>>(d.n, d.x, scale, x_dev);
+    const int grid = (int)std::min<int64_t>(4096, ((int64_t)d.n + 255) / 256);
+    if (d.disv != nullptr)
+        bk_scale_vec<<<grid, 256, 0, st>>>(d.n, d.x, d.disv, scale, x_dev);
+    else
+        bk_scale<<<grid, 256, 0, st>>>(d.n, d.x, scale, x_dev);
     NB_CU(cudaGetLastError());
     B->stat_launches += 1;
     return NC_OK;
@@ -850,6 +1231,8 @@ nc_status pcg_batch_destroy(nc_batch B) {
     cudaFree(B->d_vch);
     cudaFree(B->d_coef);
     cudaFree(B->d_ntile_step);
+    cudaFree(B->d_stiles);
+    cudaFree(B->d_sntile_step);
     cudaFree(B->d_partials);
     cudaFree(B->pool64);
     cudaFree(B->pool32);

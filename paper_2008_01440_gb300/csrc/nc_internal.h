@@ -133,6 +133,7 @@ struct nc_solver_s {
     double* pcoef = nullptr;          // 4*(k+1) step coefficients, shifted-operator form
     std::vector<int32_t> h_sell_ptr;  // host copy of the scalar SELL slice offsets
     std::vector<nc::TuneRec> tune;    // tuner measurements (pcg_tune_candidate)
+    bool tune_cached = false;         // choices taken from the NC_TUNE_CACHE file
     int num_sms = 0;                  // SM count of the device at setup
 };
 

@@ -4,6 +4,8 @@
 // layouts (NC_FORMAT_TUNE) and between step-kernel variants (NC_STEP_TUNE).
 #include <algorithm>
 #include <array>
+#include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <unordered_map>
 
@@ -617,6 +619,110 @@ nc_status tune_kind(nc_solver S, OpView& op, int kind, cudaStream_t st) {
 
 }  // namespace
 
+// Persistent tuner choices.  When the environment variable NC_TUNE_CACHE
+// names a text file, a solver that would be tuned first looks for its
+// operator's signature there (rows, stored entries, offset sets, table
+// size, apply precision, SM count and compute capability) and takes the
+// recorded choices without measuring; otherwise it measures and appends one
+// line.  Each line is written by one append, so processes sharing the file
+// do not interleave lines.  (Timings taken under a profiler mislead the
+// tuner; a cache written by an unprofiled run makes the profiled process
+// run what the unprofiled one ran.)
+constexpr int kTuneFields = 12;
+
+void tune_to_ints(const StepTune& t, int* v) {
+    const int f[kTuneFields] = {t.variant,     t.rpt,         t.stages,    t.ctas_per_sm,     t.contig,
+                                t.lookahead,   t.dot_variant, t.dot_rpt,   t.dot_stages,      t.dot_ctas_per_sm,
+                                t.dot_contig,  t.red_ctas_per_sm};
+    for (int i = 0; i < kTuneFields; ++i) v[i] = f[i];
+}
+
+void tune_from_ints(const int* v, StepTune& t) {
+    t.variant = v[0];
+    t.rpt = v[1];
+    t.stages = v[2];
+    t.ctas_per_sm = v[3];
+    t.contig = v[4];
+    t.lookahead = v[5];
+    t.dot_variant = v[6];
+    t.dot_rpt = v[7];
+    t.dot_stages = v[8];
+    t.dot_ctas_per_sm = v[9];
+    t.dot_contig = v[10];
+    t.red_ctas_per_sm = v[11];
+}
+
+bool tune_ints_valid(const int* v) {
+    auto var = [](int x) { return x == STEP_DIRECT || x == STEP_STAGED; };
+    return var(v[0]) && v[1] >= 1 && v[1] <= 2 && v[2] >= 2 && v[2] <= 4 && v[3] >= 1 && v[3] <= 8 &&
+           (v[4] == 0 || v[4] == 1) && v[5] >= -1 && var(v[6]) && v[7] >= 1 && v[7] <= 2 && v[8] >= 2 &&
+           v[8] <= 4 && v[9] >= 1 && v[9] <= 8 && (v[10] == 0 || v[10] == 1) && v[11] >= 1 &&
+           v[11] <= kRedOneTile;
+}
+
+std::string tune_key(nc_solver S) {
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaGetLastError();
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "ncpcg-tune-v1 n=%lld e=%lld p=%lld o=%d dt=%d sm=%d cc=%d%d", (long long)S->n,
+                  (long long)(S->h_sell_ptr.empty() ? 0 : S->h_sell_ptr.back()), (long long)S->npatterns,
+                  S->opP.tune.npoff, S->vdt, S->num_sms, major, minor);
+    return std::string(buf);
+}
+
+// true when the cache held this operator's choices (applied to opP, op64)
+bool tune_cache_load(nc_solver S, const char* path) {
+    std::FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    const std::string key = tune_key(S) + " |";
+    char line[1024];
+    bool found = false;
+    while (!found && std::fgets(line, sizeof(line), f)) {
+        if (std::strncmp(line, key.c_str(), key.size()) != 0) continue;
+        int a[kTuneFields], b[kTuneFields];
+        const char* q = line + key.size();
+        int used = 0;
+        bool ok = std::sscanf(q, " P%n", &used) >= 0 && used > 0;
+        q += used;
+        for (int i = 0; ok && i < kTuneFields; ++i) {
+            ok = std::sscanf(q, "%d%n", &a[i], &used) == 1;
+            q += used;
+        }
+        used = 0;
+        ok = ok && std::sscanf(q, " | D%n", &used) >= 0 && used > 0;
+        q += used;
+        for (int i = 0; ok && i < kTuneFields; ++i) {
+            ok = std::sscanf(q, "%d%n", &b[i], &used) == 1;
+            q += used;
+        }
+        if (ok && tune_ints_valid(a) && tune_ints_valid(b)) {
+            tune_from_ints(a, S->opP.tune);
+            tune_from_ints(b, S->op64.tune);
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_cache_store(nc_solver S, const char* path) {
+    int a[kTuneFields], b[kTuneFields];
+    tune_to_ints(S->opP.tune, a);
+    tune_to_ints(S->op64.tune, b);
+    std::string line = tune_key(S) + " | P";
+    for (int v : a) line += " " + std::to_string(v);
+    line += " | D";
+    for (int v : b) line += " " + std::to_string(v);
+    line += "\n";
+    std::FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fputs(line.c_str(), f);
+    std::fclose(f);
+}
+
 nc_status setup_step_kernels(nc_solver S, cudaStream_t st) {
     const nc_options& o = S->opt;
     StepTune t;
@@ -638,6 +744,11 @@ nc_status setup_step_kernels(nc_solver S, cudaStream_t st) {
     }
     const bool tune = psell && (mode == NC_STEP_TUNE || (mode == NC_STEP_AUTO && S->n >= kTuneMinRows));
     if (!tune) return NC_OK;
+    const char* cache = std::getenv("NC_TUNE_CACHE");
+    if (cache != nullptr && cache[0] != '\0' && tune_cache_load(S, cache)) {
+        S->tune_cached = true;
+        return NC_OK;
+    }
     // the buffers the measured launches read and write start at zero
     const size_t vb = S->mixed ? sizeof(float) : sizeof(double);
     const size_t n = (size_t)S->n;
@@ -651,6 +762,7 @@ nc_status setup_step_kernels(nc_solver S, cudaStream_t st) {
     } else {
         S->op64.tune = S->opP.tune;   // the same operator: q = A p takes the dot-step choice
     }
+    if (cache != nullptr && cache[0] != '\0') tune_cache_store(S, cache);
     return NC_OK;
 }
 

@@ -1,6 +1,7 @@
 // Epilogue shared by the fused step kernels of every matrix format:
 //     y = ca*u + cb*w + cc*r + cd*(A u)   (one Chebyshev step of Algorithm 2)
-// plus an optional dot product finished by the last CTA.
+// plus an optional dot product finished by the last CTA (DOT: 0 none,
+// 1 (rdot, y), 2 (u, y), 3 (y, y)).
 #pragma once
 
 #include "nc_common.cuh"
@@ -92,6 +93,7 @@ __device__ __forceinline__ double step_row_out(int row, AT acc, const StepCoef<A
     y[row] = yo;
     if (DOT == 1) return rdot[row] * (double)yo;
     if (DOT == 2) return (double)u[row] * (double)yo;
+    if (DOT == 3) return (double)yo * (double)yo;
     return 0.0;
 }
 
@@ -111,6 +113,7 @@ __device__ __forceinline__ double sell_row_out(int row, AT acc, const StepCoef<A
     y[row] = yo;
     if (DOT == 1) return rdot[row] * (double)yo;
     if (DOT == 2) return (double)u[row] * (double)yo;
+    if (DOT == 3) return (double)yo * (double)yo;
     return 0.0;
 }
 

@@ -247,3 +247,30 @@ def test_staged_gather_windows_and_fallback(env, offsets, n, dt):
         assert np.array_equal(zs, zd), rpt
     ref = O.cheb_apply(O.csr_matvec(A.rowptr, A.col, A.val, n), v, O.cheb_params(4.0, 16.0, 1.001), 7)
     assert rel_err(zd, ref) <= TOL[dt] and elem_err(zd, ref) <= TOL[dt]
+
+
+def test_tune_cache_reproduces_the_choice(env, tmp_path, monkeypatch):
+    """With NC_TUNE_CACHE set, the first solver on an operator measures and
+    appends its choices; a second solver on the same operator reads them
+    (nothing measured), runs the same kernels, and gives the same bits."""
+    torch, nc = env
+    A = W.diffusion_3d_7pt_lognormal(48, seed=5)
+    M = nc.nc_matrix_jacobi(csr_to_gpu(torch, nc, A))
+    lo, hi, _, _ = nc.nc_bounds_lanczos(M, 20, to_dev(torch, W.uniform_vector(A.n, seed=3)))
+    path = tmp_path / "tune.cache"
+    monkeypatch.setenv("NC_TUNE_CACHE", str(path))
+    vd = to_dev(torch, W.uniform_vector(A.n, seed=9))
+    i1, z1 = _apply(torch, nc, M, A.n, lo, hi, 10, 1.001, vd, apply_dtype="f32", step_kernel="tune")
+    assert i1["tune_candidates"] > 0 and i1["tune_from_cache"] == 0
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith(f"ncpcg-tune-v1 n={A.n} ")
+    i2, z2 = _apply(torch, nc, M, A.n, lo, hi, 10, 1.001, vd, apply_dtype="f32", step_kernel="tune")
+    assert i2["tune_candidates"] == 0 and i2["tune_from_cache"] == 1
+    keys = ("step_kernel", "dot_step_kernel", "step_stages", "step_ctas_per_sm", "step_rows_per_thread",
+            "dot_step_stages", "dot_step_ctas_per_sm", "prefetch_tiles", "red_ctas_per_sm")
+    assert {k: i1[k] for k in keys} == {k: i2[k] for k in keys}
+    assert np.array_equal(z1, z2)
+    assert len(path.read_text().splitlines()) == 1
+    # another precision is another signature: measured and appended
+    i3, _ = _apply(torch, nc, M, A.n, lo, hi, 10, 1.001, vd, apply_dtype="f64", step_kernel="tune")
+    assert i3["tune_from_cache"] == 0 and len(path.read_text().splitlines()) == 2

@@ -20,8 +20,10 @@ def test_step_byte_models():
 def test_traffic_is_keyed_by_layout_and_precision():
     assert bench.read_traffic("c2:2097152:psell", "f64") == 171_503_104
     assert bench.read_traffic("c2:2097152:sell", "f64") == 229_708_800
-    # no capture of this kernel in its current form: no number
-    assert bench.read_traffic("c2:2097152:psell", "f32") is None
+    assert bench.read_traffic("c2:2097152:psell", "f32") == 87_088_640
+    assert bench.read_traffic("c2:2097152:psell", "bf16") == 55_056_128
+    # no capture of this kernel in this form: no number
+    assert bench.read_traffic("c2:2097152:psell", "f16") is None
     assert bench.read_traffic("c2:2097152", "f64") is None
     # traffic at or below the algorithmic bytes: no re-reads
     assert bench.read_traffic("c2:2097152:psell", "f64") <= bench.psell_step_bytes(2_097_152, 14_581_760)
