@@ -113,7 +113,9 @@ typedef enum { NC_POLY_CHEBYSHEV = 0, NC_POLY_NEWTON = 1 } nc_poly_form;
  * on the solver's own operator and keeps the fastest for the plain steps and
  * for the steps with a dot product; pcg_tune_candidate lists what was
  * measured.  AUTO (default): TUNE for PSELL operators of at least 2^16 rows,
- * DIRECT otherwise.  When the environment variable NC_TUNE_CACHE names a
+ * DIRECT otherwise.  For matrix-free stencils TUNE (AUTO: at least 2^20
+ * points) times the z-chunk of the plain steps and, with a float apply, the
+ * planes per z-march batch.  When the environment variable NC_TUNE_CACHE names a
  * file, the choices are looked up there by the operator's signature (rows,
  * stored entries, offset sets, apply precision, SM count, compute
  * capability) and measured and appended only when absent.  Layouts other than PSELL, and the stencil and block
@@ -191,6 +193,10 @@ typedef struct {
                              results of that call are not valid)              */
     int32_t tune_from_cache; /* 1: the tuner's choices came from the file named
                              by NC_TUNE_CACHE (nothing measured)              */
+    int32_t stencil_zchunk;  /* matrix-free stencil: z-chunk (planes per CTA)
+                             of the plain steps; 0 for explicit matrices     */
+    int32_t stencil_planes_per_batch; /* and planes per z-march batch (0:
+                             the size policy, 2 or 4)                         */
 } nc_solver_info;
 
 /* One configuration measured by the tuner (pcg_setup with step_kernel =
@@ -202,6 +208,7 @@ typedef struct {
     int32_t step_kernel;  /* NC_STEP_DIRECT or NC_STEP_STAGED              */
     int32_t stages, ctas_per_sm, rows_per_thread, tile_order; /* STAGED    */
     int32_t prefetch_tiles, red_ctas_per_sm;                   /* DIRECT    */
+    int32_t zchunk, planes_per_batch; /* matrix-free stencil (else 0)      */
     double us;            /* mean duration of one launch (CUDA events)     */
     int32_t chosen;       /* 1: kept for that operator and step kind       */
     int32_t reserved0;

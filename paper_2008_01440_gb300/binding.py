@@ -60,14 +60,16 @@ class nc_solver_info(ctypes.Structure):
                 ("dot_step_rows_per_thread", ctypes.c_int32), ("dot_step_tile_order", ctypes.c_int32),
                 ("prefetch_tiles", ctypes.c_int32), ("red_ctas_per_sm", ctypes.c_int32),
                 ("tune_candidates", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("faults", ctypes.c_int32),
-                ("tune_from_cache", ctypes.c_int32)]
+                ("tune_from_cache", ctypes.c_int32), ("stencil_zchunk", ctypes.c_int32),
+                ("stencil_planes_per_batch", ctypes.c_int32)]
 
 
 class nc_tune_candidate(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int32), ("step_kernel", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("rows_per_thread", ctypes.c_int32), ("tile_order", ctypes.c_int32),
                 ("prefetch_tiles", ctypes.c_int32),
-                ("red_ctas_per_sm", ctypes.c_int32), ("us", ctypes.c_double), ("chosen", ctypes.c_int32),
+                ("red_ctas_per_sm", ctypes.c_int32), ("zchunk", ctypes.c_int32),
+                ("planes_per_batch", ctypes.c_int32), ("us", ctypes.c_double), ("chosen", ctypes.c_int32),
                 ("reserved0", ctypes.c_int32)]
 
 

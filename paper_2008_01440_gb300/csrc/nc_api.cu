@@ -305,6 +305,8 @@ nc_status pcg_get_info(nc_solver S, nc_solver_info* info) {
     info->num_sms = S->num_sms;
     info->faults = 0;
     info->tune_from_cache = S->tune_cached ? 1 : 0;
+    info->stencil_zchunk = S->opP.kind == OP_STENCIL ? stencil_zchunk(S->opP.geom) : 0;
+    info->stencil_planes_per_batch = S->opP.geom.pz;
     if (S->S) {
         int f = 0;
         if (cudaMemcpy(&f, &S->S->fault, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
@@ -325,6 +327,8 @@ nc_status pcg_tune_candidate(nc_solver S, int i, nc_tune_candidate* out) {
     out->ctas_per_sm = t.ctas_per_sm;
     out->rows_per_thread = t.rpt;
     out->tile_order = t.contig;
+    out->zchunk = t.zchunk;
+    out->planes_per_batch = t.pz;
     out->prefetch_tiles = t.lookahead;
     out->red_ctas_per_sm = t.red_ctas_per_sm;
     out->us = t.us;

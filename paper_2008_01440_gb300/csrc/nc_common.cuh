@@ -264,7 +264,12 @@ cudaError_t launch_sell_fill(int n, const int32_t* rowptr, const int32_t* col, c
 // Matrix-free 7-point stencil (c4 = {c0, cx, cy, cz}, host array).
 struct StencilGeom {
     int nx, ny, nz;
+    int zc = 0;   // plain steps: z-chunk (planes per CTA); 0 = the size policy
+    int pz = 0;   // plain float steps: planes per z-march batch (2 or 4); 0 = the policy
 };
+// The policy z-chunk (stencil_zchunk ignores g.zc): dot-product steps always
+// take it, so the partial-sum buffers sized from it hold.
+int stencil_zchunk_policy(const StencilGeom& g);
 int stencil_zchunk(const StencilGeom& g);
 dim3 stencil_grid(const StencilGeom& g);
 long long stencil_nblocks(const StencilGeom& g);

@@ -46,6 +46,7 @@ struct TuneRec {
     int op, variant, stages, ctas_per_sm, rpt, contig, lookahead, red_ctas_per_sm;
     double us;
     int chosen;
+    int zchunk = 0, pz = 0;   // matrix-free stencil: z-chunk and planes per batch
 };
 
 }  // namespace nc

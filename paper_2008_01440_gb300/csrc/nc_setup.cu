@@ -617,6 +617,46 @@ nc_status tune_kind(nc_solver S, OpView& op, int kind, cudaStream_t st) {
     return NC_OK;
 }
 
+constexpr int64_t kStencilTuneMinPoints = (int64_t)1 << 20;   // AUTO tunes stencils of at least this size
+
+// Matrix-free stencil: the z-chunk of the plain steps (planes per CTA; more
+// chunks fill the GPU, longer ones read fewer extra planes) and, in float,
+// the planes per z-march batch.  Candidates around the size policy.
+nc_status tune_stencil(nc_solver S, OpView& op, cudaStream_t st) {
+    const int nz = op.geom.nz;
+    const int pol = stencil_zchunk_policy(op.geom);
+    std::vector<int> zcs;
+    for (int z : {pol, pol / 2, 2 * pol, 32, 64, 128, 256}) {
+        z = std::min(z, nz);
+        if (z >= 4 && std::find(zcs.begin(), zcs.end(), z) == zcs.end()) zcs.push_back(z);
+    }
+    if (zcs.empty()) return NC_OK;
+    std::vector<int> pzs = S->mixed ? std::vector<int>{2, 4} : std::vector<int>{2};
+    double best = 0.0;
+    int ibest = -1;
+    for (int zc : zcs)
+        for (int pz : pzs) {
+            OpView v = op;
+            v.geom.zc = zc;
+            v.geom.pz = pz;
+            double us = 0.0;
+            NC_TRY(time_launches(st, [&]() { return launch_kind(S, v, 0, st); }, &us));
+            TuneRec rec{0, STEP_DIRECT, 0, 0, 1, 0, 0, 0, us, 0};
+            rec.zchunk = zc;
+            rec.pz = pz;
+            S->tune.push_back(rec);
+            if (ibest < 0 || us < best) {
+                best = us;
+                ibest = (int)S->tune.size() - 1;
+            }
+        }
+    TuneRec& b = S->tune[(size_t)ibest];
+    b.chosen = 1;
+    op.geom.zc = b.zchunk;
+    op.geom.pz = b.pz;
+    return NC_OK;
+}
+
 }  // namespace
 
 // Persistent tuner choices.  When the environment variable NC_TUNE_CACHE
@@ -741,6 +781,14 @@ nc_status setup_step_kernels(nc_solver S, cudaStream_t st) {
         op->tune.vcap = vcap;
         op->tune.vcap2 = vcap2;
         op->tune.npoff = npoff;
+    }
+    if (S->opP.kind == OP_STENCIL &&
+        (mode == NC_STEP_TUNE || (mode == NC_STEP_AUTO && S->n >= kStencilTuneMinPoints))) {
+        const size_t vb = S->mixed ? sizeof(float) : sizeof(double);
+        for (int i = 0; i < 3; ++i) NC_CU(cudaMemsetAsync(S->buf[i], 0, vb * (size_t)S->n, st));
+        NC_CU(cudaMemsetAsync(S->r, 0, sizeof(double) * (size_t)S->n, st));
+        if (S->mixed) NC_CU(cudaMemsetAsync(S->r32, 0, sizeof(float) * (size_t)S->n, st));
+        return tune_stencil(S, S->opP, st);
     }
     const bool tune = psell && (mode == NC_STEP_TUNE || (mode == NC_STEP_AUTO && S->n >= kTuneMinRows));
     if (!tune) return NC_OK;

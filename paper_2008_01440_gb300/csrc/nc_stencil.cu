@@ -56,9 +56,12 @@ cudaError_t stencil_dispatch(const StencilGeom& g, const double* c4, const void*
     c.cb = (AT)cb;
     c.cc = (AT)cc;
     c.terms = (cb != 0.0 ? kTermW : 0) | (cc != 0.0 ? kTermR : 0);
-    const dim3 grid = stencil_grid(g);
+    // plain steps take the tuned chunking; dot-product steps the policy's
+    StencilGeom gg = g;
+    if (dot != 0) gg.zc = gg.pz = 0;
+    const dim3 grid = stencil_grid(gg);
     const dim3 block(kTX, kTY);
-    const int zc = stencil_zchunk(g);
+    const int zc = stencil_zchunk(gg);
     const XT* uu = static_cast<const XT*>(u);
     const XT* ww = static_cast<const XT*>(w);
     const XT* rr = static_cast<const XT*>(r);
@@ -77,8 +80,8 @@ cudaError_t stencil_dispatch(const StencilGeom& g, const double* c4, const void*
             return cudaGetLastError();
         }
     } else {
-        // float: 4-plane batches for long z-chunks
-        if (zc >= kDeepChunk) {
+        // float: 4-plane batches for long z-chunks (or as tuned)
+        if (gg.pz == 4 || (gg.pz == 0 && zc >= kDeepChunk)) {
             switch (dot) {
             case 0: stencil7_step_kernel<XT, YT, 0, false, 4><<<grid, block, 0, st>>>(NC_ST_ARGS); break;
             case 1: stencil7_step_kernel<XT, YT, 1, false, 4><<<grid, block, 0, st>>>(NC_ST_ARGS); break;
@@ -107,6 +110,11 @@ cudaError_t stencil_dispatch(const StencilGeom& g, const double* c4, const void*
 // give two waves (small and mid-size systems, up to about 255^3), about two
 // waves with chunks of at least 4 planes, so that the GPU is filled.
 int stencil_zchunk(const StencilGeom& g) {
+    if (g.zc > 0) return g.zc < g.nz ? g.zc : (g.nz > 0 ? g.nz : 1);
+    return stencil_zchunk_policy(g);
+}
+
+int stencil_zchunk_policy(const StencilGeom& g) {
     const long long tiles = (long long)((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY);
     const long long wave = (long long)vec_grid_max();
     const long long c8 = (8 * wave + tiles - 1) / tiles;

@@ -138,3 +138,37 @@ def test_stencil_lanczos_and_gershgorin(env):
     lo_o, hi_o, _ = O.lanczos_bounds(mv, v0, 20, gershgorin=g)
     assert abs(lo - lo_o) <= 1e-9 * lo_o and abs(hi - hi_o) <= 1e-9 * hi_o
     assert hi >= hi_ex and lo >= lo_ex
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_stencil_tuned_chunking_is_bit_identical(env, dt):
+    """The tuner picks the z-chunk (and, in float, the planes per batch) of
+    the plain steps by measurement; every candidate computes each point by the
+    same operations, so P_k(A)v is bit-identical to the size policy's, and
+    matches the oracle."""
+    torch, nc = env
+    st = _stencil((100, 90, 120), 5)   # 1,080,000 points: AUTO tunes it too
+    M = nc.nc_matrix_stencil7(st.nx, st.ny, st.nz, st.c0, st.cx, st.cy, st.cz)
+    Ms = nc.nc_matrix_jacobi(M)
+    sc = W.Stencil7(st.nx, st.ny, st.nz, 1.0, st.cx / st.c0, st.cy / st.c0, st.cz / st.c0)
+    lo, hi = W.stencil7_bounds(sc)
+    vd = to_dev(torch, W.uniform_vector(st.n, seed=8))
+    out = {}
+    for mode in ("direct", "tune", "auto"):
+        S = nc.pcg_setup(Ms, lo, hi, 9, 1.001, apply_dtype=dt, step_kernel=mode)
+        z = torch.empty(st.n, dtype=torch.float64, device="cuda")
+        nc.pcg_apply_poly(S, vd, z)
+        info = nc.pcg_get_info(S)
+        out[mode] = (info, nc.pcg_tune_candidates(S), z.cpu().numpy())
+    info_d, cands_d, zd = out["direct"]
+    info_t, cands_t, zt = out["tune"]
+    assert not cands_d and info_d["stencil_zchunk"] > 0
+    assert len(cands_t) >= 3 and sum(c["chosen"] for c in cands_t) == 1
+    chosen = [c for c in cands_t if c["chosen"]][0]
+    assert chosen["us"] == min(c["us"] for c in cands_t)
+    assert info_t["stencil_zchunk"] == chosen["zchunk"] and chosen["zchunk"] >= 4
+    assert np.array_equal(zt, zd) and np.array_equal(out["auto"][2], zd)
+    mv = O.stencil7_matvec(st.nx, st.ny, st.nz, 1.0, sc.cx, sc.cy, sc.cz)
+    ref = O.cheb_apply(mv, vd.cpu().numpy(), O.cheb_params(lo, hi, 1.001), 9)
+    tol = 1e-12 if dt == "f64" else 1e-5
+    assert rel_err(zd, ref) <= tol and elem_err(zd, ref) <= tol
