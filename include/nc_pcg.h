@@ -443,19 +443,32 @@ NC_API nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, do
  * right-hand side b_dev (n float64 on the device, the original system's).
  * The slot runs that solver's polynomial -- its degree (1..kmax), bounds,
  * theta scale, stored operator and step coefficients -- inside the engine's
- * persistent work lists: its 256-row tiles join the other slots' tiles in
- * every step kernel, its vectors come from the pools, x0 = 0.  The solver's
- * apply precision must be the engine's (float32 or bfloat16 values with a
+ * persistent work lists: its tiles (8192 rows of the layout each) join the
+ * other slots' tiles in every step kernel, its vectors come from the pools,
+ * x0 = 0.  The solver's apply precision must be the engine's (float32 or bfloat16 values with a
  * float32 engine, float64 with NC_BATCH_F64_APPLY): NC_ERR_UNSUPPORTED
  * otherwise.  The solver (and its matrix) must stay alive until the slot is
  * released.  Not in the paper: many explicit systems in one launch. */
 NC_API nc_status pcg_batch_add_solver(nc_batch B, nc_solver S, const double* b_dev, void* stream, int* slot);
+/* Admit m (1..8) right-hand sides of one such solver as a group: column c
+ * (n float64 at B_dev + c * ldb, ldb >= n when m > 1) becomes slot slots[c]
+ * (host array of m ints), each with its own state, result, collect and
+ * release like any slot, but the group's step kernels load each row's
+ * columns and values once and apply them to all its columns (a sparse times
+ * dense-block product: the matrix is read once per step for the m
+ * right-hand sides).  A column's iterates are bit-for-bit those of the same
+ * right-hand side in a slot of its own.  The group's vectors take m * n
+ * contiguous pooled unknowns; NC_ERR_ADMISSION when m slots or that range
+ * are not free.  m = 1 is pcg_batch_add_solver. */
+NC_API nc_status pcg_batch_add_solver_multi(nc_batch B, nc_solver S, int m, const double* B_dev, int64_t ldb,
+                                            void* stream, int* slots);
 
 /* Solve nsys systems at once, system i (solver S[i], as in
  * pcg_batch_add_solver) with nrhs[i] right-hand sides B_dev[i] (n_i x nrhs[i]
  * float64 on the device, column-major) into X_dev[i] (same shape; x0 = 0):
- * every (system, right-hand side) pair is a slot of one engine and all of
- * them advance together in one graph launch.  res: host array of
+ * every (system, right-hand side) pair is a slot of one engine, a system's
+ * right-hand sides in groups of up to 8 (pcg_batch_add_solver_multi), and
+ * all of them advance together in one graph launch.  res: host array of
  * sum(nrhs) results, system by system.  All solvers share one apply
  * precision (NC_ERR_UNSUPPORTED otherwise).  Returns NC_OK when every slot
  * converged, else the first non-OK status.  Allocates the engine's pools for

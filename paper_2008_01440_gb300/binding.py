@@ -120,6 +120,8 @@ _SIGS = {
     "pcg_batch_add": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dbl, _dbl, _dbl, _dbl, _dbl,
                                      _dbl, ctypes.c_int, _dbl, _vp, _vp, ctypes.POINTER(ctypes.c_int)]),
     "pcg_batch_add_solver": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int)]),
+    "pcg_batch_add_solver_multi": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int64, _vp,
+                                                  ctypes.POINTER(ctypes.c_int)]),
     "pcg_solve_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(_vp), ctypes.POINTER(_vp), _dbl, ctypes.c_int, _vp,
                                          ctypes.POINTER(nc_result)]),
@@ -506,6 +508,24 @@ def pcg_batch_add_solver(B: Batch, S: Solver, b, stream=None):
         return None
     _check(st, "pcg_batch_add_solver")
     return slot.value
+
+
+def pcg_batch_add_solver_multi(B: Batch, S: Solver, Bm, stream=None):
+    """Admit the m <= 8 right-hand sides Bm (contiguous CUDA float64, shape
+    (m, n)) of one explicit-matrix solver as a group whose step kernels read
+    the matrix once for all m; returns the m slot ids, or None when the
+    engine has no room (NC_ERR_ADMISSION)."""
+    import torch
+    if Bm.dim() != 2 or Bm.shape[1] != S.n:
+        raise ValueError(f"Bm: expected shape (m, {S.n})")
+    m = int(Bm.shape[0])
+    slots = (ctypes.c_int * max(m, 1))()
+    st = lib.pcg_batch_add_solver_multi(B.handle, S.handle, m, _ptr(Bm, torch.float64, m * S.n, "Bm"), S.n,
+                                        _stream(stream), slots)
+    if st == NC_ERR_ADMISSION:
+        return None
+    _check(st, "pcg_batch_add_solver_multi")
+    return [slots[c] for c in range(m)]
 
 
 def pcg_solve_batched(solvers, Bs, Xs, tol: float, maxit: int, stream=None) -> list:

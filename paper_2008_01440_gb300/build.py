@@ -46,6 +46,13 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def needs_build() -> bool:
+    """True when libncpcg.so is missing or older than a source or header."""
+    if not os.path.exists(LIB):
+        return True
+    return _stale(LIB, sources() + _deps())
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     """Build libncpcg.so if any source changed; return its path.
 

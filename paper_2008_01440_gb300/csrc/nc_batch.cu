@@ -46,10 +46,10 @@ namespace {
 
 constexpr int kVch = 8192;    // vector-chunk length
 constexpr int kZC = 32;       // planes per stencil tile (32 measured 4.5% faster than 16 or 64 on the 256-system batch)
-// rows per tile of an explicit-matrix slot: as many as a stencil tile's
-// points, so the per-tile reduction (fence + atomic) stays as rare; a CTA
-// walks them in blocks of 256 rows, one row per thread
-constexpr int kSellTileRows = kFT * kZC;
+// rows per tile of an explicit-matrix slot or group: 8 blocks of 256 rows
+// (one row per thread), so that a step over a few systems still has a tile
+// for every CTA, while the per-tile reduction (fence + atomic) stays rare
+constexpr int kSellTileRows = 8 * kFT;
 
 enum Phase : int { PH_FREE = 0, PH_INIT = 1, PH_RUN = 2, PH_FINISH = 3, PH_DONE = 4 };
 
@@ -103,7 +103,33 @@ struct BVch {
 struct BCtl {
     double tol2;
     int maxit, ntiles, nvch, active;
-    int iters_this_call, iter_limit, nstiles, pad1;   // nstiles: tiles of explicit-matrix slots
+    int iters_this_call, iter_limit, nstiles, gpstride;   // tiles of explicit-matrix slots; a group
+                                                          // column's partials: [c * gpstride + tile]
+    int gseg[4];   // the group tile list's segments of widths 2, 4, 8: [gseg[i], gseg[i + 1])
+};
+
+// A group: up to kMaxGroup slots (columns) of one solver that share every
+// read of its matrix -- each step loads a row's columns and values once and
+// applies them to all the group's columns (a sparse times dense-block
+// product), as one solver's multi-right-hand-side block does.  Each column is
+// a slot of its own (state, result, collect, release); the group only owns
+// the tile list entry.  The columns' vectors lie in one pool range, column
+// c's at column 0's plus c * ld64 (float64 pool) or c * ldP (apply pool).
+constexpr int kMaxGroup = 8;
+
+struct BGDesc {
+    int M, n, k, coef0;          // M: the kernel width (2, 4 or 8 >= columns)
+    int tile0, tile1, live, vdtP;   // live: bit c set while column c is owned
+    int slot[kMaxGroup];         // the engine slot of column c
+    double shift;
+    const int32_t *sptr, *scol;
+    SellPat pat;
+    const double* val64;
+    const void* valP;
+    double *b, *x, *r, *z, *p, *q;   // column 0
+    float *t0, *t1, *t2, *r32;
+    double *dt0, *dt1, *dt2;
+    int ld64, ldP;
 };
 
 __device__ void bfinalize(BState* st, BCtl* ctl, int kind, double s) {
@@ -365,6 +391,10 @@ __global__ void __launch_bounds__(256) bk_true(const BDesc* __restrict__ D, BSta
 // that the stencil kernels keep their register budgets; launched only while
 // the engine holds such slots
 
+// The dot terms of a tile's rows are summed with __dadd_rn (never fused
+// into an fma with the term's product), so that the single-slot kernels and
+// the group kernels round them alike whatever the compiler contracts.
+
 // Chebyshev step j of the explicit slots whose values inside P are VT
 // (double: the float64 apply; float or bfloat16: the float32 apply)
 template <typename VT, typename XT, typename YT, int DOT, bool UNIT>
@@ -401,8 +431,8 @@ __global__ void __launch_bounds__(256, 6) bk_sell_opq(const BDesc* __restrict__ 
         const int f1 = min(tl.f0 + kSellTileRows, n);
 #pragma unroll 1
         for (int f = tl.f0; f < f1; f += kFT)
-            dv += sell_block<double, double, double, 2, true>(f + tid, n, sptr, scol, pat, val, p, nullptr, nullptr, q,
-                                                               c, nullptr);
+            dv = __dadd_rn(dv, sell_block<double, double, double, 2, true>(f + tid, n, sptr, scol, pat, val, p,
+                                                                            nullptr, nullptr, q, c, nullptr));
         reduce_slot(dv, partials, t, tile0, ntl, st, ctl, BF_ALPHA);
     }
 }
@@ -468,10 +498,10 @@ __global__ void __launch_bounds__(256, std::is_same<VT, double>::value ? 6 : 4) 
                 double dv = 0.0;
 #pragma unroll 1
                 for (int f = tl.f0; f < f1; f += kFT)
-                    dv += unit ? sell_block<VT, XT, double, 1, F64>(f + tid, n, sptr, scol, pat, val, u, w, r, z, c,
-                                                                     r64)
-                               : sell_block<VT, XT, double, 1, false>(f + tid, n, sptr, scol, pat, val, u, w, r, z, c,
-                                                                       r64);
+                    dv = __dadd_rn(dv, unit ? sell_block<VT, XT, double, 1, F64>(f + tid, n, sptr, scol, pat, val, u,
+                                                                                  w, r, z, c, r64)
+                                            : sell_block<VT, XT, double, 1, false>(f + tid, n, sptr, scol, pat, val,
+                                                                                    u, w, r, z, c, r64));
                 reduce_slot(dv, partials, t, tile0, ntl, st, ctl, BF_RZ);
                 continue;
             }
@@ -510,9 +540,310 @@ __global__ void __launch_bounds__(256) bk_sell_true(const BDesc* __restrict__ D,
         const int f1 = min(tl.f0 + kSellTileRows, n);
 #pragma unroll 1
         for (int f = tl.f0; f < f1; f += kFT)
-            dv += sell_block<double, double, double, 3, false>(f + tid, n, sptr, scol, pat, val, x, nullptr, b, q, c,
-                                                                nullptr);
+            dv = __dadd_rn(dv, sell_block<double, double, double, 3, false>(f + tid, n, sptr, scol, pat, val, x,
+                                                                             nullptr, b, q, c, nullptr));
         reduce_slot(dv, partials, t, tile0, ntl, st, ctl, BF_TRUE);
+    }
+}
+
+// ---- groups: kernels over the group tile list, one instance per width M
+// (2, 4 or 8 columns), each over its own segment of the list (kSellTileRows
+// rows of one group per tile, all its columns)
+
+// One row of a group of width M: the row's columns (or offsets) and values
+// are loaded once per slot and applied to every column whose bit is set in
+// `mask` (the others are neither gathered nor written).  Per column the
+// products are summed in the single-slot kernels' order and the epilogue is
+// theirs (step_row_out), so a column's result is bit-identical to the same
+// right-hand side in a slot of its own.  Column q's vectors are column 0's
+// plus q times their stride (32-bit: groups are formed only where 7 strides
+// fit).
+template <typename VT, typename XT, typename YT, int DOT, bool PAT, bool UNIT, int M>
+__device__ __forceinline__ void sell_row_group(const int row, const int n, const int32_t* __restrict__ slice_ptr,
+                                               const int32_t* __restrict__ col, const SellPat& pat,
+                                               const VT* __restrict__ val, const XT* u, const int ldu,
+                                               const XT* w, const int ldw, const XT* r, const int ldr, YT* y,
+                                               const int ldy, const double* rdot, const int ldd,
+                                               const StepCoef<typename AccOf<XT>::type>& c, const unsigned mask,
+                                               double (&dv)[M]) {
+    using AT = typename AccOf<XT>::type;
+    // slots per load group: about 16 (float) or 8 (double) gathers in flight
+    constexpr int G = sizeof(AT) == 8 ? (M >= 8 ? 1 : 8 / M) : (M >= 8 ? 2 : 16 / M);
+    const int s = row >> 5;
+    const int beg = slice_ptr[s];
+    const int len = (slice_ptr[s + 1] - beg) >> 5;   // warp-uniform
+    const VT* vp = val + beg + (row & 31);
+    const int32_t* cp = nullptr;
+    const int32_t* op = nullptr;
+    if constexpr (PAT) op = pat.poff + __ldg(pat.pstart + s);
+    else cp = col + beg + (row & 31);
+    AT acc[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) acc[q] = AT(0);
+    for (int j0 = 0; j0 < len; j0 += G) {
+        int cj[G];
+        AT vj[G];
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+            cj[t] = row;
+            vj[t] = AT(0);
+            if (j0 + t < len) {
+                if constexpr (PAT) cj[t] = min(max(row + __ldg(op + t), 0), n - 1);
+                else cj[t] = ld_stream(cp + 32 * t);
+                vj[t] = (AT)ld_stream(vp + 32 * t);
+            }
+        }
+        AT xv[M][G];
+#pragma unroll
+        for (int q = 0; q < M; ++q)
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                xv[q][t] = (((mask >> q) & 1u) && j0 + t < len) ? (AT)__ldg(u + (q * ldu + cj[t])) : AT(0);
+#pragma unroll
+        for (int q = 0; q < M; ++q)
+#pragma unroll
+            for (int t = 0; t < G; ++t)
+                if (j0 + t < len) acc[q] = fma(vj[t], xv[q][t], acc[q]);
+        vp += 32 * G;
+        if constexpr (PAT) op += G;
+        else cp += 32 * G;
+    }
+#pragma unroll
+    for (int q = 0; q < M; ++q)
+        if ((mask >> q) & 1u) {
+            const double t = step_row_out<XT, YT, DOT, AT, UNIT>(row, acc[q], c, u + q * ldu,
+                                                                 w ? w + q * ldw : nullptr, r ? r + q * ldr : nullptr,
+                                                                 y + q * ldy, rdot ? rdot + q * ldd : nullptr);
+            if (DOT != 0) dv[q] = __dadd_rn(dv[q], t);
+        }
+}
+
+// The tile's rows [f0, f1), one per thread per block of kFT rows.
+template <typename VT, typename XT, typename YT, int DOT, bool UNIT, int M>
+__device__ __forceinline__ void group_rows(const BGDesc* g, const int f0, const int f1, const VT* val, const XT* u,
+                                           const int ldu, const XT* w, const int ldw, const XT* r, const int ldr,
+                                           YT* y, const int ldy, const double* rdot,
+                                           const StepCoef<typename AccOf<XT>::type>& c, const unsigned mask,
+                                           double (&dv)[M]) {
+    const int n = g->n;
+    const int32_t *sptr = g->sptr, *scol = g->scol;
+    const SellPat pat = g->pat;
+    const int ldd = g->ld64;
+    if (pat.pstart != nullptr) {
+#pragma unroll 1
+        for (int f = f0; f < f1; f += kFT) {
+            const int row = f + (int)threadIdx.x;
+            if (row < n)
+                sell_row_group<VT, XT, YT, DOT, true, UNIT, M>(row, n, sptr, nullptr, pat, val, u, ldu, w, ldw, r,
+                                                               ldr, y, ldy, rdot, ldd, c, mask, dv);
+        }
+    } else {
+#pragma unroll 1
+        for (int f = f0; f < f1; f += kFT) {
+            const int row = f + (int)threadIdx.x;
+            if (row < n)
+                sell_row_group<VT, XT, YT, DOT, false, UNIT, M>(row, n, sptr, scol, pat, val, u, ldu, w, ldw, r,
+                                                                ldr, y, ldy, rdot, ldd, c, mask, dv);
+        }
+    }
+}
+
+// The columns of a group whose slot is in phase ph0 or ph1.  Uniform across
+// the CTA: a column's phase changes only when its last tile is reduced,
+// which cannot happen before this CTA has reduced the tile it reads for.
+template <int M>
+__device__ __forceinline__ unsigned group_mask(const BGDesc* g, const BState* S, int ph0, int ph1) {
+    unsigned m = 0;
+    const int live = g->live;
+#pragma unroll
+    for (int q = 0; q < M; ++q)
+        if ((live >> q) & 1) {
+            const int ph = S[g->slot[q]].phase;
+            if (ph == ph0 || ph == ph1) m |= 1u << q;
+        }
+    return m;
+}
+
+// Every selected column's partial of tile t into its own row of the group
+// partials (column q: [q * gpstride + tile]) and its slot's reduction, all
+// columns in one pass: each column's block sum takes block_sum's order and
+// the last tile's total reduce_slot's, so the sums are those of single slots.
+template <int M>
+__device__ void group_reduce(const double (&dv)[M], double* part, const int t, const BGDesc* g, BState* S,
+                             BCtl* ctl, const unsigned mask, const int kind) {
+    __shared__ double sh[M][256];
+    __shared__ int last[M];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < M; ++q) sh[q][tid] = dv[q];
+    __syncthreads();
+#pragma unroll
+    for (int s = 128; s >= 32; s >>= 1) {
+        if (tid < s) {
+#pragma unroll
+            for (int q = 0; q < M; ++q) sh[q][tid] += sh[q][tid + s];
+        }
+        __syncthreads();
+    }
+    if (tid < 32) {
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            double r = sh[q][tid];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+            if (tid == 0) sh[q][0] = r;
+        }
+    }
+    __syncthreads();
+    const int gps = ctl->gpstride, tile0 = g->tile0, ntl = g->tile1 - g->tile0;
+    if (tid < M) {
+        int is_last = 0;
+        if ((mask >> tid) & 1u) {
+            part[tid * gps + t] = sh[tid][0];
+            __threadfence();
+            const unsigned int c = atomicAdd(&S[g->slot[tid]].counter, 1u);
+            is_last = (c == (unsigned int)ntl - 1u);
+        }
+        last[tid] = is_last;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int q = 0; q < M; ++q) {
+        if (!last[q]) continue;   // uniform
+        __threadfence();
+        const int first = q * gps + tile0;
+        double s = 0.0;
+        for (int i = tid; i < ntl; i += 256) s += __ldcg(&part[first + i]);
+        s = block_sum<256>(s, &sh[0][0], tid);
+        if (tid == 0) {
+            BState* st = S + g->slot[q];
+            bfinalize(st, ctl, kind, s);
+            st->counter = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256, 3) bk_group_opq(const BGDesc* __restrict__ G, BState* S,
+                                                       const BTile* __restrict__ T, BCtl* ctl, double* part) {
+    const int t0 = ctl->gseg[M == 2 ? 0 : (M == 4 ? 1 : 2)], t1 = ctl->gseg[M == 2 ? 1 : (M == 4 ? 2 : 3)];
+    for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
+        const BTile tl = T[t];
+        const BGDesc* g = G + tl.pair;
+        const unsigned mask = group_mask<M>(g, S, PH_RUN, PH_RUN);
+        if (mask == 0u) continue;
+        StepCoef<double> c;   // q = A' p + shift p, (p, q)
+        c.ca = g->shift; c.cb = 0.0; c.cc = 0.0; c.cd = 1.0;
+        c.terms = (c.ca != 0.0 ? kTermU : 0) | kUnitD;
+        const int ld = g->ld64;
+        double dv[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) dv[q] = 0.0;
+        group_rows<double, double, double, 2, true, M>(g, tl.f0, min(tl.f0 + kSellTileRows, g->n), g->val64, g->p,
+                                                       ld, nullptr, 0, nullptr, 0, g->q, ld, nullptr, c, mask, dv);
+        group_reduce<M>(dv, part, t, g, S, ctl, mask, BF_ALPHA);
+    }
+}
+
+// PART 1: only the groups whose last step is j (z = P r in float64 and
+// (r, z)), 2: only the others (no dot product: the most frequent kernel
+// keeps more CTAs per SM)
+template <typename VT, int PART, int M>
+constexpr int group_min_ctas() {
+    return PART != 2 ? 3 : (std::is_same<VT, double>::value ? (M >= 8 ? 4 : 5) : (M >= 8 ? 5 : 6));
+}
+
+template <typename VT, int PART, int M>
+__global__ void __launch_bounds__(256, group_min_ctas<VT, PART, M>()) bk_group_cheb(const BGDesc* __restrict__ G, BState* S,
+                                                                        const BTile* __restrict__ T,
+                                                                        const BCoef* __restrict__ C, BCtl* ctl,
+                                                                        double* part, int j,
+                                                                        const int* __restrict__ ntile_step) {
+    constexpr bool F64 = std::is_same<VT, double>::value;
+    using XT = typename std::conditional<F64, double, float>::type;
+    constexpr int seg = M == 2 ? 0 : (M == 4 ? 1 : 2);
+    const int t0 = ctl->gseg[seg];
+    const int t1 = t0 + ntile_step[j];   // the segment's tiles of groups with k >= j (by degree)
+    for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
+        const BTile tl = T[t];
+        const BGDesc* g = G + tl.pair;
+        const int k = g->k;
+        if (j > k) continue;
+        if ((PART == 1 && j != k) || (PART == 2 && j == k)) continue;
+        if (!F64 && (g->vdtP == NC_BF16) != std::is_same<VT, __nv_bfloat16>::value) continue;
+        const unsigned mask = group_mask<M>(g, S, PH_RUN, PH_INIT);
+        if (mask == 0u) continue;
+        const BCoef bc = C[g->coef0 + j - 1];
+        const VT* val = F64 ? reinterpret_cast<const VT*>(g->val64) : static_cast<const VT*>(g->valP);
+        const int ldP = g->ldP, ld64 = g->ld64;
+        XT *v0, *v1, *v2;
+        const XT* r;
+        int ldr;
+        if constexpr (F64) {
+            v0 = g->dt0; v1 = g->dt1; v2 = g->dt2;
+            r = g->r;
+            ldr = ld64;
+        } else {
+            v0 = g->t0; v1 = g->t1; v2 = g->t2;
+            r = g->r32;
+            ldr = ldP;
+        }
+        auto tb = [&](int i) -> XT* { return i == 0 ? v0 : (i == 1 ? v1 : v2); };
+        StepCoef<XT> c;
+        if constexpr (F64) {
+            c.ca = bc.e0d; c.cb = bc.cbd; c.cc = bc.ccd; c.cd = bc.exd;
+        } else {
+            c.ca = bc.e0; c.cb = bc.cb; c.cc = bc.cc; c.cd = bc.ex;
+        }
+        c.terms = bc.terms;
+        const XT* u = (j == 1) ? r : tb((j - 1) % 3);
+        const int ldu = (j == 1) ? ldr : ldP;
+        const XT* w = (j >= 3) ? tb((j - 2) % 3) : nullptr;
+        const int f1 = min(tl.f0 + kSellTileRows, g->n);
+        const bool unit = F64 && bc.xu;
+        double dv[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) dv[q] = 0.0;
+        if constexpr (PART == 1) {
+            if (unit)
+                group_rows<VT, XT, double, 1, F64, M>(g, tl.f0, f1, val, u, ldu, w, ldP, r, ldr, g->z, ld64, g->r, c,
+                                                      mask, dv);
+            else
+                group_rows<VT, XT, double, 1, false, M>(g, tl.f0, f1, val, u, ldu, w, ldP, r, ldr, g->z, ld64, g->r,
+                                                        c, mask, dv);
+            group_reduce<M>(dv, part, t, g, S, ctl, mask, BF_RZ);
+        } else {
+            XT* y = tb(j % 3);
+            if (unit)
+                group_rows<VT, XT, XT, 0, F64, M>(g, tl.f0, f1, val, u, ldu, w, ldP, r, ldr, y, ldP, nullptr, c, mask,
+                                                  dv);
+            else
+                group_rows<VT, XT, XT, 0, false, M>(g, tl.f0, f1, val, u, ldu, w, ldP, r, ldr, y, ldP, nullptr, c,
+                                                    mask, dv);
+        }
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256, 3) bk_group_true(const BGDesc* __restrict__ G, BState* S,
+                                                        const BTile* __restrict__ T, BCtl* ctl, double* part) {
+    const int t0 = ctl->gseg[M == 2 ? 0 : (M == 4 ? 1 : 2)], t1 = ctl->gseg[M == 2 ? 1 : (M == 4 ? 2 : 3)];
+    for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
+        const BTile tl = T[t];
+        const BGDesc* g = G + tl.pair;
+        const unsigned mask = group_mask<M>(g, S, PH_FINISH, PH_FINISH);
+        if (mask == 0u) continue;
+        StepCoef<double> c;   // q = b - (A' x + shift x), ||q||^2
+        c.ca = -g->shift; c.cb = 0.0; c.cc = 1.0; c.cd = -1.0;
+        c.terms = (c.ca != 0.0 ? kTermU : 0) | kTermR;
+        const int ld = g->ld64;
+        double dv[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) dv[q] = 0.0;
+        group_rows<double, double, double, 3, false, M>(g, tl.f0, min(tl.f0 + kSellTileRows, g->n), g->val64, g->x,
+                                                        ld, nullptr, 0, g->b, ld, g->q, ld, nullptr, c, mask, dv);
+        group_reduce<M>(dv, part, t, g, S, ctl, mask, BF_TRUE);
     }
 }
 
@@ -555,8 +886,15 @@ struct nc_batch_s {
     BTile* d_stiles = nullptr;    // tiles of explicit-matrix slots
     int* d_sntile_step = nullptr; // and their counts with k >= j
     int cap_stiles = 0;
+    BGDesc* d_gdesc = nullptr;    // groups
+    BTile* d_gtiles = nullptr;    // tiles of groups
+    int* d_gntile_step = nullptr; // and their counts with k >= j
+    double* d_gpartials = nullptr;   // kMaxGroup rows of cap_gtiles
+    int cap_gdesc = 0, cap_gtiles = 0;
+    int gwidths = 0;              // group widths the captured iteration launches (bits 2, 4, 8)
     int graph_sell = 0;           // explicit-slot kernels the captured iteration launches:
-                                  // bit 0 float32 / float64 values, bit 1 bfloat16 values
+                                  // bit 0 float32 / float64 values, bit 1 bfloat16 values;
+                                  // bits 2 and 3 the same for groups
     double* d_partials = nullptr;
     double* pool64 = nullptr;
     float* pool32 = nullptr;
@@ -568,6 +906,9 @@ struct nc_batch_s {
     std::vector<double> dis;      // d^{-1/2} constant per slot
     std::vector<std::vector<BCoef>> coefs;
     std::vector<int64_t> off;     // pool offset (unknowns) per slot
+    std::vector<int> gid;         // group of a slot (-1: none)
+    std::vector<BGDesc> groups;   // host copies; live == 0: free
+    std::vector<std::vector<BCoef>> gcoefs;
     std::map<int64_t, int64_t> free_list;   // offset -> length
     bool dirty = true;
     BState* h_state = nullptr;    // pinned
@@ -668,9 +1009,19 @@ void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, c
     const dim3 tb(kTX, kTY);
     const int grid = vec_grid_max();   // persistent CTAs over the work lists (stencil and vector kernels)
     bk_opq<<<grid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
-    if (B->graph_sell)
+    if (B->graph_sell & 3)
         bk_sell_opq<<<resident_grid(bk_sell_opq, 256), 256, 0, st>>>(B->d_desc, B->d_state, B->d_stiles, B->d_ctl,
                                                                      B->d_partials);
+    if (B->graph_sell & 12) {
+#define NB_GROUP_OPQ(M) \
+    if (B->gwidths & (M)) \
+        bk_group_opq<M><<<resident_grid(bk_group_opq<M>, 256), 256, 0, st>>>(B->d_gdesc, B->d_state, B->d_gtiles, \
+                                                                             B->d_ctl, B->d_gpartials)
+        NB_GROUP_OPQ(2);
+        NB_GROUP_OPQ(4);
+        NB_GROUP_OPQ(8);
+#undef NB_GROUP_OPQ
+    }
     bk_axpy<<<grid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
     for (int j = 1; j <= B->kmax; ++j) {
         if (B->flags & NC_BATCH_F64_APPLY)
@@ -679,7 +1030,7 @@ void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, c
         else
             bk_cheb<false><<<grid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_coef, B->d_ctl,
                                                       B->d_partials, j, B->d_ntile_step);
-        if (B->graph_sell) {
+        if (B->graph_sell & 3) {
 #define NB_SELL_ARGS B->d_desc, B->d_state, B->d_stiles, B->d_coef, B->d_ctl, B->d_partials, j, B->d_sntile_step
 #define NB_SELL_CHEB(VT, P) bk_sell_cheb<VT, P><<<resident_grid(bk_sell_cheb<VT, P>, 256), 256, 0, st>>>(NB_SELL_ARGS)
             if (B->flags & NC_BATCH_F64_APPLY) {
@@ -697,12 +1048,46 @@ void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, c
 #undef NB_SELL_CHEB
 #undef NB_SELL_ARGS
         }
+        if (B->graph_sell & 12) {
+            // one launch per (value type, part, width) present
+#define NB_GROUP_CHEB1(VT, P, M, SEG)                                                                           \
+    if (B->gwidths & (M))                                                                                       \
+    bk_group_cheb<VT, P, M><<<resident_grid(bk_group_cheb<VT, P, M>, 256), 256, 0, st>>>(                       \
+        B->d_gdesc, B->d_state, B->d_gtiles, B->d_coef, B->d_ctl, B->d_gpartials, j,                            \
+        B->d_gntile_step + (SEG) * (B->kmax + 1))
+#define NB_GROUP_CHEB(VT, P) NB_GROUP_CHEB1(VT, P, 2, 0); NB_GROUP_CHEB1(VT, P, 4, 1); NB_GROUP_CHEB1(VT, P, 8, 2)
+            if (B->flags & NC_BATCH_F64_APPLY) {
+                NB_GROUP_CHEB(double, 1);
+                NB_GROUP_CHEB(double, 2);
+            } else {
+                if (B->graph_sell & 4) {
+                    NB_GROUP_CHEB(float, 1);
+                    NB_GROUP_CHEB(float, 2);
+                }
+                if (B->graph_sell & 8) {
+                    NB_GROUP_CHEB(__nv_bfloat16, 1);
+                    NB_GROUP_CHEB(__nv_bfloat16, 2);
+                }
+            }
+#undef NB_GROUP_CHEB
+#undef NB_GROUP_CHEB1
+        }
     }
     bk_pupd<<<grid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
     bk_true<<<grid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
-    if (B->graph_sell)
+    if (B->graph_sell & 3)
         bk_sell_true<<<resident_grid(bk_sell_true, 256), 256, 0, st>>>(B->d_desc, B->d_state, B->d_stiles,
                                                                        B->d_ctl, B->d_partials);
+    if (B->graph_sell & 12) {
+#define NB_GROUP_TRUE(M) \
+    if (B->gwidths & (M)) \
+        bk_group_true<M><<<resident_grid(bk_group_true<M>, 256), 256, 0, st>>>(B->d_gdesc, B->d_state, B->d_gtiles, \
+                                                                               B->d_ctl, B->d_gpartials)
+        NB_GROUP_TRUE(2);
+        NB_GROUP_TRUE(4);
+        NB_GROUP_TRUE(8);
+#undef NB_GROUP_TRUE
+    }
     bk_cond<<<1, 1, 0, st>>>(B->d_ctl, h, use_cond);
 }
 
@@ -756,7 +1141,9 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
     std::vector<int> nstep(B->kmax + 1, 0), snstep(B->kmax + 1, 0);
     for (int s : order) {
         BDesc& d = B->desc[s];
-        if (d.kind == SLOT_SELL) {   // kSellTileRows-row tiles of the layout, in their own list
+        if (d.kind == SLOT_SELL && B->gid[s] >= 0) {   // a group column: the group's tiles
+            d.tile0 = d.tile1 = 0;
+        } else if (d.kind == SLOT_SELL) {   // kSellTileRows-row tiles of the layout, in their own list
             d.tile0 = (int)stiles.size();
             for (int f0 = 0; f0 < d.n; f0 += kSellTileRows) stiles.push_back(BTile{s, f0, 0, 0});
             d.tile1 = (int)stiles.size();
@@ -775,7 +1162,34 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
         d.coef0 = (int)coef.size();
         coef.insert(coef.end(), B->coefs[s].begin(), B->coefs[s].end());
     }
+    // groups: one segment of the list per width, each by degree as well
+    std::vector<BTile> gtiles;
+    std::vector<int> gorder, gnstep(3 * (B->kmax + 1), 0);
+    for (int g = 0; g < (int)B->groups.size(); ++g)
+        if (B->groups[g].live) gorder.push_back(g);
+    std::stable_sort(gorder.begin(), gorder.end(), [&](int a, int b) {
+        const BGDesc &x = B->groups[a], &y = B->groups[b];
+        return x.M != y.M ? x.M < y.M : x.k > y.k;
+    });
+    int want_sell = 0, want_w = 0;
+    int gseg[4] = {0, 0, 0, 0};
+    for (int g : gorder) {
+        BGDesc& gd = B->groups[g];
+        const int seg = gd.M == 2 ? 0 : (gd.M == 4 ? 1 : 2);
+        const int s0 = (int)gtiles.size();
+        for (int i = seg + 1; i < 4; ++i) gseg[i] = s0;   // segments after this one start at the end so far
+        gd.tile0 = s0;
+        for (int f0 = 0; f0 < gd.n; f0 += kSellTileRows) gtiles.push_back(BTile{g, f0, 0, 0});
+        gd.tile1 = (int)gtiles.size();
+        for (int i = seg + 1; i < 4; ++i) gseg[i] = gd.tile1;
+        for (int j = 0; j <= std::min(gd.k, B->kmax); ++j) gnstep[seg * (B->kmax + 1) + j] = gd.tile1 - gseg[seg];
+        gd.coef0 = (int)coef.size();
+        coef.insert(coef.end(), B->gcoefs[g].begin(), B->gcoefs[g].end());
+        want_sell |= gd.vdtP == NC_BF16 ? 8 : 4;
+        want_w |= gd.M;
+    }
     const int cap_t = B->cap_tiles, cap_v = B->cap_vch, cap_s = B->cap_stiles;
+    const int cap_gd = B->cap_gdesc, cap_gt = B->cap_gtiles;
     nc_status s;
     if ((s = grow(reinterpret_cast<void**>(&B->d_tiles), &B->cap_tiles, (int)tiles.size(), sizeof(BTile)))) return s;
     if ((s = grow(reinterpret_cast<void**>(&B->d_stiles), &B->cap_stiles, (int)stiles.size(), sizeof(BTile))))
@@ -783,16 +1197,26 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
     if ((s = grow(reinterpret_cast<void**>(&B->d_vch), &B->cap_vch, (int)vch.size(), sizeof(BVch)))) return s;
     int cap_c = B->cap_coef;
     if ((s = grow(reinterpret_cast<void**>(&B->d_coef), &B->cap_coef, (int)coef.size(), sizeof(BCoef)))) return s;
-    int want_sell = 0;
+    if ((s = grow(reinterpret_cast<void**>(&B->d_gdesc), &B->cap_gdesc, (int)B->groups.size(), sizeof(BGDesc))))
+        return s;
+    if ((s = grow(reinterpret_cast<void**>(&B->d_gtiles), &B->cap_gtiles, (int)gtiles.size(), sizeof(BTile))))
+        return s;
     for (const BTile& tl : stiles) want_sell |= B->desc[tl.pair].vdtP == NC_BF16 ? 2 : 1;
     const bool realloc_ = cap_t != B->cap_tiles || cap_v != B->cap_vch || cap_c != B->cap_coef ||
-                          cap_s != B->cap_stiles || want_sell != B->graph_sell;
+                          cap_s != B->cap_stiles || cap_gd != B->cap_gdesc || cap_gt != B->cap_gtiles ||
+                          want_sell != B->graph_sell || want_w != B->gwidths;
     if (realloc_) {
         if (B->d_partials) cudaFree(B->d_partials);
+        if (B->d_gpartials) cudaFree(B->d_gpartials);
         B->d_partials = nullptr;
+        B->d_gpartials = nullptr;
         B->graph_sell = want_sell;
+        B->gwidths = want_w;
         const int np = std::max(std::max(B->cap_tiles, B->cap_vch), B->cap_stiles);
         if ((s = balloc(reinterpret_cast<void**>(&B->d_partials), sizeof(double) * (size_t)np))) return s;
+        if ((s = balloc(reinterpret_cast<void**>(&B->d_gpartials),
+                        sizeof(double) * kMaxGroup * (size_t)B->cap_gtiles)))
+            return s;
         if ((s = build_batch_graph(B))) return s;
     }
     if (!tiles.empty())
@@ -805,6 +1229,12 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
     if (!stiles.empty())
         NB_CU(cudaMemcpyAsync(B->d_stiles, stiles.data(), sizeof(BTile) * stiles.size(), cudaMemcpyHostToDevice, st));
     NB_CU(cudaMemcpyAsync(B->d_sntile_step, snstep.data(), sizeof(int) * snstep.size(), cudaMemcpyHostToDevice, st));
+    if (!gtiles.empty())
+        NB_CU(cudaMemcpyAsync(B->d_gtiles, gtiles.data(), sizeof(BTile) * gtiles.size(), cudaMemcpyHostToDevice, st));
+    if (!B->groups.empty())
+        NB_CU(cudaMemcpyAsync(B->d_gdesc, B->groups.data(), sizeof(BGDesc) * B->groups.size(),
+                              cudaMemcpyHostToDevice, st));
+    NB_CU(cudaMemcpyAsync(B->d_gntile_step, gnstep.data(), sizeof(int) * gnstep.size(), cudaMemcpyHostToDevice, st));
     // states of slots admitted or released since the last run (pinned source)
     for (int slot : B->state_upload)
         NB_CU(cudaMemcpyAsync(B->d_state + slot, &B->h_state[slot], sizeof(BState), cudaMemcpyHostToDevice, st));
@@ -812,6 +1242,8 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
     NB_CU(cudaMemcpyAsync(B->d_desc, B->desc.data(), sizeof(BDesc) * B->cap_slots, cudaMemcpyHostToDevice, st));
     B->h_ctl->ntiles = (int)tiles.size();
     B->h_ctl->nstiles = (int)stiles.size();
+    for (int i = 0; i < 4; ++i) B->h_ctl->gseg[i] = gseg[i];
+    B->h_ctl->gpstride = B->cap_gtiles;
     B->h_ctl->nvch = (int)vch.size();
     // the host vectors must outlive the copies
     NB_CU(cudaStreamSynchronize(st));
@@ -843,6 +1275,7 @@ nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, int fl
     B->dis.assign(max_slots, 1.0);
     B->coefs.assign(max_slots, {});
     B->off.assign(max_slots, -1);
+    B->gid.assign(max_slots, -1);
     B->free_list[0] = max_unknowns;
     nc_status s = NC_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -852,6 +1285,7 @@ nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, int fl
         if ((s = balloc(reinterpret_cast<void**>(&B->d_ctl), sizeof(BCtl)))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->d_ntile_step), sizeof(int) * (kmax + 1)))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->d_sntile_step), sizeof(int) * (kmax + 1)))) break;
+        if ((s = balloc(reinterpret_cast<void**>(&B->d_gntile_step), sizeof(int) * 3 * (kmax + 1)))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->pool64), sizeof(double) * 6 * (size_t)max_unknowns))) break;
         // apply vectors: 4 float32 per unknown (t0..t2, r32), or 3 float64 (+ slack
         // for the 16-byte rounding of the split below)
@@ -982,8 +1416,14 @@ nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, double cx
 }
 
 nc_status pcg_batch_add_solver(nc_batch B, nc_solver S, const double* b_dev, void* stream, int* slot) {
-    if (!B || !S || !slot || !b_dev) return NC_ERR_ARG;
-    *slot = -1;
+    if (!slot) return NC_ERR_ARG;
+    return pcg_batch_add_solver_multi(B, S, 1, b_dev, 0, stream, slot);
+}
+
+nc_status pcg_batch_add_solver_multi(nc_batch B, nc_solver S, int m, const double* B_dev, int64_t ldb,
+                                     void* stream, int* slots) {
+    if (!B || !S || !slots || !B_dev || m < 1 || m > kMaxGroup) return NC_ERR_ARG;
+    for (int c = 0; c < m; ++c) slots[c] = -1;
     const bool f64 = (B->flags & NC_BATCH_F64_APPLY) != 0;
     // an explicit matrix in a sliced layout, the Chebyshev form, no residual
     // replacement, scalar (Jacobi) scaling only; the apply precision must be
@@ -993,34 +1433,18 @@ nc_status pcg_batch_add_solver(nc_batch B, nc_solver S, const double* b_dev, voi
         return NC_ERR_UNSUPPORTED;
     if (S->k < 1 || S->k > B->kmax || S->n < 1) return NC_ERR_ARG;
     const int64_t n = S->n;
-    int s = -1;
-    for (int i = 0; i < B->cap_slots; ++i)
-        if (!B->used[i]) { s = i; break; }
-    if (s < 0) return NC_ERR_ADMISSION;
-    const int64_t o = pool_alloc(B, n);
+    if (m > 1 && ldb < n) return NC_ERR_ARG;
+    // the group kernels index column q by q times a 32-bit stride (6 n at
+    // most): larger systems are admitted as m separate slots, which give
+    // the same results (bit for bit)
+    const bool grouped = m > 1 && (int64_t)(kMaxGroup - 1) * 6 * n < ((int64_t)1 << 31);
+    std::vector<int> ids;
+    for (int i = 0; i < B->cap_slots && (int)ids.size() < m; ++i)
+        if (!B->used[i]) ids.push_back(i);
+    if ((int)ids.size() < m) return NC_ERR_ADMISSION;
+    const int64_t o = pool_alloc(B, m * n);   // the columns side by side
     if (o < 0) return NC_ERR_ADMISSION;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    BDesc d{};
-    d.kind = SLOT_SELL;
-    d.nx = (int)n; d.ny = 1; d.nz = 1; d.n = (int)n; d.k = S->k;
-    d.sptr = S->op64.ptr;
-    d.scol = S->op64.col;
-    d.pat = S->op64.pat;
-    d.val64 = static_cast<const double*>(S->op64.val);
-    d.valP = S->opP.val;
-    d.vdtP = S->opP.vdt;
-    d.shift = S->shift;
-    d.disv = S->A->scaled ? S->A->dis : nullptr;
-    double* base64 = B->pool64 + 6 * o;
-    d.b = base64; d.x = base64 + n; d.r = base64 + 2 * n; d.z = base64 + 3 * n; d.p = base64 + 4 * n;
-    d.q = base64 + 5 * n;
-    if (f64) {
-        double* baseP = reinterpret_cast<double*>(B->pool32) + 3 * o;
-        d.dt0 = baseP; d.dt1 = baseP + n; d.dt2 = baseP + 2 * n;
-    } else {
-        float* base32 = B->pool32 + 4 * o;
-        d.t0 = base32; d.t1 = base32 + n; d.t2 = base32 + 2 * n; d.r32 = base32 + 3 * n;
-    }
     // the solver's own step coefficients, as its solves take them (the
     // float64 iterates scaled so that the product's coefficient is 1)
     const std::vector<StepC> sc = step_coefs(S, true);
@@ -1040,27 +1464,83 @@ nc_status pcg_batch_add_solver(nc_batch B, nc_solver S, const double* b_dev, voi
         c.xu = sc[j].cd == 1.0 ? 1 : 0;
         cf[j - 1] = c;
     }
-    B->desc[s] = d;
-    B->used[s] = 1;
-    B->kdeg[s] = S->k;
-    B->dis[s] = 1.0;   // the scaling is the vector d.disv
-    B->coefs[s] = cf;
-    B->off[s] = o;
-    B->dirty = true;
+    int g = -1;
+    if (grouped) {
+        for (int i = 0; i < (int)B->groups.size(); ++i)
+            if (B->groups[i].live == 0) { g = i; break; }
+        if (g < 0) {
+            g = (int)B->groups.size();
+            B->groups.push_back(BGDesc{});
+            B->gcoefs.emplace_back();
+        }
+    }
     const int grid = (int)std::min<int64_t>(4096, (n + 255) / 256);
-    if (d.disv != nullptr)
-        bk_scale_vec<<<grid, 256, 0, st>>>((int)n, b_dev, d.disv, 1.0, d.b);
-    else
-        bk_scale<<<grid, 256, 0, st>>>((int)n, b_dev, 1.0, d.b);
-    NB_CU(cudaGetLastError());
-    BState init{};
-    init.phase = PH_INIT;
-    init.status = NC_ERR_MAXIT;
-    B->h_state[s] = init;
-    B->state_upload.push_back(s);
-    B->h_ctl->active += 1;
-    B->stat_launches += 1;
-    *slot = s;
+    for (int c = 0; c < m; ++c) {
+        const int s = ids[c];
+        const int64_t oc = o + c * n;
+        BDesc d{};
+        d.kind = SLOT_SELL;
+        d.nx = (int)n; d.ny = 1; d.nz = 1; d.n = (int)n; d.k = S->k;
+        d.sptr = S->op64.ptr;
+        d.scol = S->op64.col;
+        d.pat = S->op64.pat;
+        d.val64 = static_cast<const double*>(S->op64.val);
+        d.valP = S->opP.val;
+        d.vdtP = S->opP.vdt;
+        d.shift = S->shift;
+        d.disv = S->A->scaled ? S->A->dis : nullptr;
+        double* base64 = B->pool64 + 6 * oc;
+        d.b = base64; d.x = base64 + n; d.r = base64 + 2 * n; d.z = base64 + 3 * n; d.p = base64 + 4 * n;
+        d.q = base64 + 5 * n;
+        if (f64) {
+            double* baseP = reinterpret_cast<double*>(B->pool32) + 3 * oc;
+            d.dt0 = baseP; d.dt1 = baseP + n; d.dt2 = baseP + 2 * n;
+        } else {
+            float* base32 = B->pool32 + 4 * oc;
+            d.t0 = base32; d.t1 = base32 + n; d.t2 = base32 + 2 * n; d.r32 = base32 + 3 * n;
+        }
+        if (g >= 0 && c == 0) {   // the group: column 0's vectors, the matrix, the strides
+            BGDesc gd{};
+            gd.M = m <= 2 ? 2 : (m <= 4 ? 4 : kMaxGroup);
+            gd.n = (int)n;
+            gd.k = S->k;
+            gd.live = (1 << m) - 1;
+            gd.vdtP = d.vdtP;
+            for (int q = 0; q < kMaxGroup; ++q) gd.slot[q] = ids[q < m ? q : 0];
+            gd.shift = d.shift;
+            gd.sptr = d.sptr; gd.scol = d.scol; gd.pat = d.pat; gd.val64 = d.val64; gd.valP = d.valP;
+            gd.b = d.b; gd.x = d.x; gd.r = d.r; gd.z = d.z; gd.p = d.p; gd.q = d.q;
+            gd.t0 = d.t0; gd.t1 = d.t1; gd.t2 = d.t2; gd.r32 = d.r32;
+            gd.dt0 = d.dt0; gd.dt1 = d.dt1; gd.dt2 = d.dt2;
+            gd.ld64 = (int)(6 * n);
+            gd.ldP = (int)((f64 ? 3 : 4) * n);
+            B->groups[g] = gd;
+            B->gcoefs[g] = cf;
+        }
+        B->desc[s] = d;
+        B->used[s] = 1;
+        B->kdeg[s] = S->k;
+        B->dis[s] = 1.0;   // the scaling is the vector d.disv
+        B->gid[s] = g;
+        if (g < 0) B->coefs[s] = cf;
+        else B->coefs[s].clear();
+        B->off[s] = oc;
+        const double* bc = B_dev + (size_t)c * (size_t)ldb;
+        if (d.disv != nullptr)
+            bk_scale_vec<<<grid, 256, 0, st>>>((int)n, bc, d.disv, 1.0, d.b);
+        else
+            bk_scale<<<grid, 256, 0, st>>>((int)n, bc, 1.0, d.b);
+        NB_CU(cudaGetLastError());
+        BState init{};
+        init.phase = PH_INIT;
+        init.status = NC_ERR_MAXIT;
+        B->h_state[s] = init;
+        B->state_upload.push_back(s);
+        B->h_ctl->active += 1;
+        B->stat_launches += 1;
+        slots[c] = s;
+    }
+    B->dirty = true;
     return NC_OK;
 }
 
@@ -1083,11 +1563,13 @@ nc_status pcg_solve_batched(int nsys, const nc_solver* S, const int* nrhs, const
     if (st != NC_OK) return st;
     std::vector<int> ids;
     ids.reserve(slots);
+    // each system's right-hand sides in groups of up to kMaxGroup columns
     for (int i = 0; i < nsys && st == NC_OK; ++i)
-        for (int c = 0; c < nrhs[i] && st == NC_OK; ++c) {
-            int sl = -1;
-            st = pcg_batch_add_solver(B, S[i], B_dev[i] + (size_t)c * S[i]->n, stream, &sl);
-            ids.push_back(sl);
+        for (int c0 = 0; c0 < nrhs[i] && st == NC_OK; c0 += kMaxGroup) {
+            const int m = std::min(kMaxGroup, nrhs[i] - c0);
+            int sl[kMaxGroup];
+            st = pcg_batch_add_solver_multi(B, S[i], m, B_dev[i] + (size_t)c0 * S[i]->n, S[i]->n, stream, sl);
+            ids.insert(ids.end(), sl, sl + m);
         }
     int left = 0;
     if (st == NC_OK) st = pcg_batch_run(B, tol, maxit, 0, stream, &left);
@@ -1142,10 +1624,15 @@ nc_status pcg_batch_run(nc_batch B, double tol, int maxit, int iter_limit, void*
         NB_CU(cudaStreamSynchronize(st));
         // one iteration: opq, axpy, kmax Chebyshev steps, pupd, true, cond
         B->stat_iters += c->iters_this_call;
-        // explicit-slot Chebyshev kernels per step: 1 (float64), 2 per float value type
-        const int nsell = (B->flags & NC_BATCH_F64_APPLY) ? (B->graph_sell ? 1 : 0)
-                                                          : 2 * ((B->graph_sell & 1) + ((B->graph_sell >> 1) & 1));
-        B->stat_launches += (int64_t)c->iters_this_call * (B->kmax + 5 + (nsell ? nsell * B->kmax + 2 : 0));
+        // explicit-slot and group Chebyshev kernels per step: 1 (float64), 2
+        // per float value type; plus their opq and true kernels
+        const int gs = B->graph_sell;
+        const bool f64 = (B->flags & NC_BATCH_F64_APPLY) != 0;
+        const int nsell = f64 ? ((gs & 3) ? 1 : 0) : 2 * ((gs & 1) + ((gs >> 1) & 1));
+        const int nw = ((B->gwidths >> 1) & 1) + ((B->gwidths >> 2) & 1) + ((B->gwidths >> 3) & 1);
+        const int ngrp = nw * (f64 ? ((gs & 12) ? 2 : 0) : 2 * (((gs >> 2) & 1) + ((gs >> 3) & 1)));
+        B->stat_launches += (int64_t)c->iters_this_call *
+                            (B->kmax + 5 + (nsell ? nsell * B->kmax + 2 : 0) + (ngrp ? ngrp * B->kmax + 2 * nw : 0));
     }
     if (active_left) *active_left = B->h_ctl->active;
     return NC_OK;
@@ -1198,6 +1685,14 @@ nc_status pcg_batch_release(nc_batch B, int slot, void* stream) {
     // no synchronisation: collects already enqueued on the engine's stream
     // run before any later kernel that reuses this memory
     pool_free(B, B->off[slot], B->desc[slot].n);
+    const int g = B->gid[slot];
+    if (g >= 0) {   // the group no longer reads or writes this column; gone with its last
+        BGDesc& gd = B->groups[g];
+        for (int q = 0; q < kMaxGroup; ++q)
+            if (((gd.live >> q) & 1) && gd.slot[q] == slot) gd.live &= ~(1 << q);
+        if (gd.live == 0) B->gcoefs[g].clear();
+        B->gid[slot] = -1;
+    }
     B->used[slot] = 0;
     B->off[slot] = -1;
     B->desc[slot] = BDesc{};
@@ -1233,6 +1728,10 @@ nc_status pcg_batch_destroy(nc_batch B) {
     cudaFree(B->d_ntile_step);
     cudaFree(B->d_stiles);
     cudaFree(B->d_sntile_step);
+    cudaFree(B->d_gdesc);
+    cudaFree(B->d_gtiles);
+    cudaFree(B->d_gntile_step);
+    cudaFree(B->d_gpartials);
     cudaFree(B->d_partials);
     cudaFree(B->pool64);
     cudaFree(B->pool32);

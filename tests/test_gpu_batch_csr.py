@@ -1,14 +1,16 @@
 """Explicit matrices in the batched engine (pcg_batch_add_solver,
-pcg_solve_batched): every (system, right-hand side) pair of several CSR
-systems -- each with its own solver, layout, degree and bounds -- runs as a
-slot of one engine, in one graph launch per run.
+pcg_batch_add_solver_multi, pcg_solve_batched): every (system, right-hand
+side) pair of several CSR systems -- each with its own solver, layout,
+degree and bounds -- runs as a slot of one engine, in one graph launch per
+run; a system's right-hand sides may share its matrix reads as a group.
 
 Checked: each slot against the FP64 oracle's PCG on the same scaled system
 (iterations +-1 with the float64 apply, the solution within the tolerance's
 reach), against the solver's own pcg_solve, bit-for-bit identity of a
 slot's result alone and in a mix (every slot reduces its own dot products in
-a fixed order), explicit and stencil slots in one engine, and the
-combinations the engine refuses."""
+a fixed order), of a group's columns and single slots, a group column
+released mid-run with its range reused, explicit and stencil slots in one
+engine, and the combinations the engine refuses."""
 import numpy as np
 import pytest
 
@@ -161,3 +163,105 @@ def test_engine_refuses_what_it_cannot_run(env):
     assert e4.value.status == nc.NC_ERR_UNSUPPORTED
     assert nc.pcg_batch_add_solver(eng64, S64, b) is not None
     eng64.close()
+
+
+def _run_singles(torch, nc, S, B, f64):
+    """Every row of B as a slot of its own in a fresh engine; (X, results)."""
+    eng = nc.pcg_batch_create(B.shape[0], B.shape[0] * S.n, 32, f64_apply=f64)
+    slots = [nc.pcg_batch_add_solver(eng, S, B[c]) for c in range(B.shape[0])]
+    assert nc.pcg_batch_run(eng, 1e-8, 5000) == 0
+    X = torch.empty_like(B)
+    res = []
+    for c, sl in enumerate(slots):
+        res.append(nc.pcg_batch_status(eng, sl)[1])
+        nc.pcg_batch_collect(eng, sl, X[c])
+    torch.cuda.synchronize()
+    eng.close()
+    return X, res
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("m", [2, 3, 5, 8])
+def test_group_columns_are_bit_identical_to_single_slots(env, dt, m):
+    """A group of m right-hand sides (the matrix read once per step for all
+    of them, kernel width 2, 4 or 8 with the unused columns masked) gives
+    every column exactly the iterates of a slot of its own."""
+    torch, nc = env
+    A, scale, k, M, S, lo, hi = _setup(torch, nc, dt, [_systems()[m % 2 * 2]])[0]
+    B = to_dev(torch, np.stack([W.uniform_vector(A.n, seed=500 + c) for c in range(m)]))
+    eng = nc.pcg_batch_create(m, m * A.n, 32, f64_apply=(dt == "f64"))
+    slots = nc.pcg_batch_add_solver_multi(eng, S, B)
+    assert len(slots) == m
+    assert nc.pcg_batch_run(eng, 1e-8, 5000) == 0
+    X = torch.empty_like(B)
+    res = []
+    for c, sl in enumerate(slots):
+        res.append(nc.pcg_batch_status(eng, sl)[1])
+        nc.pcg_batch_collect(eng, sl, X[c])
+    torch.cuda.synchronize()
+    eng.close()
+    Xs, rs = _run_singles(torch, nc, S, B, dt == "f64")
+    for c in range(m):
+        assert res[c]["status"] == 0 and res[c]["iters"] == rs[c]["iters"], (c, res[c], rs[c])
+        assert res[c]["n_spmv"] == (k + 1) * res[c]["iters"] and res[c]["n_dot"] == 3 * res[c]["iters"]
+    assert torch.equal(X, Xs)
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_group_column_released_mid_run_and_its_range_reused(env, dt):
+    """Continuous batching with a group: a column that stops at once (b = 0)
+    is collected and released while the others run; a new slot admitted into
+    the freed range runs beside them.  Neither disturbs the other: every
+    column and the newcomer match their own runs bit for bit."""
+    torch, nc = env
+    sy = _setup(torch, nc, dt, _systems()[:2])
+    A, S = sy[0][0], sy[0][4]
+    A1, S1 = sy[1][0], sy[1][4]
+    Bh = np.stack([W.uniform_vector(A.n, seed=700 + c) for c in range(4)])
+    Bh[1] = 0.0
+    B = to_dev(torch, Bh)
+    # room for the group and nothing else: the newcomer must take the freed range
+    eng = nc.pcg_batch_create(5, 4 * A.n, 32, f64_apply=(dt == "f64"))
+    slots = nc.pcg_batch_add_solver_multi(eng, S, B)
+    nc.pcg_batch_run(eng, 1e-8, 5000, 2)
+    done, r1 = nc.pcg_batch_status(eng, slots[1])
+    assert done and r1["status"] == 0 and r1["iters"] == 0
+    x1 = torch.full((A.n,), float("nan"), dtype=torch.float64, device="cuda")
+    nc.pcg_batch_collect(eng, slots[1], x1)
+    nc.pcg_batch_release(eng, slots[1])
+    assert A1.n <= A.n
+    b_new = to_dev(torch, W.uniform_vector(A1.n, seed=777))
+    s_new = nc.pcg_batch_add_solver(eng, S1, b_new)
+    assert s_new is not None
+    assert nc.pcg_batch_run(eng, 1e-8, 5000) == 0
+    X = torch.empty_like(B)
+    for c in (0, 2, 3):
+        nc.pcg_batch_collect(eng, slots[c], X[c])
+    x_new = torch.empty_like(b_new)
+    nc.pcg_batch_collect(eng, s_new, x_new)
+    torch.cuda.synchronize()
+    res = {c: nc.pcg_batch_status(eng, slots[c])[1] for c in (0, 2, 3)}
+    r_new = nc.pcg_batch_status(eng, s_new)[1]
+    eng.close()
+    assert torch.count_nonzero(x1) == 0
+    Xs, rs = _run_singles(torch, nc, S, B[[0, 2, 3]].contiguous(), dt == "f64")
+    for i, c in enumerate((0, 2, 3)):
+        assert res[c]["iters"] == rs[i]["iters"]
+        assert torch.equal(X[c], Xs[i]), c
+    xn, rn = _run_singles(torch, nc, S1, b_new.reshape(1, -1), dt == "f64")
+    assert r_new["iters"] == rn[0]["iters"] and torch.equal(x_new, xn[0])
+
+
+def test_group_admission_limits(env):
+    torch, nc = env
+    A, scale, k, M, S, lo, hi = _setup(torch, nc, "f32", _systems()[1:2])[0]
+    eng = nc.pcg_batch_create(8, 3 * A.n, 32)
+    B = to_dev(torch, np.stack([W.uniform_vector(A.n, seed=c) for c in range(9)]))
+    with pytest.raises(nc.NcError) as e:
+        nc.pcg_batch_add_solver_multi(eng, S, B)          # more than 8 columns
+    assert e.value.status == nc.NC_ERR_ARG
+    assert nc.pcg_batch_add_solver_multi(eng, S, B[:4].contiguous()) is None   # 4 n unknowns > 3 n
+    sl = nc.pcg_batch_add_solver_multi(eng, S, B[:3].contiguous())
+    assert sl is not None and len(set(sl)) == 3
+    assert nc.pcg_batch_run(eng, 1e-8, 5000) == 0
+    eng.close()
