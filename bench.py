@@ -186,8 +186,16 @@ def psell_step_bytes(n, nnz, sv=8, sx=8):
     return nnz * sv + 8 * ((n + 31) // 32) + 4 * n * sx
 
 
-def step_bytes_for(layout, n, nnz, sv, sx):
-    return psell_step_bytes(n, nnz, sv, sx) if layout == "psell" else csr_step_bytes(n, nnz, sv, sx)
+def stored_nnz(info, n, nnz):
+    """Entries the layout stores: a constant diagonal folded into the step
+    coefficients (offset-pattern layout) is not among them."""
+    return nnz - (n if info.get("diag_folded") else 0)
+
+
+def step_bytes_for(info, n, nnz, sv, sx):
+    if info["spmv_format"] == "psell":
+        return psell_step_bytes(n, stored_nnz(info, n, nnz), sv, sx)
+    return csr_step_bytes(n, nnz, sv, sx)
 
 
 def bsr3_step_bytes(n, nnzb, sv=8, sx=8):
@@ -209,7 +217,7 @@ def spec_c2(args):
     # fastest of them, k = 10 (all three are reported under "degrees")
     return dict(kind="csr", A=A, n=A.n, nnz=A.nnz, jacobi=True, bounds="lanczos", k=args.k or 10, s=S_THETA,
                 rhs=rhs, rr_mixed=0,
-                bytes=lambda mode, layout: step_bytes_for(layout, A.n, A.nnz, SV[mode], 8 if mode == "f64" else 4),
+                bytes=lambda mode, info: step_bytes_for(info, A.n, A.nnz, SV[mode], 8 if mode == "f64" else 4),
                 workload=f"diffusion3d-7pt lognormal {grid}^3 CSR (n={A.n}, nnz={A.nnz}), Jacobi-scaled",
                 key=f"c2:{A.n}", l2=f"inputs larger than L2 (A = {A.nnz * 12 / 1e6:.0f} MB)")
 
@@ -221,7 +229,7 @@ def spec_c1(args):
     rhs = [W.rhs_from_solution(A, W.uniform_vector(A.n, seed=1 + i)) for i in range(4)]
     return dict(kind="csr", A=A, n=A.n, nnz=A.nnz, jacobi=False, bounds=(lo, hi), k=args.k or 8, s=1.0, rhs=rhs,
                 rr_mixed=0,
-                bytes=lambda mode, layout: step_bytes_for(layout, A.n, A.nnz, SV[mode], 8 if mode == "f64" else 4),
+                bytes=lambda mode, info: step_bytes_for(info, A.n, A.nnz, SV[mode], 8 if mode == "f64" else 4),
                 workload="laplacian2d-5pt 64x64 CSR (n=4096, nnz=20224), exact bounds 4sin^2(pi i/130) sums, b=A x*",
                 persistent=True,
                 key=f"c1:{A.n}", l2="L2-resident system (0.4 MB); latency-bound by construction")
@@ -233,7 +241,7 @@ def spec_c3(args):
     A, b = W.elasticity_q1_bsr3(N, seed=SEED_A)
     return dict(kind="bsr3", A=A, n=A.n, nnz=A.nnzb, jacobi=True, bounds="lanczos", k=args.k or 20, s=S_THETA,
                 rhs=[b], rr_mixed=50,
-                bytes=lambda mode, layout: bsr3_step_bytes(A.n, A.nnzb, SV[mode], 8 if mode == "f64" else 4),
+                bytes=lambda mode, info: bsr3_step_bytes(A.n, A.nnzb, SV[mode], 8 if mode == "f64" else 4),
                 workload=f"elasticity Q1-hex {N}^3 nodes x 3 dofs 3x3-BSR (n={A.n}, blocks={A.nnzb}), "
                          "nu~U[0.25,0.45], bottom clamped, unit body load, Jacobi-scaled",
                 key=f"c3:{A.n}", l2=f"inputs larger than L2 (A = {A.nnzb * 76 / 1e6:.0f} MB)")
@@ -304,7 +312,7 @@ def run_system(args, spec, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         per_launch_s = e0.elapsed_time(e1) / 1e3 / (reps * max(k, 1))
-        return per_launch_s, spec["bytes"](mode, nc.pcg_get_info(S)["spmv_format"])
+        return per_launch_s, spec["bytes"](mode, nc.pcg_get_info(S))
 
     persistent = (args.solve == "persistent" or (args.solve == "auto" and spec.get("persistent", False))) \
         and not args.host_loop
@@ -333,7 +341,8 @@ def run_system(args, spec, rank, world, local_rank):
                "all_converged": all(r["status"] == 0 for r in results),
                "max_relres": max(r["relres"] for r in results),
                "max_true_relres": max(r["true_relres"] for r in results), "rr_period": rr,
-               "layout": nc.pcg_get_info(S)["spmv_format"],
+               "layout": nc.pcg_get_info(S)["spmv_format"] +
+                         ("-fold" if nc.pcg_get_info(S)["diag_folded"] else ""),
                "solve": "persistent" if nc.pcg_get_info(S)["persistent"] else
                         ("host-loop" if args.host_loop else "graph")}
         t_launch, nbytes = time_step_kernel(S, mode)
@@ -433,11 +442,14 @@ def run_system(args, spec, rank, world, local_rank):
     peak, peak_src = peak_hbm()
     achieved = step_bytes / per_launch_s / 1e9
     layout = nc.pcg_get_info(S)["spmv_format"]
+    if layout == "psell" and nc.pcg_get_info(S)["diag_folded"]:
+        layout = "psell-fold"   # the constant diagonal left out of the layout
     kname = {"csr": "sell_step_kernel (fused SpMV + Chebyshev recurrence, SELL-32)",
              "bsr3": "bsell3_step_kernel (fused 3x3-block SpMV + Chebyshev recurrence, BSELL-32)"}[spec["kind"]]
-    if layout == "psell":
+    if layout.startswith("psell"):
         kname = ("sell_step_kernel<PAT> (fused SpMV + Chebyshev recurrence, SELL-32 with per-slice offset "
-                 "patterns: no column indices)")
+                 "patterns: no column indices" + ("; constant diagonal in the u coefficient)" if layout == "psell-fold"
+                                                  else ")"))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": read_traffic(f"{spec['key']}:{layout}", args.apply),
                 "layout": layout,
@@ -447,9 +459,13 @@ def run_system(args, spec, rank, world, local_rank):
         # the same step against the float64 rate: GB300 issues 2 float64 FMA
         # per clock per SM, so a float64 step can meet that ceiling before
         # HBM.  Algorithmic flops: one FMA per nonzero and the combination
-        # d (A' u) + c r + b w per row (shifted operator).  The roofline
-        # reported is the one the step is closer to.
-        flops = 2.0 * spec["nnz"] * (9 if spec["kind"] == "bsr3" else 1) + 5.0 * n
+        # d (A' u) + c r + b w per row (shifted operator); a constant diagonal
+        # folded out of the layout becomes the u term's product instead (one
+        # FMA per row either way).  The roofline reported is the one the step
+        # is closer to.
+        sinfo = nc.pcg_get_info(S)
+        flops = (2.0 * spec["nnz"] * 9 + 5.0 * n if spec["kind"] == "bsr3"
+                 else 2.0 * stored_nnz(sinfo, n, spec["nnz"]) + (7.0 if sinfo["diag_folded"] else 5.0) * n)
         tf = flops / per_launch_s / 1e12
         if tf / FP64_PEAK_TFLOPS > roofline["frac"]:
             hbm = {"achieved_GBps": roofline["achieved"], "peak": peak, "frac": roofline["frac"]}

@@ -164,6 +164,12 @@ typedef struct {
     int red_ctas_per_sm; /* DIRECT steps with a dot product: persistent CTAs
                           per SM, 1..64 (default 8; 64 = one 256-row tile per
                           CTA on any device)                                   */
+    int keep_diagonal; /* PSELL: 0 (default) leaves a constant diagonal (every
+                          row's a_ii bitwise equal, as after nc_matrix_jacobi,
+                          whose scaled diagonal is exactly 1) out of the
+                          layout and applies it through the step's u
+                          coefficient: one product and one value fewer per
+                          row; 1 stores it like any entry                      */
 } nc_options;
 
 typedef struct {
@@ -197,6 +203,10 @@ typedef struct {
                              of the plain steps; 0 for explicit matrices     */
     int32_t stencil_planes_per_batch; /* and planes per z-march batch (0:
                              the size policy, 2 or 4)                         */
+    int32_t diag_folded;  /* PSELL: 1 when the constant diagonal is left out of
+                             the layout (keep_diagonal 0)                     */
+    int32_t reserved1;
+    double diag_value;    /* and its value in the stored operator, a_ii - shift */
 } nc_solver_info;
 
 /* One configuration measured by the tuner (pcg_setup with step_kernel =

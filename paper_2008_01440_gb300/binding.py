@@ -45,7 +45,7 @@ class nc_options(ctypes.Structure):
                 ("poly_form", ctypes.c_int), ("step_kernel", ctypes.c_int), ("step_stages", ctypes.c_int),
                 ("step_ctas_per_sm", ctypes.c_int), ("step_rows_per_thread", ctypes.c_int),
                 ("step_tile_order", ctypes.c_int), ("prefetch_tiles", ctypes.c_int),
-                ("red_ctas_per_sm", ctypes.c_int)]
+                ("red_ctas_per_sm", ctypes.c_int), ("keep_diagonal", ctypes.c_int)]
 
 
 class nc_solver_info(ctypes.Structure):
@@ -61,7 +61,8 @@ class nc_solver_info(ctypes.Structure):
                 ("prefetch_tiles", ctypes.c_int32), ("red_ctas_per_sm", ctypes.c_int32),
                 ("tune_candidates", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("faults", ctypes.c_int32),
                 ("tune_from_cache", ctypes.c_int32), ("stencil_zchunk", ctypes.c_int32),
-                ("stencil_planes_per_batch", ctypes.c_int32)]
+                ("stencil_planes_per_batch", ctypes.c_int32), ("diag_folded", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32), ("diag_value", ctypes.c_double)]
 
 
 class nc_tune_candidate(ctypes.Structure):
@@ -309,7 +310,8 @@ _POLY = {"chebyshev": 0, "newton": 1}
 
 def make_options(apply_dtype="f64", rr_period=0, x0_is_zero=False, use_graph=True, spmv_format="auto",
                  persistent=False, poly="chebyshev", step_kernel="auto", step_stages=0, step_ctas_per_sm=0,
-                 step_rows_per_thread=0, step_tile_order=0, prefetch_tiles=0, red_ctas_per_sm=0) -> nc_options:
+                 step_rows_per_thread=0, step_tile_order=0, prefetch_tiles=0, red_ctas_per_sm=0,
+                 keep_diagonal=False) -> nc_options:
     o = nc_options()
     lib.nc_options_default(ctypes.byref(o))
     o.spmv_format = _FORMATS[spmv_format] if isinstance(spmv_format, str) else int(spmv_format)
@@ -325,6 +327,7 @@ def make_options(apply_dtype="f64", rr_period=0, x0_is_zero=False, use_graph=Tru
     o.step_tile_order = int(step_tile_order)
     o.prefetch_tiles = int(prefetch_tiles)
     o.red_ctas_per_sm = int(red_ctas_per_sm)
+    o.keep_diagonal = int(bool(keep_diagonal))
     return o
 
 

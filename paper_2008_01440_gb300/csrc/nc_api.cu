@@ -23,6 +23,7 @@ void nc_options_default(nc_options* opt) {
     opt->step_tile_order = 0;
     opt->prefetch_tiles = 0;
     opt->red_ctas_per_sm = 0;
+    opt->keep_diagonal = 0;
 }
 
 const char* nc_strerror(nc_status s) {
@@ -307,6 +308,8 @@ nc_status pcg_get_info(nc_solver S, nc_solver_info* info) {
     info->tune_from_cache = S->tune_cached ? 1 : 0;
     info->stencil_zchunk = S->opP.kind == OP_STENCIL ? stencil_zchunk(S->opP.geom) : 0;
     info->stencil_planes_per_batch = S->opP.geom.pz;
+    info->diag_folded = S->op64.dfolded;
+    info->diag_value = S->op64.dfold;
     if (S->S) {
         int f = 0;
         if (cudaMemcpy(&f, &S->S->fault, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {

@@ -67,7 +67,8 @@ struct BDesc {
     double *dt0, *dt1, *dt2;        // float64 apply: the Chebyshev vectors, r read directly
     // SLOT_SELL: an explicit matrix in a solver's SELL-32 layout (borrowed):
     // slice offsets, columns (plain) or offset patterns, the float64 values of
-    // A - shift I and the values inside P (apply precision vdtP)
+    // the stored operator S (A - theta' I, its constant diagonal possibly left
+    // out) and the values inside P (apply precision vdtP); A u = S u + shift u
     int kind, vdtP;
     double shift;
     const int32_t *sptr, *scol;
@@ -1447,19 +1448,21 @@ nc_status pcg_batch_add_solver_multi(nc_batch B, nc_solver S, int m, const doubl
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the solver's own step coefficients, as its solves take them (the
     // float64 iterates scaled so that the product's coefficient is 1)
+    // (a diagonal the layout leaves out enters through the u coefficient)
     const std::vector<StepC> sc = step_coefs(S, true);
     std::vector<BCoef> cf(S->k);
     for (int j = 1; j <= S->k; ++j) {
         BCoef c{};
-        c.e0 = (float)sc[j].ca;
+        const double ca = sc[j].ca + sc[j].cd * S->opP.dfold;
+        c.e0 = (float)ca;
         c.ex = (float)sc[j].cd;
         c.cb = (float)sc[j].cb;
         c.cc = (float)sc[j].cc;
-        c.e0d = sc[j].ca;
+        c.e0d = ca;
         c.exd = sc[j].cd;
         c.cbd = sc[j].cb;
         c.ccd = sc[j].cc;
-        c.terms = (sc[j].ca != 0.0 ? kTermU : 0) | (sc[j].cb != 0.0 ? kTermW : 0) | (sc[j].cc != 0.0 ? kTermR : 0) |
+        c.terms = (ca != 0.0 ? kTermU : 0) | (sc[j].cb != 0.0 ? kTermW : 0) | (sc[j].cc != 0.0 ? kTermR : 0) |
                   (sc[j].cd == 1.0 ? kUnitD : 0);
         c.xu = sc[j].cd == 1.0 ? 1 : 0;
         cf[j - 1] = c;
@@ -1487,7 +1490,7 @@ nc_status pcg_batch_add_solver_multi(nc_batch B, nc_solver S, int m, const doubl
         d.val64 = static_cast<const double*>(S->op64.val);
         d.valP = S->opP.val;
         d.vdtP = S->opP.vdt;
-        d.shift = S->shift;
+        d.shift = S->shift + S->op64.dfold;   // the u term of q = A p and b - A x
         d.disv = S->A->scaled ? S->A->dis : nullptr;
         double* base64 = B->pool64 + 6 * oc;
         d.b = base64; d.x = base64 + n; d.r = base64 + 2 * n; d.z = base64 + 3 * n; d.p = base64 + 4 * n;

@@ -248,12 +248,13 @@ int sell_staged_ctas(int vdt, bool x_f32, bool y_f64, int dot, bool unit, const 
 // SELL-32 layout with host slice offsets hsptr[0..nslices].
 int sell_max_tile_entries(const int32_t* hsptr, int nslices, int per_tile);
 // Pattern layout construction from CSR: per-slice offset sets (a counting
-// pass with off null, then a writing pass at opos), then the slot-major fill.
+// pass with off null, then a writing pass at opos), then the slot-major fill;
+// skip_diag leaves the diagonal entries out of both.
 cudaError_t launch_psell_merge(int n, const int32_t* rowptr, const int32_t* col, const int32_t* opos, int32_t* cnt,
-                               int32_t* off, int* bad, cudaStream_t st);
+                               int32_t* off, int* bad, int skip_diag, cudaStream_t st);
 cudaError_t launch_psell_fill(int n, const int32_t* rowptr, const int32_t* col, const double* val,
                               const int32_t* slice_ptr, const int32_t* pstart, const int32_t* poff, int vdt,
-                              double shift, void* sval, int* nodiag, cudaStream_t st);
+                              double shift, void* sval, int* nodiag, int skip_diag, cudaStream_t st);
 // SELL-32 construction from CSR: longest row per slice, then the slot-major fill
 cudaError_t launch_sell_lengths(int n, const int32_t* rowptr, int32_t* slice_len, cudaStream_t st);
 // (diagonal entries stored as a_ii - shift; *nodiag set if a row lacks one)
@@ -311,6 +312,9 @@ cudaError_t launch_csr_diag(int n, const int32_t* rowptr, const int32_t* col, co
                             double* dis, int* bad, cudaStream_t st);
 cudaError_t launch_csr_scale(int n, const int32_t* rowptr, const int32_t* col, const double* val,
                              const double* dis, double* out, cudaStream_t st);
+// *flags |= 1 unless every row has a diagonal entry equal (bitwise) to row 0's
+cudaError_t launch_csr_diag_const(int n, const int32_t* rowptr, const int32_t* col, const double* val, int* flags,
+                                  cudaStream_t st);
 cudaError_t launch_csr_gershgorin(int n, const int32_t* rowptr, const double* val,
                                   unsigned long long* out_bits, cudaStream_t st);
 cudaError_t launch_convert(int64_t count, const double* in, int out_dt, void* out, cudaStream_t st);

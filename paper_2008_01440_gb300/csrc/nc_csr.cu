@@ -112,14 +112,33 @@ __global__ void csr_diag_kernel(int n, const int32_t* __restrict__ rowptr,
     }
 }
 
-// a_ij -> (a_ij d_i^{-1/2}) d_j^{-1/2}
+// a_ij -> (a_ij d_i^{-1/2}) d_j^{-1/2}; the diagonal becomes its exact
+// value 1 (a_ii d_i^{-1/2} d_i^{-1/2} rounds to 1 +- an ulp otherwise), so
+// that a scaled matrix has the constant diagonal the offset-pattern layout
+// can fold into its step coefficients
 __global__ void csr_scale_kernel(int n, const int32_t* __restrict__ rowptr,
                                  const int32_t* __restrict__ col, const double* __restrict__ val,
                                  const double* __restrict__ dis, double* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double di = dis[i];
-    for (int j = rowptr[i]; j < rowptr[i + 1]; ++j) out[j] = val[j] * di * dis[col[j]];
+    for (int j = rowptr[i]; j < rowptr[i + 1]; ++j) out[j] = col[j] == i ? 1.0 : val[j] * di * dis[col[j]];
+}
+
+// Whether every row has a diagonal entry and all of them equal row 0's
+// (bitwise): *flags bit 0 set if not.  The diagonal of row 0 is the
+// reference; a row without one sets the bit as well.
+__global__ void csr_diag_const_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                      const double* __restrict__ val, int* __restrict__ flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool found = false, found0 = false;
+    double d = 0.0, d0 = 0.0;
+    for (int j = rowptr[i]; j < rowptr[i + 1]; ++j)
+        if (col[j] == i) { d = val[j]; found = true; }
+    for (int j = rowptr[0]; j < rowptr[1]; ++j)
+        if (col[j] == 0) { d0 = val[j]; found0 = true; }
+    if (!found || !found0 || __double_as_longlong(d) != __double_as_longlong(d0)) atomicOr(flags, 1);
 }
 
 // max_i sum_j |a_ij|; non-negative doubles order like their bit patterns.
@@ -188,6 +207,13 @@ cudaError_t launch_csr_scale(int n, const int32_t* rowptr, const int32_t* col, c
                              const double* dis, double* out, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     csr_scale_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, rowptr, col, val, dis, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_diag_const(int n, const int32_t* rowptr, const int32_t* col, const double* val, int* flags,
+                                  cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    csr_diag_const_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, rowptr, col, val, flags);
     return cudaGetLastError();
 }
 

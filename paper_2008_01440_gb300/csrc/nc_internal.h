@@ -33,6 +33,11 @@ struct OpView {
     double c4[4] = {0, 0, 0, 0};
     SellPat pat;                    // OP_SELL with offset patterns (pat.pstart set): col unused
     StepTune tune;                  // OP_SELL: kernel variant and launch shape
+    // OP_SELL whose layout leaves out a constant diagonal: its value in the
+    // stored operator (a_ii - shift), applied through the step's u term
+    // (op_step adds cd * dfold to ca); 0 when the diagonal is stored
+    double dfold = 0.0;
+    int dfolded = 0;                // 1: the layout leaves the diagonal out
 };
 
 

@@ -217,12 +217,13 @@ __global__ void sell_fill_kernel(int n, const int32_t* __restrict__ rowptr, cons
 // repeats counts once per repetition), so a slice holding L entries ends
 // after at most L rounds.  Counting pass (off null): cnt[s].  Writing pass:
 // off[opos[s] + j].  *bad is set if a row's columns do not increase or a
-// slice needs more than kPatMaxSlots offsets.
+// slice needs more than kPatMaxSlots offsets.  skip_diag: the diagonal
+// entries are left out (a constant diagonal applied by the step's u term).
 constexpr int kPatMaxSlots = 64;
 
 __global__ void psell_merge_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                    const int32_t* __restrict__ opos, int32_t* __restrict__ cnt,
-                                   int32_t* __restrict__ off, int* __restrict__ bad) {
+                                   int32_t* __restrict__ off, int* __restrict__ bad, const int skip_diag) {
     const int s = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     const int nslices = (n + 31) >> 5;
@@ -237,6 +238,7 @@ __global__ void psell_merge_kernel(int n, const int32_t* __restrict__ rowptr, co
     int last = INT_MIN, c = 0;
     bool fail = false;
     while (true) {
+        if (skip_diag && pos < end && col[pos] == row) ++pos;   // at most once: the columns increase
         const int my = pos < end ? col[pos] - row : INT_MAX;
         int m = my;
 #pragma unroll
@@ -259,12 +261,13 @@ __global__ void psell_merge_kernel(int n, const int32_t* __restrict__ rowptr, co
 }
 
 // Slot-major fill of the pattern layout: slot j of a row holds its entry at
-// column row + offset j, or 0; diagonal entries stored as a_ii - shift.
+// column row + offset j, or 0; diagonal entries stored as a_ii - shift, or
+// not at all (skip_diag: the pattern has no offset 0 for them).
 template <typename VT>
 __global__ void psell_fill_kernel(int n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                   const double* __restrict__ val, const int32_t* __restrict__ slice_ptr,
                                   const int32_t* __restrict__ pstart, const int32_t* __restrict__ poff, double shift,
-                                  VT* __restrict__ sval, int* __restrict__ nodiag) {
+                                  VT* __restrict__ sval, int* __restrict__ nodiag, const int skip_diag) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     const int nslices = (n + 31) >> 5;
     if ((row >> 5) >= nslices) return;
@@ -281,6 +284,10 @@ __global__ void psell_fill_kernel(int n, const int32_t* __restrict__ rowptr, con
     for (int j = 0; j < len; ++j) {
         const int o = op[j];
         double v = 0.0;
+        if (skip_diag && pos < end && col[pos] == row) {
+            ++pos;
+            has_diag = true;
+        }
         if (pos < end && col[pos] - row == o) {
             v = val[pos];
             if (o == 0) {
@@ -291,6 +298,7 @@ __global__ void psell_fill_kernel(int n, const int32_t* __restrict__ rowptr, con
         }
         put_val(&sval[beg + 32 * j], v);
     }
+    if (skip_diag && pos < end && col[pos] == row) has_diag = true;   // after the row's last stored offset
     if (row < n && !has_diag && shift != 0.0 && nodiag != nullptr) atomicOr(nodiag, 1);
 }
 
@@ -410,28 +418,30 @@ cudaError_t launch_sell_fill(int n, const int32_t* rowptr, const int32_t* col, c
 }
 
 cudaError_t launch_psell_merge(int n, const int32_t* rowptr, const int32_t* col, const int32_t* opos, int32_t* cnt,
-                               int32_t* off, int* bad, cudaStream_t st) {
+                               int32_t* off, int* bad, int skip_diag, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const long long threads = (long long)((n + 31) / 32) * 32;
-    psell_merge_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, rowptr, col, opos, cnt, off, bad);
+    psell_merge_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, rowptr, col, opos, cnt, off, bad,
+                                                                           skip_diag);
     return cudaGetLastError();
 }
 
 cudaError_t launch_psell_fill(int n, const int32_t* rowptr, const int32_t* col, const double* val,
                               const int32_t* slice_ptr, const int32_t* pstart, const int32_t* poff, int vdt,
-                              double shift, void* sval, int* nodiag, cudaStream_t st) {
+                              double shift, void* sval, int* nodiag, int skip_diag, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int threads = ((n + 31) / 32) * 32;
     const int grid = (threads + 255) / 256;
     if (vdt == NC_F64)
         psell_fill_kernel<double><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, pstart, poff, shift,
-                                                        static_cast<double*>(sval), nodiag);
+                                                        static_cast<double*>(sval), nodiag, skip_diag);
     else if (vdt == NC_F32)
         psell_fill_kernel<float><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, pstart, poff, shift,
-                                                       static_cast<float*>(sval), nodiag);
+                                                       static_cast<float*>(sval), nodiag, skip_diag);
     else if (vdt == NC_BF16)
         psell_fill_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(n, rowptr, col, val, slice_ptr, pstart, poff, shift,
-                                                               static_cast<__nv_bfloat16*>(sval), nodiag);
+                                                               static_cast<__nv_bfloat16*>(sval), nodiag,
+                                                               skip_diag);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

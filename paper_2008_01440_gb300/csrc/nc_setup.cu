@@ -177,8 +177,43 @@ nc_status setup_psell(nc_solver S, cudaStream_t st, size_t eb) {
         std::vector<int32_t> cnt(nslices);
         int bad = 0;
         cudaError_t e;
+        // a constant diagonal (every row's a_ii bitwise equal) stays out of the
+        // layout: the steps apply it through their u coefficient
+        int fold = 0;
+        double d0 = 0.0;
+        if (!S->opt.keep_diagonal && n > 0) {
+            int flags = 0, r0[2] = {0, 0};
+            if ((e = cudaMemsetAsync(dbad, 0, sizeof(int), st)) ||
+                (e = launch_csr_diag_const(n, A->rowptr, A->col, A->val, dbad, st)) ||
+                (e = cudaMemcpyAsync(&flags, dbad, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+                (e = cudaMemcpyAsync(r0, A->rowptr, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
+                (e = cudaStreamSynchronize(st))) {
+                g_last_cuda = e;
+                ret = NC_ERR_CUDA;
+                break;
+            }
+            if (flags == 0) {   // row 0 has its diagonal: find its value
+                std::vector<int32_t> c0(r0[1] - r0[0]);
+                std::vector<double> v0(c0.size());
+                if (!c0.empty() &&
+                    ((e = cudaMemcpyAsync(c0.data(), A->col + r0[0], sizeof(int32_t) * c0.size(),
+                                          cudaMemcpyDeviceToHost, st)) ||
+                     (e = cudaMemcpyAsync(v0.data(), A->val + r0[0], sizeof(double) * v0.size(),
+                                          cudaMemcpyDeviceToHost, st)) ||
+                     (e = cudaStreamSynchronize(st)))) {
+                    g_last_cuda = e;
+                    ret = NC_ERR_CUDA;
+                    break;
+                }
+                for (size_t i = 0; i < c0.size(); ++i)
+                    if (c0[i] == 0) {
+                        d0 = v0[i];
+                        fold = 1;
+                    }
+            }
+        }
         if ((e = cudaMemsetAsync(dbad, 0, sizeof(int), st)) ||
-            (e = launch_psell_merge(n, A->rowptr, A->col, nullptr, dcnt, nullptr, dbad, st)) ||
+            (e = launch_psell_merge(n, A->rowptr, A->col, nullptr, dcnt, nullptr, dbad, fold, st)) ||
             (e = cudaMemcpyAsync(cnt.data(), dcnt, sizeof(int32_t) * nslices, cudaMemcpyDeviceToHost, st)) ||
             (e = cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
             (e = cudaStreamSynchronize(st))) {
@@ -207,7 +242,7 @@ nc_status setup_psell(nc_solver S, cudaStream_t st, size_t eb) {
         ret = NC_ERR_UNSUPPORTED;
         std::vector<int32_t> off((size_t)noff);
         if ((e = cudaMemcpyAsync(dopos, opos.data(), sizeof(int32_t) * (nslices + 1), cudaMemcpyHostToDevice, st)) ||
-            (e = launch_psell_merge(n, A->rowptr, A->col, dopos, nullptr, doff, dbad, st)) ||
+            (e = launch_psell_merge(n, A->rowptr, A->col, dopos, nullptr, doff, dbad, fold, st)) ||
             (e = cudaMemcpyAsync(off.data(), doff, sizeof(int32_t) * (size_t)noff, cudaMemcpyDeviceToHost, st)) ||
             (e = cudaStreamSynchronize(st))) {
             g_last_cuda = e;
@@ -248,7 +283,7 @@ nc_status setup_psell(nc_solver S, cudaStream_t st, size_t eb) {
             (!table.empty() && (e = cudaMemcpyAsync(S->psell_off, table.data(), sizeof(int32_t) * table.size(),
                                                     cudaMemcpyHostToDevice, st))) ||
             (e = launch_psell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, S->psell_start, S->psell_off, NC_F64,
-                                   S->shift, S->sell_val64, dbad, st)) ||
+                                   S->shift, S->sell_val64, dbad, fold, st)) ||
             (e = cudaMemcpyAsync(&h_nodiag, dbad, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
             (e = cudaStreamSynchronize(st))) {
             g_last_cuda = e;
@@ -258,7 +293,7 @@ nc_status setup_psell(nc_solver S, cudaStream_t st, size_t eb) {
         if (h_nodiag) {   // a row without a diagonal entry: store A itself
             S->shift = 0.0;
             if ((e = launch_psell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, S->psell_start, S->psell_off,
-                                       NC_F64, 0.0, S->sell_val64, nullptr, st))) {
+                                       NC_F64, 0.0, S->sell_val64, nullptr, fold, st))) {
                 g_last_cuda = e;
                 ret = NC_ERR_CUDA;
                 break;
@@ -266,11 +301,13 @@ nc_status setup_psell(nc_solver S, cudaStream_t st, size_t eb) {
         }
         S->op64 = OpView{OP_SELL, n, S->sell_ptr, nullptr, S->sell_val64, NC_F64};
         S->op64.pat = SellPat{S->psell_start, S->psell_off};
+        S->op64.dfold = fold ? d0 - S->shift : 0.0;   // the stored operator's diagonal, a_ii - shift
+        S->op64.dfolded = fold;
         S->opP = S->op64;
         if (S->mixed) {
             if ((ret = dev_alloc(&S->sell_valP, eb * (size_t)(total > 0 ? total : 1))) != NC_OK) break;
             if ((e = launch_psell_fill(n, A->rowptr, A->col, A->val, S->sell_ptr, S->psell_start, S->psell_off,
-                                       S->vdt, S->shift, S->sell_valP, nullptr, st))) {
+                                       S->vdt, S->shift, S->sell_valP, nullptr, fold, st))) {
                 g_last_cuda = e;
                 ret = NC_ERR_CUDA;
                 break;

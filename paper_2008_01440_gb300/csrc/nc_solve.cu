@@ -83,9 +83,9 @@ OpView mat_view(nc_matrix A) {
 cudaError_t op_step(const OpView& op, bool x_f32, bool y_f64, const void* u, const void* w, const void* r,
                     void* y, double ca, double cb, double cc, double cd, int dot, const double* rdot,
                     const Reduce& R, const int* done, cudaStream_t st) {
-    if (op.kind == OP_SELL)
-        return launch_sell_step(op.n, op.ptr, op.col, op.pat, op.val, op.vdt, x_f32, y_f64, u, w, r, y, ca, cb, cc,
-                                cd, dot, rdot, R, done, st, op.tune);
+    if (op.kind == OP_SELL)   // a diagonal left out of the layout enters through the u term
+        return launch_sell_step(op.n, op.ptr, op.col, op.pat, op.val, op.vdt, x_f32, y_f64, u, w, r, y,
+                                ca + cd * op.dfold, cb, cc, cd, dot, rdot, R, done, st, op.tune);
     if (op.kind == OP_STENCIL)
         return launch_stencil_step(op.geom, op.c4, x_f32, y_f64, u, w, r, y, ca, cb, cc, cd, dot, rdot, R, done,
                                    st);

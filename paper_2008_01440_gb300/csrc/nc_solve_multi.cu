@@ -30,8 +30,9 @@ cudaError_t menqueue_poly(nc_solver S, int m, int fin, cudaStream_t st) {
         const bool last = (j == S->k);
         void* y = last ? static_cast<void*>(S->mz) : S->mbuf[j % 3];
         cudaError_t e = launch_sell_mstep(n, m, n, S->opP.ptr, S->opP.col, S->opP.pat, S->opP.val, S->opP.vdt,
-                                          S->mixed, last || !S->mixed, u, w, rx, y, cf[j].ca, cf[j].cb, cf[j].cc,
-                                          cf[j].cd, S->mS, st);
+                                          S->mixed, last || !S->mixed, u, w, rx, y,
+                                          cf[j].ca + cf[j].cd * S->opP.dfold, cf[j].cb, cf[j].cc, cf[j].cd, S->mS,
+                                          st);
         if (e) return e;
     }
     if (fin == FIN_NONE) return cudaSuccess;
@@ -72,7 +73,8 @@ cudaError_t menqueue_body(nc_solver S, int m, cudaGraphConditionalHandle h, int 
     cudaError_t e;
     // q = A p for all columns (A' p + shift p with the shifted operator)
     if ((e = launch_sell_mstep(n, m, n, S->op64.ptr, S->op64.col, S->op64.pat, S->op64.val, NC_F64, false, true,
-                               S->mp, nullptr, nullptr, S->mq, S->shift, 0.0, 0.0, 1.0, S->mS, st)))
+                               S->mp, nullptr, nullptr, S->mq, S->shift + S->op64.dfold, 0.0, 0.0, 1.0, S->mS,
+                               st)))
         return e;
     for (int c = 0; c < m; ++c) {
         PcgScalars* Sc = S->mS + c;

@@ -1,9 +1,11 @@
 """The offset-pattern sliced layout (NC_FORMAT_PSELL): slices store no column
 indices, only which distinct set of offsets col - row they use.
 
-Its products must equal the plain sliced layout's exactly: both run the same
-fma chain per row in column order, and a slot a row lacks holds a 0, whose
-fma leaves the sum unchanged.  Both are checked against the oracle as well,
+With its diagonal stored (keep_diagonal) its products must equal the plain
+sliced layout's exactly: both run the same fma chain per row in column
+order, and a slot a row lacks holds a 0, whose fma leaves the sum unchanged.
+A constant diagonal left out of the layout (the default) changes only the
+rounding: those results are checked against the oracle and the stored form.  Both are checked against the oracle as well,
 together with the conditions under which the solver falls back to SELL-32
 (columns not increasing, more than 64 offsets in a slice, too many distinct
 sets), a row without a diagonal (no shifted operator), grid faces whose
@@ -50,13 +52,17 @@ def test_laplacian_equals_sell_and_oracle(env, grid, k, s):
     lo, hi = W.laplacian_2d_bounds(nx, ny)
     M = csr_to_gpu(torch, nc, A)
     v = W.uniform_vector(A.n, seed=k)
-    ip, zp = apply(torch, nc, M, A.n, lo, hi, k, s, v, spmv_format="psell")
+    ip, zp = apply(torch, nc, M, A.n, lo, hi, k, s, v, spmv_format="psell", keep_diagonal=True)
     isl, zs = apply(torch, nc, M, A.n, lo, hi, k, s, v, spmv_format="sell")
-    assert ip["spmv_format"] == "psell" and isl["spmv_format"] == "sell"
+    assert ip["spmv_format"] == "psell" and isl["spmv_format"] == "sell" and ip["diag_folded"] == 0
     assert 1 <= ip["patterns"] <= 9 and ip["padding"] < 1.5
     assert np.array_equal(zp, zs)
     ref = O.cheb_apply(O.csr_matvec(A.rowptr, A.col, A.val, A.n), v, O.cheb_params(lo, hi, s), k)
     assert rel_err(zp, ref) <= 1e-12 and elem_err(zp, ref) <= 1e-12
+    # the Laplacian's constant diagonal (4) left out of the layout
+    iff, zf = apply(torch, nc, M, A.n, lo, hi, k, s, v, spmv_format="psell")
+    assert iff["diag_folded"] == 1 and iff["diag_value"] == 4.0 - iff["shift"] and iff["padding"] < 1.0
+    assert rel_err(zf, ref) <= 1e-12 and elem_err(zf, ref) <= 1e-12
 
 
 @pytest.mark.parametrize("N", [21, 32])
@@ -68,14 +74,18 @@ def test_diffusion_solve_equals_sell(env, N, dt):
     lo, hi, _, _ = nc.nc_bounds_lanczos(M, 20, to_dev(torch, W.uniform_vector(A.n, seed=3)))
     b = to_dev(torch, W.uniform_vector(A.n, seed=5))
     out = {}
-    for fmt in ("psell", "sell"):
-        S = nc.pcg_setup(M, lo, hi, 10, 1.001, apply_dtype=dt, spmv_format=fmt)
+    for fmt, keep in (("psell", True), ("sell", False), ("psell", False)):
+        S = nc.pcg_setup(M, lo, hi, 10, 1.001, apply_dtype=dt, spmv_format=fmt, keep_diagonal=keep)
         assert nc.pcg_get_info(S)["spmv_format"] == fmt
         x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
-        out[fmt] = (nc.pcg_solve(S, b, x, 1e-8, 2000), x.cpu().numpy())
-    (rp, xp), (rs, xs) = out["psell"], out["sell"]
+        out[fmt, keep] = (nc.pcg_solve(S, b, x, 1e-8, 2000), x.cpu().numpy())
+    (rp, xp), (rs, xs) = out["psell", True], out["sell", False]
     assert rp["status"] == 0 and rp["true_relres"] <= 2e-8
     assert rp["iters"] == rs["iters"] and np.array_equal(xp, xs)
+    # the scaled diagonal (exactly 1) left out: the same iterations +-1, the solution within reach
+    rf, xf = out["psell", False]
+    assert rf["status"] == 0 and abs(rf["iters"] - rp["iters"]) <= 1
+    assert rel_err(xf, xp) <= (hi / lo) * 1e-8
     # and against the oracle's PCG (float64 only: the others report error against it)
     if dt == "f64":
         val, dis = O.jacobi_scale_csr(A.rowptr, A.col, A.val, A.n)
@@ -83,8 +93,8 @@ def test_diffusion_solve_equals_sell(env, N, dt):
         prm = O.cheb_params(lo, hi, 1.001)
         bo = dis * W.uniform_vector(A.n, seed=5)
         ro = O.pcg(mv, bo, lambda r: O.cheb_apply(mv, r, prm, 10), m=10, tol=1e-8, maxit=2000)
-        assert abs(rp["iters"] - ro.iters) <= 1
-        assert rel_err(xp, dis * ro.x) <= (hi / lo) * 1e-8
+        assert abs(rp["iters"] - ro.iters) <= 1 and abs(rf["iters"] - ro.iters) <= 1
+        assert rel_err(xp, dis * ro.x) <= (hi / lo) * 1e-8 and rel_err(xf, dis * ro.x) <= (hi / lo) * 1e-8
 
 
 def test_falls_back_when_columns_do_not_increase(env):
@@ -126,7 +136,8 @@ def test_falls_back_on_unstructured_columns(env):
 
 def test_falls_back_when_the_sets_do_not_repeat(env):
     """Three offsets per slice, but a different set in every slice: the
-    distinct sets exceed the 16384-offset table."""
+    distinct sets exceed the 16384-offset table.  (The diagonal varies, so
+    it stays in the layout: folded out, two offsets per slice would fit.)"""
     torch, nc = env
     n = 1 << 18
     rows, vals = [], []
@@ -134,7 +145,7 @@ def test_falls_back_when_the_sets_do_not_repeat(env):
         d = 1 + (i >> 5)
         c = [j for j in (i - d, i, i + d) if 0 <= j < n]
         rows.append(np.array(c))
-        vals.append(np.array([4.0 if j == i else -1.0 for j in c]))
+        vals.append(np.array([4.0 + 0.25 * (i % 3) if j == i else -1.0 for j in c]))
     B = csr_from_rows(n, rows, vals)
     M = csr_to_gpu(torch, nc, B)
     v = W.uniform_vector(n, seed=6)
@@ -170,7 +181,7 @@ def test_multi_rhs_equals_sell(env, dt):
     B = torch.stack([to_dev(torch, W.uniform_vector(A.n, seed=40 + c)) for c in range(5)])
     out = {}
     for fmt in ("psell", "sell"):
-        S = nc.pcg_setup(M, lo, hi, 12, 1.001, apply_dtype=dt, spmv_format=fmt)
+        S = nc.pcg_setup(M, lo, hi, 12, 1.001, apply_dtype=dt, spmv_format=fmt, keep_diagonal=True)
         assert nc.pcg_get_info(S)["spmv_format"] == fmt
         X = torch.zeros_like(B)
         out[fmt] = (nc.pcg_solve_multi(S, B, X, 1e-8, 2000), X.cpu().numpy())

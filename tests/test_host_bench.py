@@ -11,8 +11,13 @@ def test_step_byte_models():
     assert bench.csr_step_bytes(n, nnz, 4, 4) == nnz * 8 + 4 * (n + 1) + 16 * n
     # offset-pattern layout: no column indices, 8 bytes of slice data per 32 rows
     assert bench.psell_step_bytes(n, nnz) == nnz * 8 + 8 * (n // 32) + 32 * n == 184_287_232
-    assert bench.step_bytes_for("psell", n, nnz, 8, 8) == bench.psell_step_bytes(n, nnz)
-    assert bench.step_bytes_for("sell", n, nnz, 8, 8) == bench.csr_step_bytes(n, nnz)
+    assert bench.step_bytes_for({"spmv_format": "psell"}, n, nnz, 8, 8) == bench.psell_step_bytes(n, nnz)
+    assert bench.step_bytes_for({"spmv_format": "sell"}, n, nnz, 8, 8) == bench.csr_step_bytes(n, nnz)
+    # a constant diagonal folded into the step coefficients is not stored: n values fewer
+    folded = {"spmv_format": "psell", "diag_folded": 1}
+    assert bench.step_bytes_for(folded, n, nnz, 8, 8) == bench.psell_step_bytes(n, nnz - n) == 184_287_232 - 8 * n
+    assert bench.stored_nnz(folded, n, nnz) == nnz - n
+    assert bench.stored_nnz({"spmv_format": "psell", "diag_folded": 0}, n, nnz) == nnz
     # 3x3 blocks: 9 values and one block column per block
     assert bench.bsr3_step_bytes(30, 10) == 10 * (9 * 8 + 4) + 4 * 11 + 32 * 30
 
@@ -22,6 +27,9 @@ def test_traffic_is_keyed_by_layout_and_precision():
     assert bench.read_traffic("c2:2097152:sell", "f64") == 229_708_800
     assert bench.read_traffic("c2:2097152:psell", "f32") == 87_088_640
     assert bench.read_traffic("c2:2097152:psell", "bf16") == 55_056_128
+    # the layout with its constant diagonal folded out: its own captures
+    assert bench.read_traffic("c2:2097152:psell-fold", "f64") == 155_038_976
+    assert bench.read_traffic("c2:2097152:psell-fold", "f64") <= bench.psell_step_bytes(2_097_152, 14_581_760 - 2_097_152)
     # no capture of this kernel in this form: no number
     assert bench.read_traffic("c2:2097152:psell", "f16") is None
     assert bench.read_traffic("c2:2097152", "f64") is None
