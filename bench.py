@@ -68,7 +68,7 @@ def parse():
                     help="c2: skip the compact batched (c4) and serving (c5) passes")
     ap.add_argument("--ns-requests", type=int, default=60, help="c2: requests of the compact serving pass")
     ap.add_argument("--err-inputs", default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--step-kernel", default="auto", choices=["auto", "direct", "staged", "tune"],
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "direct", "staged", "tune", "split"],
                     help="variant of the fused step kernels (auto: tuned on large offset-pattern operators)")
     ap.add_argument("--step-rpt", type=int, default=0, help="rows per thread of the plain steps (0: default)")
     ap.add_argument("--red-ctas", type=int, default=0, help="CTAs per SM of the direct dot-product steps (0: default)")

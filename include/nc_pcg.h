@@ -112,7 +112,11 @@ typedef enum { NC_POLY_CHEBYSHEV = 0, NC_POLY_NEWTON = 1 } nc_poly_form;
  * flight, CTAs per SM, L2 prefetch distance, CTAs of the dot-product steps)
  * on the solver's own operator and keeps the fastest for the plain steps and
  * for the steps with a dot product; pcg_tune_candidate lists what was
- * measured.  AUTO (default): TUNE for PSELL operators of at least 2^16 rows,
+ * measured.  SPLIT (steps with a dot product only; a tuner candidate, or
+ * forced with direct plain steps): the step without its dot product, then a
+ * separate deterministic dot product over the two finished vectors -- more
+ * bytes, but the step kernel keeps the plain step's registers and
+ * occupancy.  AUTO (default): TUNE for PSELL operators of at least 2^16 rows,
  * DIRECT otherwise.  For matrix-free stencils TUNE (AUTO: at least 2^20
  * points) times the z-chunk of the plain steps and, with a float apply, the
  * planes per z-march batch.  When the environment variable NC_TUNE_CACHE names a
@@ -124,7 +128,8 @@ typedef enum {
     NC_STEP_AUTO = 0,
     NC_STEP_DIRECT = 1,
     NC_STEP_STAGED = 2,
-    NC_STEP_TUNE = 3
+    NC_STEP_TUNE = 3,
+    NC_STEP_SPLIT = 4
 } nc_step_kernel;
 
 typedef struct {

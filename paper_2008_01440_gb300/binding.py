@@ -34,9 +34,10 @@ _FORMATS = {"auto": NC_FORMAT_AUTO, "csr": NC_FORMAT_CSR, "sell": NC_FORMAT_SELL
             "psell": NC_FORMAT_PSELL}
 
 
-NC_STEP_AUTO, NC_STEP_DIRECT, NC_STEP_STAGED, NC_STEP_TUNE = 0, 1, 2, 3
-_STEPS = {"auto": NC_STEP_AUTO, "direct": NC_STEP_DIRECT, "staged": NC_STEP_STAGED, "tune": NC_STEP_TUNE}
-_STEP_NAMES = {NC_STEP_DIRECT: "direct", NC_STEP_STAGED: "staged"}
+NC_STEP_AUTO, NC_STEP_DIRECT, NC_STEP_STAGED, NC_STEP_TUNE, NC_STEP_SPLIT = 0, 1, 2, 3, 4
+_STEPS = {"auto": NC_STEP_AUTO, "direct": NC_STEP_DIRECT, "staged": NC_STEP_STAGED, "tune": NC_STEP_TUNE,
+          "split": NC_STEP_SPLIT}
+_STEP_NAMES = {NC_STEP_DIRECT: "direct", NC_STEP_STAGED: "staged", NC_STEP_SPLIT: "split"}
 
 
 class nc_options(ctypes.Structure):

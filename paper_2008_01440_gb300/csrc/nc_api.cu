@@ -63,7 +63,7 @@ nc_status pcg_setup(nc_matrix A, double lambda_min, double lambda_max, int degre
     if (o.apply_dtype != NC_F64 && o.apply_dtype != NC_F32 && o.apply_dtype != NC_BF16) return NC_ERR_ARG;
     if (o.rr_period < 0) return NC_ERR_ARG;
     if (o.spmv_format < NC_FORMAT_AUTO || o.spmv_format > NC_FORMAT_PSELL) return NC_ERR_ARG;
-    if (o.step_kernel < NC_STEP_AUTO || o.step_kernel > NC_STEP_TUNE || o.step_stages < 0 || o.step_stages > 4 ||
+    if (o.step_kernel < NC_STEP_AUTO || o.step_kernel > NC_STEP_SPLIT || o.step_stages < 0 || o.step_stages > 4 ||
         o.step_stages == 1 || o.step_ctas_per_sm < 0 || o.step_ctas_per_sm > 8 || o.red_ctas_per_sm < 0 ||
         o.red_ctas_per_sm > 64 || o.step_rows_per_thread < 0 || o.step_rows_per_thread > 2 ||
         o.step_tile_order < 0 || o.step_tile_order > 1)
@@ -291,7 +291,8 @@ nc_status pcg_get_info(nc_solver S, nc_solver_info* info) {
     info->tune_us_sliced = S->tune_us[1];
     const StepTune& tp = S->opP.tune;
     info->step_kernel = tp.variant == STEP_STAGED ? NC_STEP_STAGED : NC_STEP_DIRECT;
-    info->dot_step_kernel = tp.dot_variant == STEP_STAGED ? NC_STEP_STAGED : NC_STEP_DIRECT;
+    info->dot_step_kernel = tp.dot_variant == STEP_STAGED ? NC_STEP_STAGED
+                          : (tp.dot_variant == STEP_SPLIT ? NC_STEP_SPLIT : NC_STEP_DIRECT);
     info->step_stages = tp.stages;
     info->step_ctas_per_sm = tp.ctas_per_sm;
     info->step_rows_per_thread = tp.rpt;
@@ -325,7 +326,8 @@ nc_status pcg_tune_candidate(nc_solver S, int i, nc_tune_candidate* out) {
     if (!S || !out || i < 0 || i >= (int)S->tune.size()) return NC_ERR_ARG;
     const TuneRec& t = S->tune[(size_t)i];
     out->op = t.op;
-    out->step_kernel = t.variant == STEP_STAGED ? NC_STEP_STAGED : NC_STEP_DIRECT;
+    out->step_kernel = t.variant == STEP_STAGED ? NC_STEP_STAGED
+                     : (t.variant == STEP_SPLIT ? NC_STEP_SPLIT : NC_STEP_DIRECT);
     out->stages = t.stages;
     out->ctas_per_sm = t.ctas_per_sm;
     out->rows_per_thread = t.rpt;

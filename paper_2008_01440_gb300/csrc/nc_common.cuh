@@ -36,9 +36,12 @@ constexpr int kRedOneTile = 64;   // CTAs per SM large enough for one tile per C
 // times candidates on the solver's own operator.
 enum StepVariant : int {
     STEP_DIRECT = 0,   // one row per thread, loads straight from global memory
-    STEP_STAGED = 1    // persistent CTAs; each 256-row tile's slices (and its r and
+    STEP_STAGED = 1,   // persistent CTAs; each 256-row tile's slices (and its r and
                        // x_{k-2} rows) brought into shared memory by bulk
                        // asynchronous copies, `stages` tiles ahead
+    STEP_SPLIT = 2     // steps with a dot product only: the plain step's kernel
+                       // (its variant and shape), then a separate dot product
+                       // over the step's two vectors (launch_dot_fast)
 };
 struct StepTune {
     int variant = STEP_DIRECT;       // plain steps (no dot product)
@@ -345,6 +348,10 @@ cudaError_t launch_p_update(int n, double* p, const double* z, PcgScalars* S,
 cudaError_t launch_scale_dot(int n, const double* r, double c, double* z, const Reduce& R,
                              const int* done, cudaStream_t st);
 // (a, b) -> R (skip if *done when done != null)
+// the same sum order for every call with the same n; 16-byte-aligned vectors
+// take a kernel with 16-byte loads, four pairs per round (others: launch_dot)
+cudaError_t launch_dot_fast(int n, const double* a, const double* b, const Reduce& R, const int* done,
+                            cudaStream_t st);
 cudaError_t launch_dot(int n, const double* a, const double* b, const Reduce& R, const int* done,
                        cudaStream_t st);
 // y = x (skip if *done)

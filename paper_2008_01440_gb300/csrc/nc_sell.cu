@@ -369,6 +369,18 @@ cudaError_t launch_sell_step(int n, const int32_t* slice_ptr, const int32_t* col
                              const double* rdot, const Reduce& R, const int* done, cudaStream_t st,
                              const StepTune& tune) {
     if (n <= 0) return cudaSuccess;
+    if (dot != 0 && tune.dot_variant == STEP_SPLIT) {
+        // the step without its dot product, then (rdot, y), (u, y) or (y, y)
+        // over the finished vectors (the dot steps write y in float64)
+        cudaError_t e = launch_sell_step(n, slice_ptr, col, pat, val, vdt, x_f32, y_f64, u, w, r, y, ca, cb, cc, cd,
+                                         0, nullptr, R, done, st, tune);
+        if (e != cudaSuccess) return e;
+        if (!y_f64) return cudaErrorInvalidValue;
+        const double* yd = static_cast<const double*>(y);
+        const double* a = dot == 1 ? rdot : (dot == 2 ? static_cast<const double*>(u) : yd);
+        if (dot == 2 && x_f32) return cudaErrorInvalidValue;
+        return launch_dot_fast(n, a, yd, R, done, st);
+    }
     if ((dot == 0 ? tune.variant : tune.dot_variant) == STEP_STAGED) {
         const cudaError_t e = launch_sell_staged(n, slice_ptr, col, pat, val, vdt, x_f32, y_f64, u, w, r, y, ca, cb,
                                                  cc, cd, dot, rdot, R, done, st, tune);

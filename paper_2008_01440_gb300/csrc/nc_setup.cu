@@ -573,6 +573,9 @@ nc_status tune_kind(nc_solver S, OpView& op, int kind, cudaStream_t st) {
                 t.red_ctas_per_sm = red;
                 cands.push_back(t);
             }
+            // or the plain step (as chosen for it) and a separate dot product
+            StepTune s = with_variant(base, STEP_SPLIT);
+            cands.push_back(s);
         }
     }
     // staged: (stages, CTAs per SM, rows per thread, tile order); a shape the
@@ -732,7 +735,7 @@ void tune_from_ints(const int* v, StepTune& t) {
 bool tune_ints_valid(const int* v) {
     auto var = [](int x) { return x == STEP_DIRECT || x == STEP_STAGED; };
     return var(v[0]) && v[1] >= 1 && v[1] <= 2 && v[2] >= 2 && v[2] <= 4 && v[3] >= 1 && v[3] <= 8 &&
-           (v[4] == 0 || v[4] == 1) && v[5] >= -1 && var(v[6]) && v[7] >= 1 && v[7] <= 2 && v[8] >= 2 &&
+           (v[4] == 0 || v[4] == 1) && v[5] >= -1 && (var(v[6]) || v[6] == STEP_SPLIT) && v[7] >= 1 && v[7] <= 2 && v[8] >= 2 &&
            v[8] <= 4 && v[9] >= 1 && v[9] <= 8 && (v[10] == 0 || v[10] == 1) && v[11] >= 1 &&
            v[11] <= kRedOneTile;
 }
@@ -812,6 +815,7 @@ nc_status setup_step_kernels(nc_solver S, cudaStream_t st) {
     const bool psell = S->opP.kind == OP_SELL && S->opP.pat.pstart != nullptr;
     const int mode = o.step_kernel;
     if (mode == NC_STEP_STAGED) t.variant = t.dot_variant = STEP_STAGED;
+    if (mode == NC_STEP_SPLIT) t.dot_variant = STEP_SPLIT;
     for (OpView* op : {&S->op64, &S->opP}) {
         const int vcap = op->tune.vcap, vcap2 = op->tune.vcap2, npoff = op->tune.npoff;
         op->tune = t;

@@ -62,6 +62,41 @@ dot_kernel(int n, const double* __restrict__ a, const double* __restrict__ b, co
     grid_reduce<kBlock>(acc, R);
 }
 
+// (a, b) for 16-byte-aligned vectors: each thread takes pairs of entries
+// gtid, gtid + T, ... (T threads), four pairs per round with all eight
+// 16-byte loads issued before the FMAs, summed in index order; the odd last
+// entry goes to thread 0.  The grid is fixed by n, so the sum's order is.
+__global__ void __launch_bounds__(kBlock)
+dot_pairs_kernel(int n, const double* __restrict__ a, const double* __restrict__ b, const Reduce R,
+                 const int* __restrict__ done) {
+    if (done != nullptr && *done) return;
+    const double2* a2 = reinterpret_cast<const double2*>(a);
+    const double2* b2 = reinterpret_cast<const double2*>(b);
+    const int n2 = n >> 1;
+    const int T = gridDim.x * kBlock;
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    double acc = 0.0;
+    for (; i + 3 * T < n2; i += 4 * T) {
+        double2 x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = __ldcs(a2 + i + u * T);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[u] = __ldcs(b2 + i + u * T);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            acc = fma(x[u].x, y[u].x, acc);
+            acc = fma(x[u].y, y[u].y, acc);
+        }
+    }
+    for (; i < n2; i += T) {
+        const double2 x = __ldcs(a2 + i), y = __ldcs(b2 + i);
+        acc = fma(x.x, y.x, acc);
+        acc = fma(x.y, y.y, acc);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) acc = fma(a[n - 1], b[n - 1], acc);
+    grid_reduce<kBlock>(acc, R);
+}
+
 __global__ void copy_kernel(int n, const double* __restrict__ x, double* __restrict__ y,
                             const int* __restrict__ done) {
     if (done != nullptr && *done) return;
@@ -172,6 +207,15 @@ cudaError_t launch_scale_dot(int n, const double* r, double c, double* z, const 
 cudaError_t launch_dot(int n, const double* a, const double* b, const Reduce& R, const int* done,
                        cudaStream_t st) {
     dot_kernel<<<vec_grid(n), kBlock, 0, st>>>(n, a, b, R, done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot_fast(int n, const double* a, const double* b, const Reduce& R, const int* done,
+                            cudaStream_t st) {
+    if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u)
+        return launch_dot(n, a, b, R, done, st);
+    // about eight pairs per thread: four-pair rounds, enough CTAs to fill the device
+    dot_pairs_kernel<<<vec_grid(((int64_t)n + 15) / 16), kBlock, 0, st>>>(n, a, b, R, done);
     return cudaGetLastError();
 }
 

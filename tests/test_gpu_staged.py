@@ -133,20 +133,24 @@ def test_staged_solve_matches_direct_and_oracle(env, dt):
     lo, hi, _, _ = nc.nc_bounds_lanczos(M, 20, to_dev(torch, W.uniform_vector(A.n, seed=3)))
     b = to_dev(torch, W.uniform_vector(A.n, seed=5))
     out = {}
-    for var in ("direct", "staged"):
+    for var in ("direct", "staged", "split"):
         S = nc.pcg_setup(M, lo, hi, 10, 1.001, apply_dtype=dt, spmv_format="psell", step_kernel=var,
                          rr_period=50 if dt != "f64" else 0, step_rows_per_thread=2 if dt == "bf16" else 0,
                          step_tile_order=1 if dt == "f32" else 0)
         info = nc.pcg_get_info(S)
-        assert info["step_kernel"] == var and info["dot_step_kernel"] == var
+        # split: direct plain steps, the dot-product steps as the plain step and a separate dot product
+        assert info["step_kernel"] == ("direct" if var == "split" else var) and info["dot_step_kernel"] == var
         x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
         r = nc.pcg_solve(S, b, x, 1e-8, 2000)
         assert nc.pcg_get_info(S)["faults"] == 0
         out[var] = (r, x.cpu().numpy())
-    (rd, xd), (rs, xs) = out["direct"], out["staged"]
-    assert rs["status"] == 0 and rs["true_relres"] <= 2e-8
-    assert abs(rs["iters"] - rd["iters"]) <= 1
-    assert rel_err(xs, xd) <= 1e-6
+    (rd, xd) = out["direct"]
+    for var in ("staged", "split"):
+        rs, xs = out[var]
+        assert rs["status"] == 0 and rs["true_relres"] <= 2e-8
+        assert abs(rs["iters"] - rd["iters"]) <= 1
+        assert rel_err(xs, xd) <= 1e-6
+    rs, xs = out["staged"]
     if dt == "f64":
         val, dis = O.jacobi_scale_csr(A.rowptr, A.col, A.val, A.n)
         mv = O.csr_matvec(A.rowptr, A.col, val, A.n)
@@ -178,7 +182,9 @@ def test_tuner_lists_candidates_and_keeps_parity(env, dt):
         assert chosen[0]["us"] == best and best > 0
     plain = [c for c in cands if c["op"] == "step" and c["chosen"]][0]
     assert info["step_kernel"] == plain["step_kernel"]
-    assert {c["step_kernel"] for c in cands} == {"direct", "staged"}
+    assert {c["step_kernel"] for c in cands if c["op"] == "step"} == {"direct", "staged"}
+    # the dot-product steps also try the plain step plus a separate dot product
+    assert {c["step_kernel"] for c in cands if c["op"] != "step"} == {"direct", "staged", "split"}
     v = W.uniform_vector(A.n, seed=9)
     z = torch.empty(A.n, dtype=torch.float64, device="cuda")
     nc.pcg_apply_poly(S, to_dev(torch, v), z)
