@@ -102,12 +102,13 @@ __device__ __forceinline__ void sell_rows2(const int row0, const int n, const in
 
 // Resident CTAs per SM the register budget aims at: plain steps 8 with
 // float64 values (32 registers), 5 with float32 (48), 4 with bfloat16 (64),
-// 3 with two rows per thread; dot-product variants 6 in float64 (40) and 4
-// in float (64).
+// 3 with two rows per thread; dot-product variants 8 in float64 (32: they fit
+// without spilling, so a persistent grid of 8 per SM is one wave) and 4 in
+// float (64).
 template <typename VT, typename XT, int DOT, int RPT>
 constexpr int sell_min_ctas() {
     constexpr bool f64 = sizeof(typename AccOf<XT>::type) == 8;
-    return DOT != 0 ? (f64 ? 6 : 4) : (RPT == 2 ? 3 : (f64 ? 8 : (sizeof(VT) == 4 ? 5 : 4)));
+    return DOT != 0 ? (f64 ? 8 : 4) : (RPT == 2 ? 3 : (f64 ? 8 : (sizeof(VT) == 4 ? 5 : 4)));
 }
 
 template <typename VT, typename XT, typename YT, int DOT, bool PAT, bool UNIT, int RPT = 1>
