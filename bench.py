@@ -81,6 +81,9 @@ def parse():
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the PCG loop from the host instead of the device-side graph "
                          "(same kernels; lets a profiler list every launch)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="c4csr: bracket the grouped engine's timed batches with cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off; the work is unchanged)")
     return ap.parse_args()
 
 
@@ -1074,7 +1077,7 @@ def run_c4_csr(args, rank, world, local_rank):
     t_setup = time.perf_counter() - t0
     pairs = [(i, c) for i, B in enumerate(Bs) for c in range(B.shape[0])]
     units = sum(Bs[i].shape[1] for i, _ in pairs)
-    eng = nc.pcg_batch_create(len(pairs), units, 32)
+    eng = nc.pcg_batch_create(len(pairs), units, 32, host_loop=args.host_loop)
     X = [torch.empty_like(B) for B in Bs]
 
     def one_batch(grouped):
@@ -1100,11 +1103,16 @@ def run_c4_csr(args, rank, world, local_rank):
         clk = start_clocks(torch, dev) if clocks else None
         times = []
         _, l0 = nc.pcg_batch_stats(eng)
+        rng = args.profile_range and grouped
+        if rng:
+            torch.cuda.profiler.start()
         for _ in range(args.steps):
             a = time.perf_counter()
             res = one_batch(grouped)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - a)
+        if rng:
+            torch.cuda.profiler.stop()
         ck = clk.stop() if clocks else None
         _, l1 = nc.pcg_batch_stats(eng)
         return replica_max(statistics.median(times), world), res, ck, l1 - l0
