@@ -465,13 +465,14 @@ NC_API nc_status pcg_batch_add(nc_batch B, int nx, int ny, int nz, double c0, do
  * otherwise.  The solver (and its matrix) must stay alive until the slot is
  * released.  Not in the paper: many explicit systems in one launch. */
 NC_API nc_status pcg_batch_add_solver(nc_batch B, nc_solver S, const double* b_dev, void* stream, int* slot);
-/* Admit m (1..8) right-hand sides of one such solver as a group: column c
+/* Admit m (1..8) right-hand sides of one such solver in groups: column c
  * (n float64 at B_dev + c * ldb, ldb >= n when m > 1) becomes slot slots[c]
  * (host array of m ints), each with its own state, result, collect and
- * release like any slot, but the group's step kernels load each row's
- * columns and values once and apply them to all its columns (a sparse times
- * dense-block product: the matrix is read once per step for the m
- * right-hand sides).  A column's iterates are bit-for-bit those of the same
+ * release like any slot, but the columns form groups of up to 4 (a last
+ * single column stays a plain slot) whose step kernels load each row's
+ * columns and values once and apply them to all the group's columns (a
+ * sparse times dense-block product: the matrix is read once per step for up
+ * to 4 right-hand sides).  A column's iterates are bit-for-bit those of the same
  * right-hand side in a slot of its own.  The group's vectors take m * n
  * contiguous pooled unknowns; NC_ERR_ADMISSION when m slots or that range
  * are not free.  m = 1 is pcg_batch_add_solver. */

@@ -106,22 +106,27 @@ struct BCtl {
     int maxit, ntiles, nvch, active;
     int iters_this_call, iter_limit, nstiles, gpstride;   // tiles of explicit-matrix slots; a group
                                                           // column's partials: [c * gpstride + tile]
-    int gseg[4];   // the group tile list's segments of widths 2, 4, 8: [gseg[i], gseg[i + 1])
+    int gseg[3];   // the group tile list's segments of widths 2 and 4: [gseg[i], gseg[i + 1])
+    int pad2;
 };
 
-// A group: up to kMaxGroup slots (columns) of one solver that share every
+// A group: up to kGroupWidth slots (columns) of one solver that share every
 // read of its matrix -- each step loads a row's columns and values once and
 // applies them to all the group's columns (a sparse times dense-block
 // product), as one solver's multi-right-hand-side block does.  Each column is
 // a slot of its own (state, result, collect, release); the group only owns
 // the tile list entry.  The columns' vectors lie in one pool range, column
 // c's at column 0's plus c * ld64 (float64 pool) or c * ldP (apply pool).
-constexpr int kMaxGroup = 8;
+constexpr int kMaxGroup = 8;     // right-hand sides one pcg_batch_add_solver_multi call takes
+// columns of one group: a call with more forms several groups (two groups of
+// 4 measured faster than one of 8 on the c4csr batch, 0.86 against 0.91 s:
+// the 8-wide kernel holds too few rows in flight at its register count)
+constexpr int kGroupWidth = 4;
 
 struct BGDesc {
     int M, n, k, coef0;          // M: the kernel width (2, 4 or 8 >= columns)
     int tile0, tile1, live, vdtP;   // live: bit c set while column c is owned
-    int slot[kMaxGroup];         // the engine slot of column c
+    int slot[kGroupWidth];       // the engine slot of column c
     double shift;
     const int32_t *sptr, *scol;
     SellPat pat;
@@ -728,7 +733,7 @@ __device__ void group_reduce(const double (&dv)[M], double* part, const int t, c
 template <int M>
 __global__ void __launch_bounds__(256, 3) bk_group_opq(const BGDesc* __restrict__ G, BState* S,
                                                        const BTile* __restrict__ T, BCtl* ctl, double* part) {
-    const int t0 = ctl->gseg[M == 2 ? 0 : (M == 4 ? 1 : 2)], t1 = ctl->gseg[M == 2 ? 1 : (M == 4 ? 2 : 3)];
+    const int t0 = ctl->gseg[M == 2 ? 0 : 1], t1 = ctl->gseg[M == 2 ? 1 : 2];
     for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
         const BTile tl = T[t];
         const BGDesc* g = G + tl.pair;
@@ -763,7 +768,7 @@ __global__ void __launch_bounds__(256, group_min_ctas<VT, PART, M>()) bk_group_c
                                                                         const int* __restrict__ ntile_step) {
     constexpr bool F64 = std::is_same<VT, double>::value;
     using XT = typename std::conditional<F64, double, float>::type;
-    constexpr int seg = M == 2 ? 0 : (M == 4 ? 1 : 2);
+    constexpr int seg = M == 2 ? 0 : 1;
     const int t0 = ctl->gseg[seg];
     const int t1 = t0 + ntile_step[j];   // the segment's tiles of groups with k >= j (by degree)
     for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
@@ -829,7 +834,7 @@ __global__ void __launch_bounds__(256, group_min_ctas<VT, PART, M>()) bk_group_c
 template <int M>
 __global__ void __launch_bounds__(256, 3) bk_group_true(const BGDesc* __restrict__ G, BState* S,
                                                         const BTile* __restrict__ T, BCtl* ctl, double* part) {
-    const int t0 = ctl->gseg[M == 2 ? 0 : (M == 4 ? 1 : 2)], t1 = ctl->gseg[M == 2 ? 1 : (M == 4 ? 2 : 3)];
+    const int t0 = ctl->gseg[M == 2 ? 0 : 1], t1 = ctl->gseg[M == 2 ? 1 : 2];
     for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
         const BTile tl = T[t];
         const BGDesc* g = G + tl.pair;
@@ -890,9 +895,9 @@ struct nc_batch_s {
     BGDesc* d_gdesc = nullptr;    // groups
     BTile* d_gtiles = nullptr;    // tiles of groups
     int* d_gntile_step = nullptr; // and their counts with k >= j
-    double* d_gpartials = nullptr;   // kMaxGroup rows of cap_gtiles
+    double* d_gpartials = nullptr;   // kGroupWidth rows of cap_gtiles
     int cap_gdesc = 0, cap_gtiles = 0;
-    int gwidths = 0;              // group widths the captured iteration launches (bits 2, 4, 8)
+    int gwidths = 0;              // group widths the captured iteration launches (bits 2 and 4)
     int graph_sell = 0;           // explicit-slot kernels the captured iteration launches:
                                   // bit 0 float32 / float64 values, bit 1 bfloat16 values;
                                   // bits 2 and 3 the same for groups
@@ -1020,7 +1025,6 @@ void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, c
                                                                              B->d_ctl, B->d_gpartials)
         NB_GROUP_OPQ(2);
         NB_GROUP_OPQ(4);
-        NB_GROUP_OPQ(8);
 #undef NB_GROUP_OPQ
     }
     bk_axpy<<<grid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
@@ -1056,7 +1060,7 @@ void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, c
     bk_group_cheb<VT, P, M><<<resident_grid(bk_group_cheb<VT, P, M>, 256), 256, 0, st>>>(                       \
         B->d_gdesc, B->d_state, B->d_gtiles, B->d_coef, B->d_ctl, B->d_gpartials, j,                            \
         B->d_gntile_step + (SEG) * (B->kmax + 1))
-#define NB_GROUP_CHEB(VT, P) NB_GROUP_CHEB1(VT, P, 2, 0); NB_GROUP_CHEB1(VT, P, 4, 1); NB_GROUP_CHEB1(VT, P, 8, 2)
+#define NB_GROUP_CHEB(VT, P) NB_GROUP_CHEB1(VT, P, 2, 0); NB_GROUP_CHEB1(VT, P, 4, 1)
             if (B->flags & NC_BATCH_F64_APPLY) {
                 NB_GROUP_CHEB(double, 1);
                 NB_GROUP_CHEB(double, 2);
@@ -1086,7 +1090,6 @@ void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, c
                                                                                B->d_ctl, B->d_gpartials)
         NB_GROUP_TRUE(2);
         NB_GROUP_TRUE(4);
-        NB_GROUP_TRUE(8);
 #undef NB_GROUP_TRUE
     }
     bk_cond<<<1, 1, 0, st>>>(B->d_ctl, h, use_cond);
@@ -1165,7 +1168,7 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
     }
     // groups: one segment of the list per width, each by degree as well
     std::vector<BTile> gtiles;
-    std::vector<int> gorder, gnstep(3 * (B->kmax + 1), 0);
+    std::vector<int> gorder, gnstep(2 * (B->kmax + 1), 0);
     for (int g = 0; g < (int)B->groups.size(); ++g)
         if (B->groups[g].live) gorder.push_back(g);
     std::stable_sort(gorder.begin(), gorder.end(), [&](int a, int b) {
@@ -1173,16 +1176,14 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
         return x.M != y.M ? x.M < y.M : x.k > y.k;
     });
     int want_sell = 0, want_w = 0;
-    int gseg[4] = {0, 0, 0, 0};
+    int gseg[3] = {0, 0, 0};
     for (int g : gorder) {
         BGDesc& gd = B->groups[g];
-        const int seg = gd.M == 2 ? 0 : (gd.M == 4 ? 1 : 2);
-        const int s0 = (int)gtiles.size();
-        for (int i = seg + 1; i < 4; ++i) gseg[i] = s0;   // segments after this one start at the end so far
-        gd.tile0 = s0;
+        const int seg = gd.M == 2 ? 0 : 1;
+        gd.tile0 = (int)gtiles.size();
         for (int f0 = 0; f0 < gd.n; f0 += kSellTileRows) gtiles.push_back(BTile{g, f0, 0, 0});
         gd.tile1 = (int)gtiles.size();
-        for (int i = seg + 1; i < 4; ++i) gseg[i] = gd.tile1;
+        for (int i = seg + 1; i < 3; ++i) gseg[i] = gd.tile1;   // later segments start at the end so far
         for (int j = 0; j <= std::min(gd.k, B->kmax); ++j) gnstep[seg * (B->kmax + 1) + j] = gd.tile1 - gseg[seg];
         gd.coef0 = (int)coef.size();
         coef.insert(coef.end(), B->gcoefs[g].begin(), B->gcoefs[g].end());
@@ -1216,7 +1217,7 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
         const int np = std::max(std::max(B->cap_tiles, B->cap_vch), B->cap_stiles);
         if ((s = balloc(reinterpret_cast<void**>(&B->d_partials), sizeof(double) * (size_t)np))) return s;
         if ((s = balloc(reinterpret_cast<void**>(&B->d_gpartials),
-                        sizeof(double) * kMaxGroup * (size_t)B->cap_gtiles)))
+                        sizeof(double) * kGroupWidth * (size_t)B->cap_gtiles)))
             return s;
         if ((s = build_batch_graph(B))) return s;
     }
@@ -1243,7 +1244,7 @@ nc_status sync_tables(nc_batch B, cudaStream_t st) {
     NB_CU(cudaMemcpyAsync(B->d_desc, B->desc.data(), sizeof(BDesc) * B->cap_slots, cudaMemcpyHostToDevice, st));
     B->h_ctl->ntiles = (int)tiles.size();
     B->h_ctl->nstiles = (int)stiles.size();
-    for (int i = 0; i < 4; ++i) B->h_ctl->gseg[i] = gseg[i];
+    for (int i = 0; i < 3; ++i) B->h_ctl->gseg[i] = gseg[i];
     B->h_ctl->gpstride = B->cap_gtiles;
     B->h_ctl->nvch = (int)vch.size();
     // the host vectors must outlive the copies
@@ -1286,7 +1287,7 @@ nc_status pcg_batch_create(int max_slots, int64_t max_unknowns, int kmax, int fl
         if ((s = balloc(reinterpret_cast<void**>(&B->d_ctl), sizeof(BCtl)))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->d_ntile_step), sizeof(int) * (kmax + 1)))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->d_sntile_step), sizeof(int) * (kmax + 1)))) break;
-        if ((s = balloc(reinterpret_cast<void**>(&B->d_gntile_step), sizeof(int) * 3 * (kmax + 1)))) break;
+        if ((s = balloc(reinterpret_cast<void**>(&B->d_gntile_step), sizeof(int) * 2 * (kmax + 1)))) break;
         if ((s = balloc(reinterpret_cast<void**>(&B->pool64), sizeof(double) * 6 * (size_t)max_unknowns))) break;
         // apply vectors: 4 float32 per unknown (t0..t2, r32), or 3 float64 (+ slack
         // for the 16-byte rounding of the split below)
@@ -1435,10 +1436,11 @@ nc_status pcg_batch_add_solver_multi(nc_batch B, nc_solver S, int m, const doubl
     if (S->k < 1 || S->k > B->kmax || S->n < 1) return NC_ERR_ARG;
     const int64_t n = S->n;
     if (m > 1 && ldb < n) return NC_ERR_ARG;
-    // the group kernels index column q by q times a 32-bit stride (6 n at
-    // most): larger systems are admitted as m separate slots, which give
-    // the same results (bit for bit)
-    const bool grouped = m > 1 && (int64_t)(kMaxGroup - 1) * 6 * n < ((int64_t)1 << 31);
+    // the columns form groups of up to kGroupWidth (a last one of a single
+    // column is a plain slot); the group kernels index column q by q times a
+    // 32-bit stride (6 n at most), so larger systems are admitted as m
+    // separate slots, which give the same results (bit for bit)
+    const bool groupable = (int64_t)(kGroupWidth - 1) * 6 * n < ((int64_t)1 << 31);
     std::vector<int> ids;
     for (int i = 0; i < B->cap_slots && (int)ids.size() < m; ++i)
         if (!B->used[i]) ids.push_back(i);
@@ -1467,18 +1469,23 @@ nc_status pcg_batch_add_solver_multi(nc_batch B, nc_solver S, int m, const doubl
         c.xu = sc[j].cd == 1.0 ? 1 : 0;
         cf[j - 1] = c;
     }
-    int g = -1;
-    if (grouped) {
-        for (int i = 0; i < (int)B->groups.size(); ++i)
-            if (B->groups[i].live == 0) { g = i; break; }
-        if (g < 0) {
-            g = (int)B->groups.size();
-            B->groups.push_back(BGDesc{});
-            B->gcoefs.emplace_back();
-        }
-    }
+    int g = -1, gc0 = 0, gw = 0;   // the current chunk's group, first column and width
     const int grid = (int)std::min<int64_t>(4096, (n + 255) / 256);
     for (int c = 0; c < m; ++c) {
+        if (c % kGroupWidth == 0) {   // a new chunk of columns
+            gc0 = c;
+            gw = std::min(kGroupWidth, m - c);
+            g = -1;
+            if (groupable && gw > 1) {
+                for (int i = 0; i < (int)B->groups.size(); ++i)
+                    if (B->groups[i].live == 0) { g = i; break; }
+                if (g < 0) {
+                    g = (int)B->groups.size();
+                    B->groups.push_back(BGDesc{});
+                    B->gcoefs.emplace_back();
+                }
+            }
+        }
         const int s = ids[c];
         const int64_t oc = o + c * n;
         BDesc d{};
@@ -1502,14 +1509,14 @@ nc_status pcg_batch_add_solver_multi(nc_batch B, nc_solver S, int m, const doubl
             float* base32 = B->pool32 + 4 * oc;
             d.t0 = base32; d.t1 = base32 + n; d.t2 = base32 + 2 * n; d.r32 = base32 + 3 * n;
         }
-        if (g >= 0 && c == 0) {   // the group: column 0's vectors, the matrix, the strides
+        if (g >= 0 && c == gc0) {   // the group: its first column's vectors, the matrix, the strides
             BGDesc gd{};
-            gd.M = m <= 2 ? 2 : (m <= 4 ? 4 : kMaxGroup);
+            gd.M = gw <= 2 ? 2 : kGroupWidth;
             gd.n = (int)n;
             gd.k = S->k;
-            gd.live = (1 << m) - 1;
+            gd.live = (1 << gw) - 1;
             gd.vdtP = d.vdtP;
-            for (int q = 0; q < kMaxGroup; ++q) gd.slot[q] = ids[q < m ? q : 0];
+            for (int q = 0; q < kGroupWidth; ++q) gd.slot[q] = ids[gc0 + (q < gw ? q : 0)];
             gd.shift = d.shift;
             gd.sptr = d.sptr; gd.scol = d.scol; gd.pat = d.pat; gd.val64 = d.val64; gd.valP = d.valP;
             gd.b = d.b; gd.x = d.x; gd.r = d.r; gd.z = d.z; gd.p = d.p; gd.q = d.q;
@@ -1566,7 +1573,8 @@ nc_status pcg_solve_batched(int nsys, const nc_solver* S, const int* nrhs, const
     if (st != NC_OK) return st;
     std::vector<int> ids;
     ids.reserve(slots);
-    // each system's right-hand sides in groups of up to kMaxGroup columns
+    // each system's right-hand sides, up to kMaxGroup per admission (groups of
+    // up to kGroupWidth columns)
     for (int i = 0; i < nsys && st == NC_OK; ++i)
         for (int c0 = 0; c0 < nrhs[i] && st == NC_OK; c0 += kMaxGroup) {
             const int m = std::min(kMaxGroup, nrhs[i] - c0);
@@ -1632,7 +1640,7 @@ nc_status pcg_batch_run(nc_batch B, double tol, int maxit, int iter_limit, void*
         const int gs = B->graph_sell;
         const bool f64 = (B->flags & NC_BATCH_F64_APPLY) != 0;
         const int nsell = f64 ? ((gs & 3) ? 1 : 0) : 2 * ((gs & 1) + ((gs >> 1) & 1));
-        const int nw = ((B->gwidths >> 1) & 1) + ((B->gwidths >> 2) & 1) + ((B->gwidths >> 3) & 1);
+        const int nw = ((B->gwidths >> 1) & 1) + ((B->gwidths >> 2) & 1);
         const int ngrp = nw * (f64 ? ((gs & 12) ? 2 : 0) : 2 * (((gs >> 2) & 1) + ((gs >> 3) & 1)));
         B->stat_launches += (int64_t)c->iters_this_call *
                             (B->kmax + 5 + (nsell ? nsell * B->kmax + 2 : 0) + (ngrp ? ngrp * B->kmax + 2 * nw : 0));
@@ -1691,7 +1699,7 @@ nc_status pcg_batch_release(nc_batch B, int slot, void* stream) {
     const int g = B->gid[slot];
     if (g >= 0) {   // the group no longer reads or writes this column; gone with its last
         BGDesc& gd = B->groups[g];
-        for (int q = 0; q < kMaxGroup; ++q)
+        for (int q = 0; q < kGroupWidth; ++q)
             if (((gd.live >> q) & 1) && gd.slot[q] == slot) gd.live &= ~(1 << q);
         if (gd.live == 0) B->gcoefs[g].clear();
         B->gid[slot] = -1;

@@ -183,9 +183,10 @@ def _run_singles(torch, nc, S, B, f64):
 @pytest.mark.parametrize("dt", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("m", [2, 3, 5, 8])
 def test_group_columns_are_bit_identical_to_single_slots(env, dt, m):
-    """A group of m right-hand sides (the matrix read once per step for all
-    of them, kernel width 2, 4 or 8 with the unused columns masked) gives
-    every column exactly the iterates of a slot of its own."""
+    """m right-hand sides admitted together (groups of up to 4 reading the
+    matrix once per step -- 3 runs a width-4 kernel with a column masked, 5
+    a group of 4 and a plain slot, 8 two groups) give every column exactly
+    the iterates of a slot of its own."""
     torch, nc = env
     A, scale, k, M, S, lo, hi = _setup(torch, nc, dt, [_systems()[m % 2 * 2]])[0]
     B = to_dev(torch, np.stack([W.uniform_vector(A.n, seed=500 + c) for c in range(m)]))
