@@ -239,8 +239,9 @@ __global__ void __launch_bounds__(256) bk_opq(const BDesc* __restrict__ D, BStat
         c.cc = 0.0;
         c.terms = 0;
         const int k0 = tl.bz * kZC, k1 = min(k0 + kZC, d.nz);
-        const double dv = stencil_flat<double, double, 2>(d.nx, d.ny, d.nz, tl.f0, k0, k1, d.p, nullptr, nullptr,
-                                                          d.q, c, nullptr, tid);
+        // (the admitted operator is Jacobi scaled: c0 == 1, the centre takes no multiply)
+        const double dv = stencil_flat<double, double, 2, false, true>(d.nx, d.ny, d.nz, tl.f0, k0, k1, d.p, nullptr,
+                                                                       nullptr, d.q, c, nullptr, tid);
         reduce_slot(dv, partials, t, d.tile0, d.tile1 - d.tile0, st, ctl, BF_ALPHA);
     }
 }
@@ -307,9 +308,10 @@ __global__ void __launch_bounds__(256) bk_cheb(const BDesc* __restrict__ D, BSta
             c.cb = bc.cbd;
             c.cc = bc.ccd;
             c.terms = bc.terms;
-            double* tb[3] = {d.dt0, d.dt1, d.dt2};
-            const double* u = (j == 1) ? d.r : tb[(j - 1) % 3];
-            const double* w = (j >= 3) ? tb[(j - 2) % 3] : nullptr;
+            // the rotating vectors by index, selected (an indexed array would sit in local memory)
+            auto tb = [&](int i) -> double* { return i == 0 ? d.dt0 : (i == 1 ? d.dt1 : d.dt2); };
+            const double* u = (j == 1) ? d.r : tb((j - 1) % 3);
+            const double* w = (j >= 3) ? tb((j - 2) % 3) : nullptr;
             if (j == d.k) {
                 const double dv =
                     bc.xu ? stencil_flat<double, double, 1, true>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r, d.z, c,
@@ -318,10 +320,10 @@ __global__ void __launch_bounds__(256) bk_cheb(const BDesc* __restrict__ D, BSta
                                                             tid);
                 reduce_slot(dv, partials, t, d.tile0, d.tile1 - d.tile0, st, ctl, BF_RZ);
             } else if (bc.xu) {
-                stencil_flat<double, double, 0, true>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r, tb[j % 3], c,
+                stencil_flat<double, double, 0, true>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r, tb(j % 3), c,
                                                       nullptr, tid);
             } else {
-                stencil_flat<double, double, 0>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r, tb[j % 3], c, nullptr,
+                stencil_flat<double, double, 0>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r, tb(j % 3), c, nullptr,
                                                 tid);
             }
         } else {
@@ -333,15 +335,15 @@ __global__ void __launch_bounds__(256) bk_cheb(const BDesc* __restrict__ D, BSta
         c.cb = bc.cb;
         c.cc = bc.cc;
         c.terms = bc.terms;
-        float* tb[3] = {d.t0, d.t1, d.t2};
-        const float* u = (j == 1) ? d.r32 : tb[(j - 1) % 3];
-        const float* w = (j >= 3) ? tb[(j - 2) % 3] : nullptr;
+        auto tb = [&](int i) -> float* { return i == 0 ? d.t0 : (i == 1 ? d.t1 : d.t2); };
+        const float* u = (j == 1) ? d.r32 : tb((j - 1) % 3);
+        const float* w = (j >= 3) ? tb((j - 2) % 3) : nullptr;
         if (j == d.k) {
             const double dv = stencil_flat<float, double, 1>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r32, d.z, c,
                                                              d.r, tid);
             reduce_slot(dv, partials, t, d.tile0, d.tile1 - d.tile0, st, ctl, BF_RZ);
         } else {
-            stencil_flat<float, float, 0>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r32, tb[j % 3], c, nullptr, tid);
+            stencil_flat<float, float, 0>(d.nx, d.ny, d.nz, tl.f0, k0, k1, u, w, d.r32, tb(j % 3), c, nullptr, tid);
         }
         }
     }

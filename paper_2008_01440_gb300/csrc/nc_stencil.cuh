@@ -110,7 +110,9 @@ __device__ __forceinline__ double stencil_tile(const int nx, const int ny, const
 // called by all lanes of each warp together.
 constexpr int kFT = 256;
 
-template <typename XT, typename YT, int DOT, bool XU = false>
+// E1: e0 == 1 exactly (the Jacobi-scaled operator itself, q = A p and
+// b - A x): the centre term is u itself, no multiply (the same value).
+template <typename XT, typename YT, int DOT, bool XU = false, bool E1 = false>
 __device__ __forceinline__ double stencil_flat(const int nx, const int ny, const int nz, const int f0, const int k0,
                                                const int k1, const XT* __restrict__ u, const XT* __restrict__ w,
                                                const XT* __restrict__ r, YT* __restrict__ y,
@@ -168,7 +170,7 @@ __device__ __forceinline__ double stencil_flat(const int nx, const int ny, const
                 if constexpr (XU) {   // ex == -1 exactly
                     o = fma(c.e0, u_cur, -(xm + xp));
                 } else {
-                    o = c.e0 * u_cur;
+                    o = E1 ? u_cur : c.e0 * u_cur;
                     o = fma(c.ex, xm + xp, o);
                 }
                 o = fma(c.ey, ym[t] + yp[t], o);
