@@ -609,11 +609,22 @@ nc_status tune_kind(nc_solver S, OpView& op, int kind, cudaStream_t st) {
     double best = 0.0;
     int ibest = -1;
     const size_t first = S->tune.size();
-    for (const StepTune& t : cands) {
-        OpView v = op;
-        v.tune = t;
-        double us = 0.0;
-        NC_TRY(time_launches(st, [&]() { return launch_kind(S, v, kind, st); }, &us));
+    // two passes over the candidates, the second in reverse order; each keeps
+    // the lower of its two means (a transient slowdown during one
+    // measurement does not decide the choice)
+    std::vector<double> tus(cands.size(), 0.0);
+    for (int pass = 0; pass < 2; ++pass)
+        for (size_t ii = 0; ii < cands.size(); ++ii) {
+            const size_t ci = pass == 0 ? ii : cands.size() - 1 - ii;
+            OpView v = op;
+            v.tune = cands[ci];
+            double us = 0.0;
+            NC_TRY(time_launches(st, [&]() { return launch_kind(S, v, kind, st); }, &us));
+            tus[ci] = pass == 0 ? us : std::min(tus[ci], us);
+        }
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+        const StepTune& t = cands[ci];
+        const double us = tus[ci];
         const int var = kind == 0 ? t.variant : t.dot_variant;
         S->tune.push_back(TuneRec{kind, var, kind == 0 ? t.stages : t.dot_stages,
                                   kind == 0 ? t.ctas_per_sm : t.dot_ctas_per_sm, kind == 0 ? t.rpt : t.dot_rpt,
