@@ -37,189 +37,12 @@
 #include <type_traits>
 #include <vector>
 
-#include "nc_internal.h"
-#include "nc_sell.cuh"
-#include "nc_stencil.cuh"
+#include "nc_batch.cuh"
+
 
 namespace nc {
+using namespace batch;
 namespace {
-
-constexpr int kVch = 8192;    // vector-chunk length
-constexpr int kZC = 32;       // planes per stencil tile (32 measured 4.5% faster than 16 or 64 on the 256-system batch)
-// rows per tile of an explicit-matrix slot or group: 8 blocks of 256 rows
-// (one row per thread), so that a step over a few systems still has a tile
-// for every CTA, while the per-tile reduction (fence + atomic) stays rare
-constexpr int kSellTileRows = 8 * kFT;
-
-enum Phase : int { PH_FREE = 0, PH_INIT = 1, PH_RUN = 2, PH_FINISH = 3, PH_DONE = 4 };
-
-enum BFin : int { BF_ALPHA = 1, BF_RR = 2, BF_INIT = 3, BF_RZ = 4, BF_START = 5, BF_TRUE = 6 };
-
-enum SlotKind : int { SLOT_STENCIL = 0, SLOT_SELL = 1 };
-
-struct BDesc {
-    int nx, ny, nz, n;
-    int k, coef0;
-    int tile0, tile1, vch0, vch1;
-    double c0, cx, cy, cz;
-    double *b, *x, *r, *z, *p, *q;
-    float *t0, *t1, *t2, *r32;      // float32 apply (NC_BATCH_F64_APPLY unset)
-    double *dt0, *dt1, *dt2;        // float64 apply: the Chebyshev vectors, r read directly
-    // SLOT_SELL: an explicit matrix in a solver's SELL-32 layout (borrowed):
-    // slice offsets, columns (plain) or offset patterns, the float64 values of
-    // the stored operator S (A - theta' I, its constant diagonal possibly left
-    // out) and the values inside P (apply precision vdtP); A u = S u + shift u
-    int kind, vdtP;
-    double shift;
-    const int32_t *sptr, *scol;
-    SellPat pat;
-    const double* val64;
-    const void* valP;
-    const double* disv;             // d^{-1/2} per unknown (null: the slot's scalar)
-};
-
-struct BState {
-    double rz, pq, alpha, beta, rr, bb, rr_true;
-    int iter, phase, status, n_dot, n_prec;
-    unsigned int counter;
-};
-
-struct BCoef {
-    float e0, ex, ey, ez, cb, cc;
-    int terms;
-    int xu;                                // float64 fields: exd == -1 exactly (no centre multiply)
-    double e0d, exd, eyd, ezd, cbd, ccd;   // float64 apply: the step for the scaled iterates
-    // SLOT_SELL: y = ca u + cb w + cc r + cd A' u (nc_step.cuh's StepCoef),
-    // float for the float32 apply, double for the float64 one; xu: cd == 1
-};
-
-struct BTile {
-    int pair, f0, pad, bz;   // f0: first point of the tile in the flattened xy-plane
-};
-
-struct BVch {
-    int pair, start;
-};
-
-struct BCtl {
-    double tol2;
-    int maxit, ntiles, nvch, active;
-    int iters_this_call, iter_limit, nstiles, gpstride;   // tiles of explicit-matrix slots; a group
-                                                          // column's partials: [c * gpstride + tile]
-    int gseg[3];   // the group tile list's segments of widths 2 and 4: [gseg[i], gseg[i + 1])
-    int pad2;
-};
-
-// A group: up to kGroupWidth slots (columns) of one solver that share every
-// read of its matrix -- each step loads a row's columns and values once and
-// applies them to all the group's columns (a sparse times dense-block
-// product), as one solver's multi-right-hand-side block does.  Each column is
-// a slot of its own (state, result, collect, release); the group only owns
-// the tile list entry.  The columns' vectors lie in one pool range, column
-// c's at column 0's plus c * ld64 (float64 pool) or c * ldP (apply pool).
-constexpr int kMaxGroup = 8;     // right-hand sides one pcg_batch_add_solver_multi call takes
-// columns of one group: a call with more forms several groups (two groups of
-// 4 measured faster than one of 8 on the c4csr batch, 0.86 against 0.91 s:
-// the 8-wide kernel holds too few rows in flight at its register count)
-constexpr int kGroupWidth = 4;
-
-struct BGDesc {
-    int M, n, k, coef0;          // M: the kernel width (2, 4 or 8 >= columns)
-    int tile0, tile1, live, vdtP;   // live: bit c set while column c is owned
-    int slot[kGroupWidth];       // the engine slot of column c
-    double shift;
-    const int32_t *sptr, *scol;
-    SellPat pat;
-    const double* val64;
-    const void* valP;
-    double *b, *x, *r, *z, *p, *q;   // column 0
-    float *t0, *t1, *t2, *r32;
-    double *dt0, *dt1, *dt2;
-    int ld64, ldP;
-};
-
-__device__ void bfinalize(BState* st, BCtl* ctl, int kind, double s) {
-    const bool finite = isfinite(s);
-    switch (kind) {
-    case BF_ALPHA:
-        st->n_dot += 1;
-        st->pq = s;
-        if (!(s > 0.0) || !finite) {
-            st->status = finite ? NC_ERR_INDEFINITE : NC_ERR_BREAKDOWN;
-            st->phase = PH_FINISH;
-        } else {
-            st->alpha = st->rz / s;
-        }
-        break;
-    case BF_RR:
-        st->n_dot += 1;
-        st->rr = s;
-        st->iter += 1;
-        if (!finite) { st->status = NC_ERR_BREAKDOWN; st->phase = PH_FINISH; }
-        else if (s <= ctl->tol2 * st->bb) { st->status = NC_OK; st->phase = PH_FINISH; }
-        else if (st->iter >= ctl->maxit) { st->status = NC_ERR_MAXIT; st->phase = PH_FINISH; }
-        break;
-    case BF_INIT:   // r = b: ||r0||^2 = ||b||^2
-        st->bb = s;
-        st->rr = s;
-        if (!finite) { st->status = NC_ERR_BREAKDOWN; st->phase = PH_FINISH; }
-        else if (s == 0.0) { st->status = NC_OK; st->phase = PH_FINISH; }
-        else if (ctl->maxit <= 0) { st->status = NC_ERR_MAXIT; st->phase = PH_FINISH; }
-        break;
-    case BF_RZ:
-        st->n_dot += 1;
-        st->n_prec += 1;
-        if (!(s > 0.0) || !finite) {
-            st->status = finite ? NC_ERR_INDEFINITE : NC_ERR_BREAKDOWN;
-            st->phase = PH_FINISH;
-        } else if (st->phase == PH_INIT) {
-            st->rz = s;
-        } else {
-            st->beta = s / st->rz;
-            st->rz = s;
-        }
-        break;
-    case BF_START:
-        if (st->phase == PH_INIT) st->phase = PH_RUN;
-        break;
-    case BF_TRUE:
-        st->rr_true = s;
-        st->phase = PH_DONE;
-        atomicSub(&ctl->active, 1);
-        break;
-    default:
-        break;
-    }
-}
-
-// Per-slot reduction: this CTA's partial goes to partials[slotidx]; the CTA
-// completing the slot's count-th partial sums partials[first, first+count)
-// in order and finalizes.  All threads of the CTA call it (uniform).
-__device__ void reduce_slot(double v, double* partials, int slotidx, int first, int count, BState* st, BCtl* ctl,
-                            int kind) {
-    __shared__ double sh[256];
-    __shared__ int is_last;
-    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    v = block_sum<256>(v, sh, tid);
-    if (tid == 0) {
-        partials[slotidx] = v;
-        __threadfence();
-        const unsigned int t = atomicAdd(&st->counter, 1u);
-        is_last = (t == (unsigned int)count - 1u);
-    }
-    __syncthreads();
-    if (is_last) {
-        __threadfence();
-        double s = 0.0;
-        for (int i = tid; i < count; i += 256) s += __ldcg(&partials[first + i]);
-        s = block_sum<256>(s, sh, tid);
-        if (tid == 0) {
-            bfinalize(st, ctl, kind, s);
-            st->counter = 0u;
-        }
-    }
-    __syncthreads();
-}
 
 __global__ void __launch_bounds__(256) bk_opq(const BDesc* __restrict__ D, BState* S, const BTile* __restrict__ T,
                                               BCtl* ctl, double* partials) {
@@ -394,467 +217,6 @@ __global__ void __launch_bounds__(256) bk_true(const BDesc* __restrict__ D, BSta
     }
 }
 
-// ---- explicit-matrix slots: their own kernels over their own tile list
-// (kSellTileRows rows per tile, walked by the CTA in 256-row blocks), so
-// that the stencil kernels keep their register budgets; launched only while
-// the engine holds such slots
-
-// The dot terms of a tile's rows are summed with __dadd_rn (never fused
-// into an fma with the term's product), so that the single-slot kernels and
-// the group kernels round them alike whatever the compiler contracts.
-
-// Chebyshev step j of the explicit slots whose values inside P are VT
-// (double: the float64 apply; float or bfloat16: the float32 apply)
-template <typename VT, typename XT, typename YT, int DOT, bool UNIT>
-__device__ __forceinline__ double sell_block(int row, int n, const int32_t* sptr, const int32_t* scol,
-                                             const SellPat& pat, const VT* val, const XT* u, const XT* w,
-                                             const XT* r, YT* y, const StepCoef<typename AccOf<XT>::type>& c,
-                                             const double* rdot) {
-    if (row >= n) return 0.0;
-    if (pat.pstart != nullptr)
-        return sell_row<VT, XT, YT, DOT, true, UNIT>(row, n, sptr, nullptr, pat, val, u, w, r, y, c, rdot);
-    return sell_row<VT, XT, YT, DOT, false, UNIT>(row, n, sptr, scol, pat, val, u, w, r, y, c, rdot);
-}
-
-__global__ void __launch_bounds__(256, 6) bk_sell_opq(const BDesc* __restrict__ D, BState* S,
-                                                   const BTile* __restrict__ T, BCtl* ctl, double* partials) {
-    const int tid = threadIdx.x;
-    const int nt = ctl->nstiles;
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        const BTile tl = T[t];
-        BState* st = S + tl.pair;
-        if (st->phase != PH_RUN) continue;
-        const BDesc* dp = D + tl.pair;
-        const int n = dp->n;
-        const SellPat pat = dp->pat;
-        const int32_t *sptr = dp->sptr, *scol = dp->scol;
-        const double* val = dp->val64;
-        const double* p = dp->p;
-        double* q = dp->q;
-        StepCoef<double> c;   // q = A' p + shift p, (p, q)
-        c.ca = dp->shift; c.cb = 0.0; c.cc = 0.0; c.cd = 1.0;
-        c.terms = (c.ca != 0.0 ? kTermU : 0) | kUnitD;
-        const int tile0 = dp->tile0, ntl = dp->tile1 - dp->tile0;
-        double dv = 0.0;
-        const int f1 = min(tl.f0 + kSellTileRows, n);
-#pragma unroll 1
-        for (int f = tl.f0; f < f1; f += kFT)
-            dv = __dadd_rn(dv, sell_block<double, double, double, 2, true>(f + tid, n, sptr, scol, pat, val, p,
-                                                                            nullptr, nullptr, q, c, nullptr));
-        reduce_slot(dv, partials, t, tile0, ntl, st, ctl, BF_ALPHA);
-    }
-}
-
-// PART: 0 every slot (float64 apply), 1 only the slots whose last step is
-// j (with (r, z)), 2 only the others -- the float kernels are split so that
-// each inlines one row path and keeps its register budget
-template <typename VT, int PART>
-__global__ void __launch_bounds__(256, std::is_same<VT, double>::value ? 6 : 4) bk_sell_cheb(const BDesc* __restrict__ D, BState* S,
-                                                    const BTile* __restrict__ T, const BCoef* __restrict__ C,
-                                                    BCtl* ctl, double* partials, int j,
-                                                    const int* __restrict__ ntile_step) {
-    constexpr bool F64 = std::is_same<VT, double>::value;
-    using XT = typename std::conditional<F64, double, float>::type;
-    using AT = XT;
-    const int tid = threadIdx.x;
-    const int nt = ntile_step[j];   // tiles of slots with k >= j (ordered by degree)
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        const BTile tl = T[t];
-        BState* st = S + tl.pair;
-        const int ph = st->phase;
-        if (ph != PH_RUN && ph != PH_INIT) continue;
-        const BDesc* dp = D + tl.pair;
-        const int k = dp->k;
-        if (j > k) continue;
-        if ((PART == 1 && j != k) || (PART == 2 && j == k)) continue;
-        const int vdt = dp->vdtP;
-        if (!F64 && (vdt == NC_BF16) != std::is_same<VT, __nv_bfloat16>::value) continue;   // the other kernel's
-        // the fields this step needs, read once per tile
-        const int n = dp->n;
-        const int32_t* sptr = dp->sptr;
-        const int32_t* scol = dp->scol;
-        const SellPat pat = dp->pat;
-        const VT* val = F64 ? reinterpret_cast<const VT*>(dp->val64) : static_cast<const VT*>(dp->valP);
-        const double* r64 = dp->r;
-        double* z = dp->z;
-        XT *t0, *t1, *t2;
-        const XT* r;
-        if constexpr (F64) {
-            t0 = dp->dt0; t1 = dp->dt1; t2 = dp->dt2;
-            r = dp->r;
-        } else {
-            t0 = dp->t0; t1 = dp->t1; t2 = dp->t2;
-            r = dp->r32;
-        }
-        // the rotating vectors by index, selected (not an indexed array: no local memory)
-        auto tb = [&](int i) -> XT* { return i == 0 ? t0 : (i == 1 ? t1 : t2); };
-        const int tile0 = dp->tile0, ntl = dp->tile1 - dp->tile0;
-        const BCoef bc = C[dp->coef0 + j - 1];
-        StepCoef<AT> c;
-        if constexpr (F64) {
-            c.ca = bc.e0d; c.cb = bc.cbd; c.cc = bc.ccd; c.cd = bc.exd;
-        } else {
-            c.ca = bc.e0; c.cb = bc.cb; c.cc = bc.cc; c.cd = bc.ex;
-        }
-        c.terms = bc.terms;
-        const XT* u = (j == 1) ? r : tb((j - 1) % 3);
-        const XT* w = (j >= 3) ? tb((j - 2) % 3) : nullptr;
-        const int f1 = min(tl.f0 + kSellTileRows, n);
-        const bool unit = F64 && bc.xu;
-        if constexpr (PART != 2) {
-            if (j == k) {
-                double dv = 0.0;
-#pragma unroll 1
-                for (int f = tl.f0; f < f1; f += kFT)
-                    dv = __dadd_rn(dv, unit ? sell_block<VT, XT, double, 1, F64>(f + tid, n, sptr, scol, pat, val, u,
-                                                                                  w, r, z, c, r64)
-                                            : sell_block<VT, XT, double, 1, false>(f + tid, n, sptr, scol, pat, val,
-                                                                                    u, w, r, z, c, r64));
-                reduce_slot(dv, partials, t, tile0, ntl, st, ctl, BF_RZ);
-                continue;
-            }
-        }
-        if constexpr (PART != 1) {
-            XT* y = tb(j % 3);
-#pragma unroll 1
-            for (int f = tl.f0; f < f1; f += kFT) {
-                if (unit) sell_block<VT, XT, XT, 0, F64>(f + tid, n, sptr, scol, pat, val, u, w, r, y, c, nullptr);
-                else sell_block<VT, XT, XT, 0, false>(f + tid, n, sptr, scol, pat, val, u, w, r, y, c, nullptr);
-            }
-        }
-    }
-}
-
-__global__ void __launch_bounds__(256) bk_sell_true(const BDesc* __restrict__ D, BState* S,
-                                                    const BTile* __restrict__ T, BCtl* ctl, double* partials) {
-    const int tid = threadIdx.x;
-    const int nt = ctl->nstiles;
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-        const BTile tl = T[t];
-        BState* st = S + tl.pair;
-        if (st->phase != PH_FINISH) continue;
-        const BDesc* dp = D + tl.pair;
-        const int n = dp->n;
-        const SellPat pat = dp->pat;
-        const int32_t *sptr = dp->sptr, *scol = dp->scol;
-        const double* val = dp->val64;
-        StepCoef<double> c;   // q = b - (A' x + shift x), ||q||^2
-        c.ca = -dp->shift; c.cb = 0.0; c.cc = 1.0; c.cd = -1.0;
-        c.terms = (c.ca != 0.0 ? kTermU : 0) | kTermR;
-        const double *x = dp->x, *b = dp->b;
-        double* q = dp->q;
-        const int tile0 = dp->tile0, ntl = dp->tile1 - dp->tile0;
-        double dv = 0.0;
-        const int f1 = min(tl.f0 + kSellTileRows, n);
-#pragma unroll 1
-        for (int f = tl.f0; f < f1; f += kFT)
-            dv = __dadd_rn(dv, sell_block<double, double, double, 3, false>(f + tid, n, sptr, scol, pat, val, x,
-                                                                             nullptr, b, q, c, nullptr));
-        reduce_slot(dv, partials, t, tile0, ntl, st, ctl, BF_TRUE);
-    }
-}
-
-// ---- groups: kernels over the group tile list, one instance per width M
-// (2, 4 or 8 columns), each over its own segment of the list (kSellTileRows
-// rows of one group per tile, all its columns)
-
-// One row of a group of width M: the row's columns (or offsets) and values
-// are loaded once per slot and applied to every column whose bit is set in
-// `mask` (the others are neither gathered nor written).  Per column the
-// products are summed in the single-slot kernels' order and the epilogue is
-// theirs (step_row_out), so a column's result is bit-identical to the same
-// right-hand side in a slot of its own.  Column q's vectors are column 0's
-// plus q times their stride (32-bit: groups are formed only where 7 strides
-// fit).
-template <typename VT, typename XT, typename YT, int DOT, bool PAT, bool UNIT, int M>
-__device__ __forceinline__ void sell_row_group(const int row, const int n, const int32_t* __restrict__ slice_ptr,
-                                               const int32_t* __restrict__ col, const SellPat& pat,
-                                               const VT* __restrict__ val, const XT* u, const int ldu,
-                                               const XT* w, const int ldw, const XT* r, const int ldr, YT* y,
-                                               const int ldy, const double* rdot, const int ldd,
-                                               const StepCoef<typename AccOf<XT>::type>& c, const unsigned mask,
-                                               double (&dv)[M]) {
-    using AT = typename AccOf<XT>::type;
-    // slots per load group: about 16 (float) or 8 (double) gathers in flight
-    constexpr int G = sizeof(AT) == 8 ? (M >= 8 ? 1 : 8 / M) : (M >= 8 ? 2 : 16 / M);
-    const int s = row >> 5;
-    const int beg = slice_ptr[s];
-    const int len = (slice_ptr[s + 1] - beg) >> 5;   // warp-uniform
-    const VT* vp = val + beg + (row & 31);
-    const int32_t* cp = nullptr;
-    const int32_t* op = nullptr;
-    if constexpr (PAT) op = pat.poff + __ldg(pat.pstart + s);
-    else cp = col + beg + (row & 31);
-    AT acc[M];
-#pragma unroll
-    for (int q = 0; q < M; ++q) acc[q] = AT(0);
-    for (int j0 = 0; j0 < len; j0 += G) {
-        int cj[G];
-        AT vj[G];
-#pragma unroll
-        for (int t = 0; t < G; ++t) {
-            cj[t] = row;
-            vj[t] = AT(0);
-            if (j0 + t < len) {
-                if constexpr (PAT) cj[t] = min(max(row + __ldg(op + t), 0), n - 1);
-                else cj[t] = ld_stream(cp + 32 * t);
-                vj[t] = (AT)ld_stream(vp + 32 * t);
-            }
-        }
-        AT xv[M][G];
-#pragma unroll
-        for (int q = 0; q < M; ++q)
-#pragma unroll
-            for (int t = 0; t < G; ++t)
-                xv[q][t] = (((mask >> q) & 1u) && j0 + t < len) ? (AT)__ldg(u + (q * ldu + cj[t])) : AT(0);
-#pragma unroll
-        for (int q = 0; q < M; ++q)
-#pragma unroll
-            for (int t = 0; t < G; ++t)
-                if (j0 + t < len) acc[q] = fma(vj[t], xv[q][t], acc[q]);
-        vp += 32 * G;
-        if constexpr (PAT) op += G;
-        else cp += 32 * G;
-    }
-#pragma unroll
-    for (int q = 0; q < M; ++q)
-        if ((mask >> q) & 1u) {
-            const double t = step_row_out<XT, YT, DOT, AT, UNIT>(row, acc[q], c, u + q * ldu,
-                                                                 w ? w + q * ldw : nullptr, r ? r + q * ldr : nullptr,
-                                                                 y + q * ldy, rdot ? rdot + q * ldd : nullptr);
-            if (DOT != 0) dv[q] = __dadd_rn(dv[q], t);
-        }
-}
-
-// The tile's rows [f0, f1), one per thread per block of kFT rows.
-template <typename VT, typename XT, typename YT, int DOT, bool UNIT, int M>
-__device__ __forceinline__ void group_rows(const BGDesc* g, const int f0, const int f1, const VT* val, const XT* u,
-                                           const int ldu, const XT* w, const int ldw, const XT* r, const int ldr,
-                                           YT* y, const int ldy, const double* rdot,
-                                           const StepCoef<typename AccOf<XT>::type>& c, const unsigned mask,
-                                           double (&dv)[M]) {
-    const int n = g->n;
-    const int32_t *sptr = g->sptr, *scol = g->scol;
-    const SellPat pat = g->pat;
-    const int ldd = g->ld64;
-    if (pat.pstart != nullptr) {
-#pragma unroll 1
-        for (int f = f0; f < f1; f += kFT) {
-            const int row = f + (int)threadIdx.x;
-            if (row < n)
-                sell_row_group<VT, XT, YT, DOT, true, UNIT, M>(row, n, sptr, nullptr, pat, val, u, ldu, w, ldw, r,
-                                                               ldr, y, ldy, rdot, ldd, c, mask, dv);
-        }
-    } else {
-#pragma unroll 1
-        for (int f = f0; f < f1; f += kFT) {
-            const int row = f + (int)threadIdx.x;
-            if (row < n)
-                sell_row_group<VT, XT, YT, DOT, false, UNIT, M>(row, n, sptr, scol, pat, val, u, ldu, w, ldw, r,
-                                                                ldr, y, ldy, rdot, ldd, c, mask, dv);
-        }
-    }
-}
-
-// The columns of a group whose slot is in phase ph0 or ph1.  Uniform across
-// the CTA: a column's phase changes only when its last tile is reduced,
-// which cannot happen before this CTA has reduced the tile it reads for.
-template <int M>
-__device__ __forceinline__ unsigned group_mask(const BGDesc* g, const BState* S, int ph0, int ph1) {
-    unsigned m = 0;
-    const int live = g->live;
-#pragma unroll
-    for (int q = 0; q < M; ++q)
-        if ((live >> q) & 1) {
-            const int ph = S[g->slot[q]].phase;
-            if (ph == ph0 || ph == ph1) m |= 1u << q;
-        }
-    return m;
-}
-
-// Every selected column's partial of tile t into its own row of the group
-// partials (column q: [q * gpstride + tile]) and its slot's reduction, all
-// columns in one pass: each column's block sum takes block_sum's order and
-// the last tile's total reduce_slot's, so the sums are those of single slots.
-template <int M>
-__device__ void group_reduce(const double (&dv)[M], double* part, const int t, const BGDesc* g, BState* S,
-                             BCtl* ctl, const unsigned mask, const int kind) {
-    __shared__ double sh[M][256];
-    __shared__ int last[M];
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int q = 0; q < M; ++q) sh[q][tid] = dv[q];
-    __syncthreads();
-#pragma unroll
-    for (int s = 128; s >= 32; s >>= 1) {
-        if (tid < s) {
-#pragma unroll
-            for (int q = 0; q < M; ++q) sh[q][tid] += sh[q][tid + s];
-        }
-        __syncthreads();
-    }
-    if (tid < 32) {
-#pragma unroll
-        for (int q = 0; q < M; ++q) {
-            double r = sh[q][tid];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-            if (tid == 0) sh[q][0] = r;
-        }
-    }
-    __syncthreads();
-    const int gps = ctl->gpstride, tile0 = g->tile0, ntl = g->tile1 - g->tile0;
-    if (tid < M) {
-        int is_last = 0;
-        if ((mask >> tid) & 1u) {
-            part[tid * gps + t] = sh[tid][0];
-            __threadfence();
-            const unsigned int c = atomicAdd(&S[g->slot[tid]].counter, 1u);
-            is_last = (c == (unsigned int)ntl - 1u);
-        }
-        last[tid] = is_last;
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int q = 0; q < M; ++q) {
-        if (!last[q]) continue;   // uniform
-        __threadfence();
-        const int first = q * gps + tile0;
-        double s = 0.0;
-        for (int i = tid; i < ntl; i += 256) s += __ldcg(&part[first + i]);
-        s = block_sum<256>(s, &sh[0][0], tid);
-        if (tid == 0) {
-            BState* st = S + g->slot[q];
-            bfinalize(st, ctl, kind, s);
-            st->counter = 0u;
-        }
-        __syncthreads();
-    }
-}
-
-template <int M>
-__global__ void __launch_bounds__(256, 3) bk_group_opq(const BGDesc* __restrict__ G, BState* S,
-                                                       const BTile* __restrict__ T, BCtl* ctl, double* part) {
-    const int t0 = ctl->gseg[M == 2 ? 0 : 1], t1 = ctl->gseg[M == 2 ? 1 : 2];
-    for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
-        const BTile tl = T[t];
-        const BGDesc* g = G + tl.pair;
-        const unsigned mask = group_mask<M>(g, S, PH_RUN, PH_RUN);
-        if (mask == 0u) continue;
-        StepCoef<double> c;   // q = A' p + shift p, (p, q)
-        c.ca = g->shift; c.cb = 0.0; c.cc = 0.0; c.cd = 1.0;
-        c.terms = (c.ca != 0.0 ? kTermU : 0) | kUnitD;
-        const int ld = g->ld64;
-        double dv[M];
-#pragma unroll
-        for (int q = 0; q < M; ++q) dv[q] = 0.0;
-        group_rows<double, double, double, 2, true, M>(g, tl.f0, min(tl.f0 + kSellTileRows, g->n), g->val64, g->p,
-                                                       ld, nullptr, 0, nullptr, 0, g->q, ld, nullptr, c, mask, dv);
-        group_reduce<M>(dv, part, t, g, S, ctl, mask, BF_ALPHA);
-    }
-}
-
-// PART 1: only the groups whose last step is j (z = P r in float64 and
-// (r, z)), 2: only the others (no dot product: the most frequent kernel
-// keeps more CTAs per SM)
-template <typename VT, int PART, int M>
-constexpr int group_min_ctas() {
-    return PART != 2 ? 3 : (std::is_same<VT, double>::value ? (M >= 8 ? 4 : 5) : (M >= 8 ? 5 : 6));
-}
-
-template <typename VT, int PART, int M>
-__global__ void __launch_bounds__(256, group_min_ctas<VT, PART, M>()) bk_group_cheb(const BGDesc* __restrict__ G, BState* S,
-                                                                        const BTile* __restrict__ T,
-                                                                        const BCoef* __restrict__ C, BCtl* ctl,
-                                                                        double* part, int j,
-                                                                        const int* __restrict__ ntile_step) {
-    constexpr bool F64 = std::is_same<VT, double>::value;
-    using XT = typename std::conditional<F64, double, float>::type;
-    constexpr int seg = M == 2 ? 0 : 1;
-    const int t0 = ctl->gseg[seg];
-    const int t1 = t0 + ntile_step[j];   // the segment's tiles of groups with k >= j (by degree)
-    for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
-        const BTile tl = T[t];
-        const BGDesc* g = G + tl.pair;
-        const int k = g->k;
-        if (j > k) continue;
-        if ((PART == 1 && j != k) || (PART == 2 && j == k)) continue;
-        if (!F64 && (g->vdtP == NC_BF16) != std::is_same<VT, __nv_bfloat16>::value) continue;
-        const unsigned mask = group_mask<M>(g, S, PH_RUN, PH_INIT);
-        if (mask == 0u) continue;
-        const BCoef bc = C[g->coef0 + j - 1];
-        const VT* val = F64 ? reinterpret_cast<const VT*>(g->val64) : static_cast<const VT*>(g->valP);
-        const int ldP = g->ldP, ld64 = g->ld64;
-        XT *v0, *v1, *v2;
-        const XT* r;
-        int ldr;
-        if constexpr (F64) {
-            v0 = g->dt0; v1 = g->dt1; v2 = g->dt2;
-            r = g->r;
-            ldr = ld64;
-        } else {
-            v0 = g->t0; v1 = g->t1; v2 = g->t2;
-            r = g->r32;
-            ldr = ldP;
-        }
-        auto tb = [&](int i) -> XT* { return i == 0 ? v0 : (i == 1 ? v1 : v2); };
-        StepCoef<XT> c;
-        if constexpr (F64) {
-            c.ca = bc.e0d; c.cb = bc.cbd; c.cc = bc.ccd; c.cd = bc.exd;
-        } else {
-            c.ca = bc.e0; c.cb = bc.cb; c.cc = bc.cc; c.cd = bc.ex;
-        }
-        c.terms = bc.terms;
-        const XT* u = (j == 1) ? r : tb((j - 1) % 3);
-        const int ldu = (j == 1) ? ldr : ldP;
-        const XT* w = (j >= 3) ? tb((j - 2) % 3) : nullptr;
-        const int f1 = min(tl.f0 + kSellTileRows, g->n);
-        const bool unit = F64 && bc.xu;
-        double dv[M];
-#pragma unroll
-        for (int q = 0; q < M; ++q) dv[q] = 0.0;
-        if constexpr (PART == 1) {
-            if (unit)
-                group_rows<VT, XT, double, 1, F64, M>(g, tl.f0, f1, val, u, ldu, w, ldP, r, ldr, g->z, ld64, g->r, c,
-                                                      mask, dv);
-            else
-                group_rows<VT, XT, double, 1, false, M>(g, tl.f0, f1, val, u, ldu, w, ldP, r, ldr, g->z, ld64, g->r,
-                                                        c, mask, dv);
-            group_reduce<M>(dv, part, t, g, S, ctl, mask, BF_RZ);
-        } else {
-            XT* y = tb(j % 3);
-            if (unit)
-                group_rows<VT, XT, XT, 0, F64, M>(g, tl.f0, f1, val, u, ldu, w, ldP, r, ldr, y, ldP, nullptr, c, mask,
-                                                  dv);
-            else
-                group_rows<VT, XT, XT, 0, false, M>(g, tl.f0, f1, val, u, ldu, w, ldP, r, ldr, y, ldP, nullptr, c,
-                                                    mask, dv);
-        }
-    }
-}
-
-template <int M>
-__global__ void __launch_bounds__(256, 3) bk_group_true(const BGDesc* __restrict__ G, BState* S,
-                                                        const BTile* __restrict__ T, BCtl* ctl, double* part) {
-    const int t0 = ctl->gseg[M == 2 ? 0 : 1], t1 = ctl->gseg[M == 2 ? 1 : 2];
-    for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
-        const BTile tl = T[t];
-        const BGDesc* g = G + tl.pair;
-        const unsigned mask = group_mask<M>(g, S, PH_FINISH, PH_FINISH);
-        if (mask == 0u) continue;
-        StepCoef<double> c;   // q = b - (A' x + shift x), ||q||^2
-        c.ca = -g->shift; c.cb = 0.0; c.cc = 1.0; c.cd = -1.0;
-        c.terms = (c.ca != 0.0 ? kTermU : 0) | kTermR;
-        const int ld = g->ld64;
-        double dv[M];
-#pragma unroll
-        for (int q = 0; q < M; ++q) dv[q] = 0.0;
-        group_rows<double, double, double, 3, false, M>(g, tl.f0, min(tl.f0 + kSellTileRows, g->n), g->val64, g->x,
-                                                        ld, nullptr, 0, g->b, ld, g->q, ld, nullptr, c, mask, dv);
-        group_reduce<M>(dv, part, t, g, S, ctl, mask, BF_TRUE);
-    }
-}
-
 __global__ void bk_cond(BCtl* ctl, cudaGraphConditionalHandle h, int use_cond) {
     ctl->iters_this_call += 1;
     const int go = ctl->active > 0 && ctl->iters_this_call < ctl->iter_limit;
@@ -999,101 +361,40 @@ nc_status grow(void** p, int* cap, int need, size_t elem) {
 }
 
 // One PCG iteration of every slot (the graph body).
-// Persistent grid of a kernel: as many CTAs as the device holds at once (a
-// second, partial wave would start its statically assigned tiles late),
-// capped at kCtasPerSm per SM.
-template <typename K>
-int resident_grid(K kernel, int threads) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm <= 0) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    if (per_sm > kCtasPerSm) per_sm = kCtasPerSm;
-    return per_sm * num_sms();
-}
-
 void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, cudaStream_t st) {
     const dim3 tb(kTX, kTY);
     const int grid = vec_grid_max();   // persistent CTAs over the work lists (stencil and vector kernels)
+    SellLaunch L;
+    L.desc = B->d_desc;
+    L.state = B->d_state;
+    L.stiles = B->d_stiles;
+    L.gdesc = B->d_gdesc;
+    L.gtiles = B->d_gtiles;
+    L.coef = B->d_coef;
+    L.ctl = B->d_ctl;
+    L.partials = B->d_partials;
+    L.gpartials = B->d_gpartials;
+    L.sntile_step = B->d_sntile_step;
+    L.gntile_step = B->d_gntile_step;
+    L.kmax = B->kmax;
+    L.graph_sell = B->graph_sell;
+    L.gwidths = B->gwidths;
+    L.f64 = (B->flags & NC_BATCH_F64_APPLY) != 0;
     bk_opq<<<grid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
-    if (B->graph_sell & 3)
-        bk_sell_opq<<<resident_grid(bk_sell_opq, 256), 256, 0, st>>>(B->d_desc, B->d_state, B->d_stiles, B->d_ctl,
-                                                                     B->d_partials);
-    if (B->graph_sell & 12) {
-#define NB_GROUP_OPQ(M) \
-    if (B->gwidths & (M)) \
-        bk_group_opq<M><<<resident_grid(bk_group_opq<M>, 256), 256, 0, st>>>(B->d_gdesc, B->d_state, B->d_gtiles, \
-                                                                             B->d_ctl, B->d_gpartials)
-        NB_GROUP_OPQ(2);
-        NB_GROUP_OPQ(4);
-#undef NB_GROUP_OPQ
-    }
+    launch_sell_opq(L, st);
     bk_axpy<<<grid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
     for (int j = 1; j <= B->kmax; ++j) {
-        if (B->flags & NC_BATCH_F64_APPLY)
+        if (L.f64)
             bk_cheb<true><<<grid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_coef, B->d_ctl,
                                                      B->d_partials, j, B->d_ntile_step);
         else
             bk_cheb<false><<<grid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_coef, B->d_ctl,
                                                       B->d_partials, j, B->d_ntile_step);
-        if (B->graph_sell & 3) {
-#define NB_SELL_ARGS B->d_desc, B->d_state, B->d_stiles, B->d_coef, B->d_ctl, B->d_partials, j, B->d_sntile_step
-#define NB_SELL_CHEB(VT, P) bk_sell_cheb<VT, P><<<resident_grid(bk_sell_cheb<VT, P>, 256), 256, 0, st>>>(NB_SELL_ARGS)
-            if (B->flags & NC_BATCH_F64_APPLY) {
-                NB_SELL_CHEB(double, 0);
-            } else {
-                if (B->graph_sell & 1) {
-                    NB_SELL_CHEB(float, 1);
-                    NB_SELL_CHEB(float, 2);
-                }
-                if (B->graph_sell & 2) {
-                    NB_SELL_CHEB(__nv_bfloat16, 1);
-                    NB_SELL_CHEB(__nv_bfloat16, 2);
-                }
-            }
-#undef NB_SELL_CHEB
-#undef NB_SELL_ARGS
-        }
-        if (B->graph_sell & 12) {
-            // one launch per (value type, part, width) present
-#define NB_GROUP_CHEB1(VT, P, M, SEG)                                                                           \
-    if (B->gwidths & (M))                                                                                       \
-    bk_group_cheb<VT, P, M><<<resident_grid(bk_group_cheb<VT, P, M>, 256), 256, 0, st>>>(                       \
-        B->d_gdesc, B->d_state, B->d_gtiles, B->d_coef, B->d_ctl, B->d_gpartials, j,                            \
-        B->d_gntile_step + (SEG) * (B->kmax + 1))
-#define NB_GROUP_CHEB(VT, P) NB_GROUP_CHEB1(VT, P, 2, 0); NB_GROUP_CHEB1(VT, P, 4, 1)
-            if (B->flags & NC_BATCH_F64_APPLY) {
-                NB_GROUP_CHEB(double, 1);
-                NB_GROUP_CHEB(double, 2);
-            } else {
-                if (B->graph_sell & 4) {
-                    NB_GROUP_CHEB(float, 1);
-                    NB_GROUP_CHEB(float, 2);
-                }
-                if (B->graph_sell & 8) {
-                    NB_GROUP_CHEB(__nv_bfloat16, 1);
-                    NB_GROUP_CHEB(__nv_bfloat16, 2);
-                }
-            }
-#undef NB_GROUP_CHEB
-#undef NB_GROUP_CHEB1
-        }
+        launch_sell_cheb(L, j, st);
     }
     bk_pupd<<<grid, 256, 0, st>>>(B->d_desc, B->d_state, B->d_vch, B->d_ctl, B->d_partials);
     bk_true<<<grid, tb, 0, st>>>(B->d_desc, B->d_state, B->d_tiles, B->d_ctl, B->d_partials);
-    if (B->graph_sell & 3)
-        bk_sell_true<<<resident_grid(bk_sell_true, 256), 256, 0, st>>>(B->d_desc, B->d_state, B->d_stiles,
-                                                                       B->d_ctl, B->d_partials);
-    if (B->graph_sell & 12) {
-#define NB_GROUP_TRUE(M) \
-    if (B->gwidths & (M)) \
-        bk_group_true<M><<<resident_grid(bk_group_true<M>, 256), 256, 0, st>>>(B->d_gdesc, B->d_state, B->d_gtiles, \
-                                                                               B->d_ctl, B->d_gpartials)
-        NB_GROUP_TRUE(2);
-        NB_GROUP_TRUE(4);
-#undef NB_GROUP_TRUE
-    }
+    launch_sell_true(L, st);
     bk_cond<<<1, 1, 0, st>>>(B->d_ctl, h, use_cond);
 }
 
