@@ -363,7 +363,12 @@ nc_status grow(void** p, int* cap, int need, size_t elem) {
 // One PCG iteration of every slot (the graph body).
 void enqueue_iteration(nc_batch B, cudaGraphConditionalHandle h, int use_cond, cudaStream_t st) {
     const dim3 tb(kTX, kTY);
-    const int grid = vec_grid_max();   // persistent CTAs over the work lists (stencil and vector kernels)
+    // CTAs over the work lists of the stencil and vector kernels: four times
+    // as many as the device holds at 8 per SM, so that each walks a few tiles
+    // and the CTAs that finish early are replaced instead of waiting for the
+    // slowest's statically assigned tiles (C4 batch: 1x 2502, 2x 2647, 4x 2718,
+    // 8x 2704, 16x 2650 solves/s)
+    const int grid = 4 * vec_grid_max();
     SellLaunch L;
     L.desc = B->d_desc;
     L.state = B->d_state;
