@@ -133,18 +133,19 @@ void launch_sell_opq(const SellLaunch& L, cudaStream_t st);
 void launch_sell_cheb(const SellLaunch& L, int j, cudaStream_t st);
 void launch_sell_true(const SellLaunch& L, cudaStream_t st);
 
-// Persistent grid of a kernel: as many CTAs as the device holds at once (a
-// second, partial wave would start its statically assigned tiles late),
-// capped at kCtasPerSm per SM.
+// Grid of a kernel over a work list: `waves` times as many CTAs as the
+// device holds at once (per SM capped at kCtasPerSm).  One wave keeps every
+// CTA resident with statically assigned tiles; several let CTAs that finish
+// early be replaced (the group kernels: 4 waves, c4csr 1359 -> 1407 solves/s).
 template <typename K>
-inline int resident_grid(K kernel, int threads) {
+inline int resident_grid(K kernel, int threads, int waves = 1) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm <= 0) {
         cudaGetLastError();
         per_sm = 1;
     }
     if (per_sm > kCtasPerSm) per_sm = kCtasPerSm;
-    return per_sm * num_sms();
+    return waves * per_sm * num_sms();
 }
 
 namespace {   // device helpers: one copy per translation unit

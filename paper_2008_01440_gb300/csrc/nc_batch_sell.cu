@@ -480,7 +480,7 @@ void launch_sell_opq(const SellLaunch& L, cudaStream_t st) {
     if (L.graph_sell & 12) {
 #define NB_GROUP_OPQ(M) \
     if (L.gwidths & (M)) \
-        bk_group_opq<M><<<resident_grid(bk_group_opq<M>, 256), 256, 0, st>>>(L.gdesc, L.state, L.gtiles, L.ctl, \
+        bk_group_opq<M><<<resident_grid(bk_group_opq<M>, 256, 4), 256, 0, st>>>(L.gdesc, L.state, L.gtiles, L.ctl, \
                                                                              L.gpartials)
         NB_GROUP_OPQ(2);
         NB_GROUP_OPQ(4);
@@ -511,7 +511,7 @@ void launch_sell_cheb(const SellLaunch& L, int j, cudaStream_t st) {
         // one launch per (value type, part, width) present
 #define NB_GROUP_CHEB1(VT, P, M, SEG)                                                                         \
     if (L.gwidths & (M))                                                                                      \
-    bk_group_cheb<VT, P, M><<<resident_grid(bk_group_cheb<VT, P, M>, 256), 256, 0, st>>>(                     \
+    bk_group_cheb<VT, P, M><<<resident_grid(bk_group_cheb<VT, P, M>, 256, 4), 256, 0, st>>>(                     \
         L.gdesc, L.state, L.gtiles, L.coef, L.ctl, L.gpartials, j, L.gntile_step + (SEG) * (L.kmax + 1))
 #define NB_GROUP_CHEB(VT, P) NB_GROUP_CHEB1(VT, P, 2, 0); NB_GROUP_CHEB1(VT, P, 4, 1)
         if (L.f64) {
@@ -538,7 +538,7 @@ void launch_sell_true(const SellLaunch& L, cudaStream_t st) {
     if (L.graph_sell & 12) {
 #define NB_GROUP_TRUE(M) \
     if (L.gwidths & (M)) \
-        bk_group_true<M><<<resident_grid(bk_group_true<M>, 256), 256, 0, st>>>(L.gdesc, L.state, L.gtiles, L.ctl, \
+        bk_group_true<M><<<resident_grid(bk_group_true<M>, 256, 4), 256, 0, st>>>(L.gdesc, L.state, L.gtiles, L.ctl, \
                                                                                L.gpartials)
         NB_GROUP_TRUE(2);
         NB_GROUP_TRUE(4);
