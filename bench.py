@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--c4-systems", type=int, default=256, help="c4: number of systems")
     ap.add_argument("--no-modes", action="store_true", help="skip the other apply precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--no-north-star", action="store_true",
+    ap.add_argument("--no-batched", action="store_true",
                     help="c2: skip the compact batched (c4) and serving (c5) passes")
     ap.add_argument("--ns-requests", type=int, default=60, help="c2: requests of the compact serving pass")
     ap.add_argument("--err-inputs", default=None, help=argparse.SUPPRESS)
@@ -514,7 +514,7 @@ def run_system(args, spec, rank, world, local_rank):
     # solves against the plain FP64 solver one at a time (compact passes of
     # the batched and serving workloads, same process and GPU)
     north = None
-    if args.workload == "c2" and world == 1 and not args.no_north_star:
+    if args.workload == "c2" and world == 1 and not args.no_batched:
         c4line, c4err = measure_c4(args, dev, world, plain_budget_s=20.0, steps=3, warmup=1,
                                    n_err=4 if want_err else 0)
         c5line, c5err = measure_c5(args, dev, world, args.ns_requests, n_err=4 if want_err else 0)
@@ -560,7 +560,7 @@ def run_system(args, spec, rank, world, local_rank):
         "all_converged": rec["all_converged"], "max_relres": rec["max_relres"],
         "clocks": main["clocks"], "e2e": e2e, "gpu_launches": launches_per_solve * args.steps,
         "roofline": roofline, "cpu_baseline": cpu, "modes": out_modes, "multi_rhs": multi, "degrees": degrees,
-        "two_level_block_jacobi": two_level, "north_star": north,
+        "two_level_block_jacobi": two_level, "batched_and_served": north,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
