@@ -513,16 +513,16 @@ def run_system(args, spec, rank, world, local_rank):
     # the target of the configuration: mixed-precision batched and served
     # solves against the plain FP64 solver one at a time (compact passes of
     # the batched and serving workloads, same process and GPU)
-    north = None
+    batched = None
     if args.workload == "c2" and world == 1 and not args.no_batched:
         c4line, c4err = measure_c4(args, dev, world, plain_budget_s=20.0, steps=3, warmup=1,
                                    n_err=4 if want_err else 0)
         c5line, c5err = measure_c5(args, dev, world, args.ns_requests, n_err=4 if want_err else 0)
         drop = ("metric", "unit", "n_gpus", "higher_is_better", "scaling", "vs_baseline")
-        north = {"c4_batched": {kk: vv for kk, vv in c4line.items() if kk not in drop},
+        batched = {"c4_batched": {kk: vv for kk, vv in c4line.items() if kk not in drop},
                  "c5_serving": {kk: vv for kk, vv in c5line.items() if kk not in drop}}
-        north["c4_batched"]["unit"] = north["c5_serving"]["unit"] = "solves/s"
-        north["c5_serving"]["note"] = (f"compact stream of {args.ns_requests} requests (the --workload c5 line "
+        batched["c4_batched"]["unit"] = batched["c5_serving"]["unit"] = "solves/s"
+        batched["c5_serving"]["note"] = (f"compact stream of {args.ns_requests} requests (the --workload c5 line "
                                        f"runs {args.requests})")
         if want_err:
             err_inputs["c4"] = c4err
@@ -536,10 +536,10 @@ def run_system(args, spec, rank, world, local_rank):
         for mode, e in (errs.get("c2") or {}).items():
             if mode in out_modes:
                 out_modes[mode]["err_vs_oracle"] = e
-        if north is not None:
+        if batched is not None:
             for key, nk in (("c4", "c4_batched"), ("c5", "c5_serving")):
                 if errs.get(key) is not None:
-                    north[nk]["err_vs_oracle"] = errs[key]
+                    batched[nk]["err_vs_oracle"] = errs[key]
 
     iters = rec["iters"]
     kk = max(k, 1)
@@ -560,7 +560,7 @@ def run_system(args, spec, rank, world, local_rank):
         "all_converged": rec["all_converged"], "max_relres": rec["max_relres"],
         "clocks": main["clocks"], "e2e": e2e, "gpu_launches": launches_per_solve * args.steps,
         "roofline": roofline, "cpu_baseline": cpu, "modes": out_modes, "multi_rhs": multi, "degrees": degrees,
-        "two_level_block_jacobi": two_level, "batched_and_served": north,
+        "two_level_block_jacobi": two_level, "batched_and_served": batched,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
